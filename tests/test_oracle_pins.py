@@ -1,0 +1,453 @@
+"""Pins of the CPU oracle to facts the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each checks it against a
+closed form, a library routine, an identity, brute force, or a value printed
+in the paper (Mukherjee et al. 2021).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import lpmv
+
+import ics
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+RNG = np.random.default_rng(12345)
+
+
+def idx(n, m):
+    return n * (n + 1) // 2 + m
+
+
+def full(a, n, m):
+    """X_n^m for m < 0 from the m >= 0 storage: X^{-m} = (-1)^m conj(X^m)."""
+    if m >= 0:
+        return a[idx(n, m)]
+    return (-1) ** (-m) * np.conj(a[idx(n, -m)])
+
+
+# --------------------------------------------------------------- harmonics
+
+@pytest.mark.parametrize("trial", range(6))
+def test_harmonics_match_legendre_closed_form(trial):
+    """Sec. 2.2 (Dehnen 2014 normalisation): Upsilon = r^n P_n^m e^{im phi}/(n+m)!,
+    Theta = (n-m)! P_n^m e^{im phi}/r^{n+1}, P without the Condon-Shortley
+    phase; scipy's lpmv includes it, hence the (-1)^m."""
+    p = 16
+    x, y, z = RNG.normal(size=3) * RNG.uniform(0.3, 3.0)
+    r = math.sqrt(x * x + y * y + z * z)
+    ct, ph = z / r, math.atan2(y, x)
+    U = oracle.regular(p, x, y, z)
+    T = oracle.irregular(p, x, y, z)
+    for n in range(p + 1):
+        for m in range(n + 1):
+            pbar = (-1) ** m * lpmv(m, n, ct)
+            e = np.exp(1j * m * ph)
+            u_ref = r ** n * pbar * e / math.factorial(n + m)
+            t_ref = math.factorial(n - m) * pbar * e / r ** (n + 1)
+            assert abs(U[idx(n, m)] - u_ref) <= 1e-12 * max(1e-300, abs(u_ref)) + 1e-14 * r ** n / math.factorial(n + m)
+            assert abs(T[idx(n, m)] - t_ref) <= 1e-12 * abs(t_ref) + 1e-13 * math.factorial(n - m) / r ** (n + 1)
+
+
+def test_harmonics_match_paper_p2_list():
+    """The explicit p = 2 list printed in Sec. 2.2: each regular harmonic is
+    one real constant times (printed re + i printed im)."""
+    rows = []
+    with open(os.path.join(GOLDEN, "harmonics_p2.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            n, m, re, im = line.split()
+            rows.append((int(n), int(m), re, im))
+    assert len(rows) == 6  # the 9 printed functions: 1 + 3 + 5 real parts
+    pts = RNG.normal(size=(20, 3))
+    for n, m, re, im in rows:
+        consts = []
+        for x, y, z in pts:
+            r = math.sqrt(x * x + y * y + z * z)
+            env = {"x": x, "y": y, "z": z, "r": r}
+            val = eval(re, {}, env) + (1j * eval(im, {}, env) if im != "-" else 0.0)
+            u = oracle.regular(2, x, y, z)[idx(n, m)]
+            consts.append(u / val)
+        consts = np.array(consts)
+        assert np.allclose(consts.imag, 0.0, atol=1e-12)
+        assert np.allclose(consts.real, consts.real[0], rtol=1e-12)
+        assert consts.real[0] != 0.0
+
+
+@pytest.mark.parametrize("p", [2, 5, 10, 20])
+def test_addition_theorem(p):
+    """1/|x - y| = sum_{n<=p} sum_m conj(Upsilon_n^m(y)) Theta_n^m(x) up to
+    the truncation bound (|y|/|x|)^{p+1} / (|x| - |y|)."""
+    for _ in range(20):
+        x = RNG.normal(size=3)
+        x *= 2.0 / np.linalg.norm(x)
+        y = RNG.normal(size=3)
+        y *= RNG.uniform(0.1, 1.2) / np.linalg.norm(y)
+        U = oracle.regular(p, *y)
+        T = oracle.irregular(p, *x)
+        s = sum((np.conj(full(U, n, m)) * full(T, n, m)).real for n in range(p + 1) for m in range(-n, n + 1))
+        exact = 1.0 / np.linalg.norm(x - y)
+        rx, ry = np.linalg.norm(x), np.linalg.norm(y)
+        bound = (ry / rx) ** (p + 1) / (rx - ry)
+        assert abs(s - exact) <= bound + 1e-14
+
+
+# ------------------------------------------------------------- translations
+
+def _cluster(n, center, radius, seed):
+    g = np.random.default_rng(seed)
+    d = g.normal(size=(n, 3))
+    d *= (radius * g.uniform(0, 1, n) ** (1 / 3) / np.linalg.norm(d, axis=1))[:, None]
+    return center + d, g.uniform(0.5, 1.5, n)
+
+
+def test_m2m_is_exact():
+    """P2M at the parent equals M2M of the children's P2M (no truncation)."""
+    p = 12
+    parent = np.array([0.1, -0.2, 0.3])
+    Mp_direct = np.zeros(oracle.NCOEF(p), complex)
+    Mp_shift = np.zeros(oracle.NCOEF(p), complex)
+    for k in range(4):
+        c = parent + RNG.normal(size=3) * 0.3
+        pos, m = _cluster(30, c, 0.2, k)
+        Mp_direct += oracle.p2m(p, pos, m, parent)
+        Mc = oracle.p2m(p, pos, m, c)
+        Mp_shift += oracle.m2m(p, Mc, c - parent)
+    scale = np.abs(Mp_direct).max()
+    assert np.abs(Mp_direct - Mp_shift).max() <= 1e-13 * scale
+
+
+def test_m2l_l2p_converge_to_direct_potential_and_force():
+    """M2L + L2P reproduces the direct potential and acceleration of a distant
+    cluster, within an error that falls geometrically with p."""
+    za = np.array([3.0, 1.0, -2.0])
+    zb = np.array([0.0, 0.0, 0.0])
+    pos, m = _cluster(40, za, 0.5, 7)
+    x = zb + np.array([0.2, -0.1, 0.15])
+    d = pos - x
+    r = np.linalg.norm(d, axis=1)
+    phi_ref = -(m / r).sum()
+    acc_ref = (m[:, None] * d / r[:, None] ** 3).sum(0)
+    errs = []
+    for p in (2, 4, 6, 8, 10, 12, 14):
+        M = oracle.p2m(p, pos, m, za)
+        F = oracle.m2l(p, M, za - zb)
+        phi, ax, ay, az = oracle.l2p(p, F, x - zb)
+        e = max(abs(phi - phi_ref) / abs(phi_ref), np.linalg.norm(np.array([ax, ay, az]) - acc_ref) / np.linalg.norm(acc_ref))
+        errs.append(e)
+    assert errs[-1] < 1e-9
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+
+
+def test_l2l_is_exact_for_the_truncated_expansion():
+    """Evaluating a local expansion at x equals evaluating its L2L shift."""
+    p = 10
+    pos, m = _cluster(20, np.array([4.0, -3.0, 2.0]), 0.7, 3)
+    za = pos.T @ m / m.sum()
+    zp = np.array([0.1, 0.2, -0.1])
+    zc = zp + np.array([0.15, -0.05, 0.1])
+    F = oracle.m2l(p, oracle.p2m(p, pos, m, za), za - zp)
+    Fc = oracle.l2l(p, F, zc - zp)
+    x = zc + np.array([0.05, 0.07, -0.02])
+    a = np.array(oracle.l2p(p, F, x - zp))
+    b = np.array(oracle.l2p(p, Fc, x - zc))
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+
+
+def test_l2p_acceleration_is_minus_gradient_of_potential():
+    p = 8
+    pos, m = _cluster(25, np.array([2.0, 2.0, 1.0]), 0.5, 11)
+    za = pos.T @ m / m.sum()
+    F = oracle.m2l(p, oracle.p2m(p, pos, m, za), za)
+    x = np.array([0.1, -0.05, 0.08])
+    phi, ax, ay, az = oracle.l2p(p, F, x)
+    h = 1e-5
+    grad = []
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        grad.append((oracle.l2p(p, F, x + e)[0] - oracle.l2p(p, F, x - e)[0]) / (2 * h))
+    assert np.allclose([ax, ay, az], -np.array(grad), rtol=1e-7)
+
+
+def test_multipole_far_field_potential():
+    p = 10
+    pos, m = _cluster(50, np.zeros(3), 1.0, 5)
+    M = oracle.p2m(p, pos, m, np.zeros(3))
+    x = np.array([3.0, -2.5, 4.0])
+    ref = -(m / np.linalg.norm(pos - x, axis=1)).sum()
+    assert abs(oracle.eval_multipole(p, M, np.zeros(3), x) - ref) < 1e-7 * abs(ref)
+
+
+# ------------------------------------------------------------------ solves
+
+def test_single_body_and_two_body_exact():
+    one = oracle.fmm(np.array([[0.3, -0.2, 0.1]]), np.array([1.0]), p=4)
+    assert np.all(one[0] == 0.0) and np.all(one[1] == 0.0)
+    pos = np.array([[0.0, 0.0, 0.0], [1.0, 2.0, 2.0]])
+    m = np.array([2.0, 3.0])
+    acc, pot = oracle.fmm(pos, m, p=4, G=1.5)
+    r = 3.0
+    assert np.allclose(acc[0], 1.5 * 3.0 * pos[1] / r ** 3, rtol=1e-15)
+    assert np.allclose(acc[1], -1.5 * 2.0 * pos[1] / r ** 3, rtol=1e-15)
+    assert np.allclose(pot, [-1.5 * 3.0 / r, -1.5 * 2.0 / r], rtol=1e-15)
+
+
+def test_direct_sum_obeys_newtons_third_law():
+    pos, _, m = ics.plummer(2000, 9)
+    m = ics.kroupa_masses(2000, 10)
+    acc, _ = oracle.direct(pos, m)
+    mom = (m[:, None] * acc).sum(0)
+    assert np.abs(mom).max() < 1e-12 * (m[:, None] * np.abs(acc)).sum()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 63, 64, 65, 200, 512])
+def test_all_direct_when_eps_is_zero(n):
+    """With eps = 0 the MAC never accepts, every interaction is P2P and the
+    solve equals the direct sum to round-off."""
+    pos, _, m = ics.plummer(n, 100 + n)
+    run = oracle.OracleRun(pos, m, p=4, eps=0.0, leaf_size=8)
+    assert run.status == 0 and run.npairs("m2l") == 0
+    acc, pot = run.forces()
+    ad, pd = oracle.direct(pos, m)
+    if n > 1:
+        assert np.abs(acc - ad).max() <= 1e-12 * np.abs(ad).max()
+        assert np.abs(pot - pd).max() <= 1e-12 * np.abs(pd).max()
+    mom = (m[:, None] * acc).sum(0)
+    assert np.abs(mom).max() <= 1e-12 * max(1e-300, (m[:, None] * np.abs(acc)).sum())
+
+
+def test_error_falls_with_p_at_fixed_geometric_mac():
+    """With eps -> infinity the MAC is theta < 1 alone; the error then falls
+    monotonically with the expansion order."""
+    pos, _, m = ics.plummer(3000, 21)
+    ad, _ = oracle.direct(pos, m)
+    rms = []
+    for p in (1, 2, 4, 6, 8, 10, 12):
+        acc, _ = oracle.fmm(pos, m, p=p, eps=1e30, leaf_size=16)
+        rms.append(oracle.error_stats(acc, ad)["rms"])
+    assert all(b < a for a, b in zip(rms, rms[1:])), rms
+
+
+def test_median_error_below_eps_and_falls_with_p():
+    """Sec. 4.1: the median relative force error is always below the
+    tolerance, and at a fixed tolerance it improves as p grows, except where
+    the tolerance is small for the order (the paper's lower-left corner:
+    there low p opens more cells and is more accurate)."""
+    pos, _, m = ics.plummer(8192, 4)
+    ad, _ = oracle.direct(pos, m)
+    for eps in (1e-3, 1e-4, 1e-6):
+        med = []
+        for p in (4, 8, 12):
+            acc, _ = oracle.fmm(pos, m, p=p, eps=eps)
+            med.append(oracle.error_stats(acc, ad)["median"])
+        assert all(v < eps for v in med), (eps, med)
+        if eps >= 1e-4:
+            assert med[2] < med[1] < med[0], (eps, med)
+
+
+def test_plummer_closed_form_radial_profile():
+    """A truncated Plummer sphere has M(<r) = M_P r^3/(r^2+a^2)^{3/2}, so the
+    mean radial acceleration in a shell is -G M(<r)/r^2."""
+    n = 20000
+    pos, _, m = ics.plummer(n, 31, center=False)
+    acc, pot = oracle.fmm(pos, m, p=8, eps=1e-6)
+    a = ics.PLUMMER_A
+    mp = 1.0 / (20.0 ** 3 / (400.0 + a * a) ** 1.5)  # normalisation of the untruncated model
+    r = np.linalg.norm(pos, axis=1)
+    ar = (acc * pos).sum(1) / r
+    edges = np.array([0.2, 0.4, 0.7, 1.0, 1.5, 2.5])
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = (r >= lo) & (r < hi)
+        rr = r[sel]
+        model = -mp * rr ** 3 / (rr * rr + a * a) ** 1.5 / rr ** 2
+        diff = ar[sel] - model
+        # shot noise of N discrete bodies: a few sigma of the shell scatter
+        assert abs(diff.mean()) < 4 * diff.std() / math.sqrt(sel.sum()) + 0.02 * abs(model.mean())
+
+
+def test_plummer_scale_radius_matches_paper():
+    vals = {}
+    with open(os.path.join(GOLDEN, "plummer.txt")) as fh:
+        for line in fh:
+            if line.startswith("#"):
+                continue
+            k, v = line.split()
+            vals[k] = float(v)
+    assert abs(ics.PLUMMER_A - vals["scale_radius_printed"]) < vals["scale_radius_tolerance"]
+    assert abs(-3 * math.pi / (64 * ics.PLUMMER_A) - vals["energy"]) < 1e-15
+
+
+def test_coincident_particles_are_rejected():
+    pos = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    run = oracle.OracleRun(pos, np.ones(3), p=4)
+    assert run.status == -5
+
+
+# --------------------------------------------------------------- tree, lists
+
+@pytest.mark.parametrize("n,leaf", [(1, 64), (65, 64), (4096, 64), (3000, 8)])
+def test_tree_definition(n, leaf):
+    pos, _, m = ics.plummer(n, 40 + n)
+    run = oracle.OracleRun(pos, m, leaf_size=leaf, stage=oracle.STAGE_TREE)
+    t = run.tree()
+    keys = t["keys"].astype(np.uint64)
+    assert np.all(keys[1:] >= keys[:-1])
+    assert np.array_equal(np.sort(t["perm"]), np.arange(n))
+    # equal keys keep input order (stable)
+    eq = keys[1:] == keys[:-1]
+    assert np.all(t["perm"][1:][eq] > t["perm"][:-1][eq])
+    lvl, b, e, nch, fc = t["level"], t["begin"], t["end"], t["nchild"], t["first_child"]
+    assert np.all(np.diff(lvl) >= 0)  # level-major
+    leafcount = np.zeros(n, int)
+    for k in range(run.nnodes):
+        L = lvl[k]
+        shift = np.uint64(3 * (21 - L))
+        pre = keys[b[k]:e[k]] >> shift
+        assert np.all(pre == pre[0])
+        if nch[k] == 0:
+            assert e[k] - b[k] <= leaf or L == 21
+            leafcount[b[k]:e[k]] += 1
+        else:
+            assert e[k] - b[k] > leaf and L < 21
+            kids = range(fc[k], fc[k] + nch[k])
+            assert b[fc[k]] == b[k] and e[fc[k] + nch[k] - 1] == e[k]
+            digits = [int((keys[b[c]] >> np.uint64(3 * (20 - L))) & np.uint64(7)) for c in kids]
+            assert digits == sorted(set(digits))
+            for c in kids:
+                assert t["parent"][c] == k and lvl[c] == L + 1
+    assert np.all(leafcount == 1)
+
+
+@pytest.mark.parametrize("n,eps,p", [(1200, 1e-4, 4), (1500, 1e-7, 8), (900, 1e30, 3)])
+def test_lists_cover_every_particle_pair_exactly_once(n, eps, p):
+    """Every ordered pair (i, j), i != j, is handled exactly once: by one M2L
+    pair or one P2P pair (the dual-tree walk of Sec. 2.1). Accepted pairs are
+    well separated, theta = (r_A + r_B)/r < 1."""
+    pos, _, m = ics.plummer(n, 77)
+    run = oracle.OracleRun(pos, m, p=p, eps=eps, leaf_size=16, stage=oracle.STAGE_LISTS)
+    t, g = run.tree(), run.geometry()
+    cover = np.zeros((n, n), int)
+    for which in ("m2l", "p2p"):
+        for a, b in run.pairs(which):
+            ia = np.arange(t["begin"][a], t["end"][a])
+            ib = np.arange(t["begin"][b], t["end"][b])
+            if a == b:
+                cover[np.ix_(ia, ia)] += 1
+            else:
+                cover[np.ix_(ia, ib)] += 1
+                cover[np.ix_(ib, ia)] += 1
+            if which == "m2l":
+                rr = np.linalg.norm(g["z"][a] - g["z"][b])
+                assert g["r"][a] + g["r"][b] < rr
+    off = ~np.eye(n, dtype=bool)
+    assert np.all(cover[off] == 1)
+
+
+def test_cell_geometry_definitions():
+    pos, _, _ = ics.plummer(3000, 8)
+    m = ics.kroupa_masses(3000, 9)
+    run = oracle.OracleRun(pos, m, leaf_size=32, stage=oracle.STAGE_F)
+    t, g = run.tree(), run.geometry()
+    ps = pos[t["perm"]]
+    ms = m[t["perm"]]
+    for k in range(run.nnodes):
+        sl = slice(t["begin"][k], t["end"][k])
+        com = (ms[sl, None] * ps[sl]).sum(0) / ms[sl].sum()
+        assert np.allclose(g["z"][k], com, rtol=1e-12, atol=1e-13)
+        assert math.isclose(g["M"][k], ms[sl].sum(), rel_tol=1e-13)
+        rmax = np.linalg.norm(ps[sl] - g["z"][k], axis=1).max()
+        assert g["r"][k] >= rmax * (1 - 1e-12)
+        if t["nchild"][k] == 0:
+            assert math.isclose(g["r"][k], rmax, rel_tol=1e-12)
+
+
+def test_degree_norms_are_rotation_invariant():
+    """P_n of Sec. 2.3 depends only on the multipole's shape: rotating the
+    particles about the centre leaves it unchanged."""
+    p = 10
+    pos, m = _cluster(40, np.zeros(3), 1.0, 2)
+    th = 0.7
+    rot = np.array([[math.cos(th), 0, math.sin(th)], [0, 1, 0], [-math.sin(th), 0, math.cos(th)]])
+    rot = rot @ np.array([[math.cos(1.1), -math.sin(1.1), 0], [math.sin(1.1), math.cos(1.1), 0], [0, 0, 1]])
+
+    def norms(M):
+        return np.array([math.sqrt(sum(math.factorial(n - mm) * math.factorial(n + mm) * abs(full(M, n, mm)) ** 2
+                                       for mm in range(-n, n + 1))) for n in range(p + 1)])
+    a = norms(oracle.p2m(p, pos, m, np.zeros(3)))
+    b = norms(oracle.p2m(p, pos @ rot.T, m, np.zeros(3)))
+    assert np.allclose(a, b, rtol=1e-12)
+
+
+def test_scalar_force_estimate_is_exact_when_all_near():
+    """With one leaf (N <= leaf size) the estimate f_i is the exact scalar
+    force sum_j m_j/|x_i - x_j|^2 in FP32 (Sec. 2.3)."""
+    pos, _, m = ics.plummer(50, 3)
+    run = oracle.OracleRun(pos, m, leaf_size=64, stage=oracle.STAGE_F)
+    f = run.geometry()["f"]
+    ps, ms = pos[run.tree()["perm"]], m[run.tree()["perm"]]
+    d = ps[:, None, :] - ps[None, :, :]
+    r2 = (d * d).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    exact = (ms[None, :] / r2).sum(1)
+    assert np.allclose(f, exact, rtol=2e-5)
+
+
+def test_scalar_force_estimate_tracks_exact():
+    pos, _, m = ics.plummer(4096, 6)
+    run = oracle.OracleRun(pos, m, leaf_size=64, stage=oracle.STAGE_F)
+    f = run.geometry()["f"].astype(np.float64)
+    ps, ms = pos[run.tree()["perm"]], m[run.tree()["perm"]]
+    exact = np.zeros(len(ms))
+    for i in range(0, len(ms), 512):
+        d = ps[i:i + 512, None, :] - ps[None, :, :]
+        r2 = (d * d).sum(-1)
+        r2[r2 == 0] = np.inf
+        exact[i:i + 512] = (ms[None, :] / r2).sum(1)
+    # theta < 1 lets a monopole stand for a cell seen at up to ~90 degrees, so
+    # the estimate is rough; a dropped far term or a wrong power of r would
+    # shift the whole distribution by far more than these bounds
+    rel = (f - exact) / exact
+    assert np.median(np.abs(rel)) < 0.15
+    lo, hi = np.percentile(rel, [1, 99])
+    assert -0.5 < lo and hi < 1.0 and rel.max() < 2.0
+
+
+def test_mac_error_estimate_bounds_the_true_m2l_error():
+    """E_{A->B} M_A / r^2 (Sec. 2.3) estimates the force error of the
+    truncated M2L from A at any particle of B. On the pairs a solve accepts
+    it must cover the true error, and not by a wide margin."""
+    n, p = 3000, 6
+    pos, _, m = ics.plummer(n, 55)
+    run = oracle.OracleRun(pos, m, p=p, eps=1e-5, leaf_size=16, stage=oracle.STAGE_LISTS)
+    t, g = run.tree(), run.geometry()
+    mult = run.multipoles()
+    ps, ms = pos[t["perm"]], m[t["perm"]]
+    pairs = run.pairs("m2l")
+    sel = np.random.default_rng(1).choice(len(pairs), size=min(150, len(pairs)), replace=False)
+    worst = 0.0
+    ratios = []
+    for a, b in pairs[sel]:
+        v = run.mac_values(a, b)
+        assert v[4] == 1.0 and v[0] < v[2] and v[1] < v[3]
+        for src, dst, lhs in ((a, b, v[0]), (b, a, v[1])):
+            F = oracle.m2l(p, mult[src], g["z"][src] - g["z"][dst])
+            js = np.arange(t["begin"][src], t["end"][src])
+            for i in range(t["begin"][dst], t["end"][dst]):
+                _, ax, ay, az = oracle.l2p(p, F, ps[i] - g["z"][dst])
+                d = ps[js] - ps[i]
+                rr = np.linalg.norm(d, axis=1)
+                ref = (ms[js, None] * d / rr[:, None] ** 3).sum(0)
+                err = np.linalg.norm(np.array([ax, ay, az]) - ref)
+                floor = 1e-12 * np.linalg.norm(ref)  # round-off of the reference sum
+                if lhs > 1e3 * floor:
+                    worst = max(worst, err / lhs)
+                    ratios.append(err / lhs)
+    q90, q99 = np.percentile(ratios, [90, 99])
+    # an estimate, not a strict bound: it covers 99% of particles and is
+    # never off by more than 2x; and it is not loose by orders of magnitude
+    assert q99 <= 1.0 and worst <= 2.0 and q90 > 0.02, (q90, q99, worst)
