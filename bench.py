@@ -1,0 +1,346 @@
+"""Benchmark: particles/s of one FMM force solve at N = 2^20.
+
+Workload (Mukherjee et al. 2021 method; synthetic inputs standing in for the
+paper's MCLUSTER Plummer models): Plummer sphere, N = 1,048,576, Henon units,
+seed 2, Kroupa IMF masses (seed 3) renormalised to M = 1; mixed precision,
+expansion order p and MAC tolerance eps chosen so that the RMS relative
+acceleration error against the FP64 direct sum is <= 1e-6; leaf size 64. The
+same solve in FP64 mode runs beside it for the mixed-vs-FP64 comparison.
+
+One step = one complete force solve (tree build included) on inputs already
+resident in HBM. The inputs (32 MB) fit in L2, so L2 is flushed before every
+timed solve by writing a 512 MB buffer; the flush is outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbfmm|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_BODIES = 1 << 20
+P_DEFAULT = 10
+EPS_DEFAULT = 1e-7
+LEAF = 64
+SAMPLE_N = 1 << 16          # bounded CPU sample for the oracle timings
+ERR_SAMPLE = 4096           # bodies whose force error is measured per precision
+METRIC = "particles/s per FMM force solve at N=1e6: mixed vs FP64 at RMS err<=1e-6"
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
+    return N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def m2l_flops(p):
+    """Algorithmic flops of one directed rotation-accelerated M2L at order p:
+    four z-rotations (complex products on every m >= 1 coefficient), four
+    swaps (one FMA per non-zero of the cosine and sine blocks), the
+    z-translation (one FMA per (n, k, m) term and real/imag part) and the
+    accumulation of the (p+1)^2 result."""
+    rot = sum(6 + 6 * (p - m + 1) for m in range(1, p + 1))
+    swap = 0
+    for n in range(1, p + 1):
+        swap += sum(1 for m in range(n + 1) for j in range(n + 1) if (j + m + n) % 2 == 0)
+        swap += sum(1 for m in range(1, n + 1) for j in range(1, n + 1) if (j + m + n) % 2 == 1)
+    trans = 0
+    for m in range(p + 1):
+        parts = 2 if m else 1
+        trans += parts * (p - m + 1)                     # signs and powers of u
+        for n in range(m, p + 1):
+            trans += parts * 2 * max(0, p - n - m + 1) + parts  # FMAs + final scale
+    return 4 * rot + 4 * 2 * swap + 2 * trans + (p + 1) ** 2
+
+
+P2P_FLOPS = 20  # per directed body-body interaction (the usual gravity-kernel count)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload():
+    import ics
+    pos, m = ics.config_inputs("kroupa1m")
+    return pos, m
+
+
+def cpu_sample(p, eps):
+    """The oracle FMM on a bounded sample of the same workload."""
+    import ics
+    import oracle
+    pos, _, _ = ics.plummer(SAMPLE_N, 2)
+    m = ics.kroupa_masses(SAMPLE_N, 3)
+    t0 = time.perf_counter()
+    oracle.fmm(pos, m, p=p, eps=eps, leaf_size=LEAF)
+    dt = time.perf_counter() - t0
+    return SAMPLE_N / dt, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p, eps = args.p, args.eps
+    for _ in range(args.warmup):
+        cpu_sample(p, eps)
+    vals, times = [], []
+    cores = 1
+    for _ in range(args.steps):
+        v, dt, cores = cpu_sample(p, eps)
+        vals.append(v)
+        times.append(dt)
+    value = SAMPLE_N * len(times) / sum(times)
+    sample = f"oracle FMM (FP64, OpenMP) on a Plummer/Kroupa sample of N={SAMPLE_N}, p={p}, eps={eps}, per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"plummer_kroupa_n{SAMPLE_N}_sample", "p": p, "eps": eps,
+                                         "leaf_size": LEAF},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbfmm", choices=["gbfmm", "reference"])
+    ap.add_argument("--p", type=int, default=P_DEFAULT)
+    ap.add_argument("--eps", type=float, default=EPS_DEFAULT)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    import paper_2012_02207_gb300 as gb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = dist_mod
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    pos, m = workload()
+    n = len(m)
+    cols = [torch.tensor(np.ascontiguousarray(pos[:, d]), device=dev) for d in range(3)]
+    mt = torch.tensor(m, device=dev)
+    outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed_solves(solver, steps, warmup):
+        for _ in range(warmup):
+            solver.solve(*cols, mt, out=outs)
+        barrier()
+        times, stats = [], []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.solve(*cols, mt, out=outs)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            stats.append(solver.stats())
+        barrier()
+        return times, stats
+
+    mixed = gb.FMM(p=args.p, eps=args.eps, leaf_size=LEAF, precision="mixed")
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        times, stats = timed_solves(mixed, args.steps, args.warmup)
+        wall = time.perf_counter() - wall0
+    clocks = clk.summary()
+    ms = sum(times) / len(times)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * world / (ms * 1e-3)
+
+    # accuracy of this exact run on a fixed sample of bodies, FP64 direct sum on the GPU
+    rng = np.random.default_rng(0)
+    sample = torch.tensor(rng.choice(n, ERR_SAMPLE, replace=False), device=dev)
+    dax, day, daz, _ = mixed.direct(*cols, mt, targets=sample)
+    dref = torch.stack([dax, day, daz], 1)
+
+    def rms_err(ax, ay, az):
+        a = torch.stack([ax, ay, az], 1)[sample]
+        d = torch.linalg.norm(a - dref, dim=1) / torch.linalg.norm(dref, dim=1)
+        return float(torch.sqrt((d * d).mean()).item()), float(d.median().item())
+
+    mixed.solve(*cols, mt, out=outs)
+    err_mixed, med_mixed = rms_err(*outs[:3])
+
+    # FP64 mode on the same inputs (slow; a few steps)
+    fp64 = gb.FMM(p=args.p, eps=args.eps, leaf_size=LEAF, precision="fp64")
+    t64, s64 = timed_solves(fp64, args.fp64_steps, 1)
+    ms64 = sum(t64) / len(t64)
+    err64, med64 = rms_err(*outs[:3])
+    value64 = n / (ms64 * 1e-3)
+
+    # end to end through the host entry point (pinned host buffers)
+    hin = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(4)]
+    for h, c in zip(hin, cols + [mt]):
+        h.copy_(c.cpu())
+    hout = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(4)]
+    L = gb.lib()
+    e2e_times = []
+    for i in range(args.warmup + max(3, args.steps // 2)):
+        barrier()
+        t0 = time.perf_counter()
+        rc = L.fmm_solve_host(mixed._h, n, *[h.data_ptr() for h in hin], *[o.data_ptr() for o in hout],
+                              stream.cuda_stream)
+        t1 = time.perf_counter()
+        if rc != 0:
+            raise gb.FmmError(rc, L.fmm_last_error(mixed._h).decode())
+        if i >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e_value = n * world / (sum(e2e_times) / len(e2e_times))
+
+    # roofline of the dominant phase (FP32 ALU bound in mixed mode)
+    st = stats[-1]
+    p = args.p
+    phase_ms = {"m2l": statistics.median(s["ms_m2l"] for s in stats),
+                "leaf_p2p_l2p": statistics.median(s["ms_leaf"] for s in stats)}
+    flops = {"m2l": 2 * st["n_m2l"] * m2l_flops(p), "leaf_p2p_l2p": P2P_FLOPS * st["p2p_interactions"]}
+    dom = max(phase_ms, key=phase_ms.get)
+    sm_for_peak = load_peaks().get("sm_max_mhz", 2070.0)
+    peak = fp32_peak_tflops(sm_for_peak)
+    achieved = flops[dom] / (phase_ms[dom] * 1e-3) / 1e12
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt, cores = cpu_sample(p, args.eps)
+        cpu = {"value": v, "unit": "particles/s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle FMM (FP64, OpenMP) on one Plummer/Kroupa solve of N={SAMPLE_N}, "
+                         f"p={p}, eps={args.eps}: {dt:.2f} s"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "plummer_kroupa_n1048576_mixed", "n": n, "p": p, "eps": args.eps,
+                       "leaf_size": LEAF, "precision": "mixed", "l2": "flushed (512 MB write) before each step",
+                       "parallelism": f"replicas{world}"},
+            "fp64": {"value": value64, "ms_per_step": ms64, "steps": args.fp64_steps, "rms_err": err64,
+                     "median_err": med64},
+            "speedup_vs_fp64": value / value64,
+            "rms_err": err_mixed, "median_err": med_mixed, "err_sample": ERR_SAMPLE,
+            "phases_ms": {k: statistics.median(s[k] for s in stats) for k in
+                          ("ms_tree", "ms_upward", "ms_estimate", "ms_walk", "ms_m2l", "ms_downward", "ms_leaf",
+                           "ms_total")},
+            "counts": {k: st[k] for k in ("nnodes", "nlevels", "n_far", "n_near", "n_m2l", "n_p2p",
+                                          "p2p_interactions", "walk_iters")},
+            "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_note": f"FP32 lanes x 2 x {sm_for_peak:.0f} MHz (sm_max_mhz of measured peaks)"},
+            "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": 32 * n,
+                    "d2h_bytes_per_step": 32 * n},
+            "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+            "clocks": clocks, "wall_s_timed": wall,
+            "cpu_baseline": cpu,
+        }), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

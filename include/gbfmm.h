@@ -1,0 +1,155 @@
+/*
+ * gbfmm: GPU fast multipole force solve for collisional star systems.
+ *
+ * The method is that of Mukherjee, Zhu, Trac & Rodriguez (2021), "Fast
+ * Multipole Methods for N-body Simulations of Collisional Star Systems",
+ * Section 2: an octree, multipole moments in solid spherical harmonics
+ * (Sec. 2.2, Eq. moments), an error-controlled multipole-acceptance
+ * criterion built on a scalar-force estimate (Sec. 2.3), a dual-tree walk
+ * (Sec. 2.1) emitting M2L and P2P interaction lists, the rotation-accelerated
+ * M2L (Sec. 2.4), L2L/L2P, and direct summation for the near field.
+ *
+ * Problem (Sec. 2.3, Sec. 3.1.1): given N bodies with positions x_i and masses
+ * m_i, compute a_i = G sum_{j != i} m_j (x_j - x_i)/|x_j - x_i|^3 and
+ * phi_i = -G sum_{j != i} m_j/|x_j - x_i|, approximately, with the expansion
+ * order p and the tolerance eps of the MAC. No softening.
+ *
+ * Conventions for every call:
+ *  - All array arguments of fmm_solve/fmm_solve_batch are DEVICE pointers
+ *    (cudaMalloc'd or from a tensor on the current device), FP64, one value
+ *    per body, in the caller's order; outputs are written in the same order.
+ *    The caller owns them; the library never frees or keeps them.
+ *  - The library owns its workspace inside the context, grows it on demand
+ *    and frees it in fmm_destroy.
+ *  - All GPU work is issued on the caller's stream (NULL = legacy default).
+ *    Calls return when the outputs are complete on that stream's timeline:
+ *    the library synchronises the stream internally (it reads back tree and
+ *    list sizes).
+ *  - Every call returns an fmm_status; fmm_last_error() gives a message. On
+ *    error the outputs are unspecified and the context stays usable. The
+ *    library never aborts and never traps on the device.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef GBFMM_H
+#define GBFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_ARG = -1,        /* invalid argument (n < 0, p outside [1, 30], eps < 0, ...) */
+    FMM_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+    FMM_ERR_OOM = -3,        /* device allocation failed */
+    FMM_ERR_NONFINITE = -4,  /* a position or mass is NaN or infinite, or a mass is <= 0 */
+    FMM_ERR_COINCIDENT = -5, /* two bodies share exactly the same position */
+    FMM_ERR_CAPACITY = -6,   /* an internal list outgrew its capacity after one regrow */
+    FMM_ERR_TIMEOUT = -7     /* a bounded device-side wait ran out */
+} fmm_status;
+
+typedef enum {
+    FMM_PRECISION_FP64 = 0,  /* every expansion and pair sum in FP64 */
+    FMM_PRECISION_MIXED = 1  /* M2L, L2L, L2P and P2P in FP32 on scaled / cell-relative
+                                values with compensated or FP64 accumulation; tree,
+                                multipoles for the MAC and the walk in FP64 */
+} fmm_precision;
+
+typedef struct {
+    int p;                 /* expansion order, 1..30 (swap matrices are tabulated to 30, Sec. 2.4) */
+    double eps;            /* MAC tolerance epsilon of Sec. 2.3, >= 0 (0: never accept, all P2P) */
+    int leaf_size;         /* split a cell while it holds more than leaf_size bodies, 1..256 */
+    int precision;         /* fmm_precision */
+    double G;              /* gravitational constant (Henon units: 1) */
+    unsigned flags;        /* reserved, 0 */
+    unsigned fault_inject; /* test hook, 0 in production: bit 0 forces tiny list capacities
+                              so the capacity-regrow path runs */
+} fmm_config;
+
+typedef struct {
+    int64_t n;              /* bodies in the last solve */
+    int32_t nnodes, nleaves, nlevels;
+    int64_t n_far, n_near;  /* pair counts of the theta < 1 walk (scalar-force estimate) */
+    int64_t n_m2l, n_p2p;   /* pair counts of the eps walk (unordered pairs, self pairs in P2P) */
+    int64_t p2p_interactions; /* directed body-body interactions evaluated */
+    double ms_tree, ms_upward, ms_estimate, ms_walk, ms_m2l, ms_downward, ms_leaf, ms_total;
+    int32_t walk_iters, regrows;
+    int64_t kernel_launches;  /* kernels the library launched in the last solve */
+} fmm_stats;
+
+typedef struct fmm_ctx fmm_ctx;
+
+/* Create a context for the current CUDA device. Validates cfg (FMM_ERR_ARG)
+ * and uploads the swap matrices and coefficient tables. *out is NULL on error. */
+int fmm_create(fmm_ctx** out, const fmm_config* cfg);
+
+/* Release every device and host resource of the context. NULL is allowed. */
+void fmm_destroy(fmm_ctx* ctx);
+
+/* One force solve (Sec. 2.1, Fig. 1): tree, P2M/M2M, scalar-force estimate,
+ * error-controlled walk, M2L/L2L/L2P and P2P. x, y, z, m: n device FP64
+ * values each; ax, ay, az, pot: n device FP64 outputs (pot may be NULL).
+ * n = 0 is a no-op. */
+int fmm_solve(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
+              const double* m, double* ax, double* ay, double* az, double* pot, void* cuda_stream);
+
+/* The same solve from HOST buffers: copies the inputs in, solves, copies the
+ * outputs back, all on cuda_stream; returns when the host outputs are final.
+ * Host buffers may be pageable or pinned. */
+int fmm_solve_host(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
+                   const double* m, double* ax, double* ay, double* az, double* pot, void* cuda_stream);
+
+/* Independent solves of nclusters clusters stored back to back: cluster c
+ * holds bodies [offsets[c], offsets[c+1]) (offsets: HOST array of
+ * nclusters + 1 values, offsets[0] = 0). Bodies of different clusters do
+ * not interact. Device arrays as in fmm_solve. */
+int fmm_solve_batch(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, const double* x,
+                    const double* y, const double* z, const double* m, double* ax, double* ay,
+                    double* az, double* pot, void* cuda_stream);
+
+/* Plain FP64 O(N * ntargets) direct sum at the given target indices (a
+ * device int64 array, or NULL for all n bodies): the exact quantity the FMM
+ * approximates (Sec. 3.1.1), used to measure force errors. */
+int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
+               const double* m, int64_t ntargets, const int64_t* targets, double* ax, double* ay,
+               double* az, double* pot, void* cuda_stream);
+
+/* Statistics of the last solve. */
+int fmm_get_stats(const fmm_ctx* ctx, fmm_stats* out);
+
+/* Export the octree of the last solve to HOST buffers, for parity tests.
+ * keys/perm: n values (Morton keys in sorted order; perm[i] = caller index of
+ * the i-th sorted body). Node arrays: nnodes values each, nodes numbered level
+ * by level and in key order within a level. Any pointer may be NULL. */
+int fmm_export_tree(const fmm_ctx* ctx, uint64_t* keys, int64_t* perm, int32_t* level,
+                    int32_t* begin, int32_t* end, int32_t* parent, int32_t* first_child,
+                    int32_t* nchild);
+
+/* Export per-node geometry of the last solve to HOST buffers (any may be NULL):
+ * M (nnodes), z (3*nnodes, centre of mass), r (nnodes, cell size), P
+ * (nnodes*(p+1), degree norms of Sec. 2.3), fmin (nnodes, minimum scalar-force
+ * estimate), f (n, per sorted body). */
+int fmm_export_geometry(const fmm_ctx* ctx, double* M, double* z, double* r, double* P,
+                        float* fmin, float* f);
+
+/* Export an interaction list of the last solve to HOST memory: which = 0 far
+ * pairs and 1 near pairs of the theta < 1 walk, 2 M2L pairs and 3 P2P pairs of
+ * the eps walk; pairs: 2*count int32 (A, B), in the library's own order.
+ * *count receives the number of pairs; pairs may be NULL to query it. */
+int fmm_export_pairs(const fmm_ctx* ctx, int which, int64_t* count, int32_t* pairs);
+
+/* Export the swap-matrix table (degrees 0..30, layout of the generator: cosine
+ * blocks then sine blocks) to HOST memory; ncos/nsin receive the counts. */
+int fmm_export_swap(int64_t* ncos, int64_t* nsin, double* cos_blocks, double* sin_blocks);
+
+/* Message of the last error on this context (or of the last failed
+ * fmm_create when ctx is NULL). Never NULL. */
+const char* fmm_last_error(const fmm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBFMM_H */

@@ -1,0 +1,659 @@
+// C ABI of the gbfmm library: context, workspace and the solve pipeline.
+//
+// One solve (Sec. 2.1, Fig. 1 of Mukherjee et al. 2021):
+//   bounding cube -> Morton keys -> radix sort -> octree -> cell geometry
+//   -> P2M / M2M (FP64 hat multipoles) and degree norms P_n
+//   -> theta < 1 walk -> scalar-force estimate f (Sec. 2.3)
+//   -> error-controlled walk -> M2L (rotation, Sec. 2.4) -> L2L
+//   -> per leaf: L2P + P2P, written to the caller's order.
+// The host reads back three small things (node count, level starts, list
+// sizes); everything else stays on the device.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gbfmm_internal.cuh"
+#include "swap_table.inc"
+
+namespace gbfmm {
+namespace {
+thread_local int64_t g_launches = 0;
+}
+void note_launch() { ++g_launches; }
+bool m2l32_supported(int p);
+void tree_build_count(TreeBuffers& b, int* sorted_in_1, cudaStream_t st);
+void tree_build_emit(TreeBuffers& b, cudaStream_t st);
+}  // namespace gbfmm
+
+using namespace gbfmm;
+
+namespace {
+
+std::string g_create_error = "no error";
+
+struct Buf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+template <typename T>
+T* as(Buf& b) { return reinterpret_cast<T*>(b.ptr); }
+
+}  // namespace
+
+struct fmm_ctx {
+    fmm_config cfg{};
+    int device = 0;
+    std::string err = "no error";
+    fmm_stats stats{};
+    HostTables ht{};
+    DevTables tb{};
+    Buf tables;
+    DevScalars* ds = nullptr;
+    DevScalars* h_ds = nullptr;  // pinned
+    cudaEvent_t ev[10] = {};
+    // per-body
+    Buf k0, k1, v0, v1, hist, xs, ys, zs, ms, xf, prel, lcp, win, hi, chunk, f, bbox;
+    // per-node
+    Buf level, begin, end, parent, first_child, nchild, M, S, zc, r, Pk, mult, mult32, loc, loc32,
+        fmin, fscratch;
+    // walk and lists
+    Buf front0, front1, lists[4], dkeys[4], dalt, doff[4], dcount;
+    int64_t front_cap = 0, list_cap[4] = {0, 0, 0, 0};
+    // host staging for fmm_solve_host
+    Buf hin[4], hout[4];
+    // last solve
+    int64_t n = 0;
+    int nnodes = 0, nlevels = 0, nb = 1, sorted_in_1 = 0;
+    int h_level_start[kMaxLevel + 3] = {};
+    int64_t npairs[4] = {0, 0, 0, 0}, ndirected[4] = {0, 0, 0, 0};
+    int dk_in_alt[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+int fail(fmm_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, FMM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int ensure(fmm_ctx* ctx, Buf& b, size_t bytes) {
+    if (b.bytes >= bytes) return FMM_OK;
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    size_t want = bytes + bytes / 4 + 256;
+    if (cudaMalloc(&b.ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        b.ptr = nullptr;
+        return fail(ctx, FMM_ERR_OOM, "device allocation of " + std::to_string(want) + " bytes failed");
+    }
+    b.bytes = want;
+    return FMM_OK;
+}
+
+void release(Buf& b) {
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+void build_host_tables(HostTables& h) {
+    h.fact[0] = 1.0;
+    for (int k = 1; k < 2 * kMaxP + 4; ++k) h.fact[k] = h.fact[k - 1] * (double)k;
+    for (int n = 0; n < kMaxP + 2; ++n)
+        for (int m = 0; m < kMaxP + 2; ++m) {
+            if (m <= n) {
+                h.w[n][m] = std::sqrt(h.fact[n + m] * h.fact[n - m]);
+                h.iw[n][m] = 1.0 / h.w[n][m];
+            } else {
+                h.w[n][m] = 0.0;
+                h.iw[n][m] = 0.0;
+            }
+        }
+    for (int n = 0; n <= kMaxP; ++n) {
+        h.binom[n][0] = 1.0;
+        h.binom[n][n] = 1.0;
+        for (int k = 1; k < n; ++k) h.binom[n][k] = h.binom[n - 1][k - 1] + h.binom[n - 1][k];
+        for (int m = 0; m <= kMaxP; ++m) {
+            if (m < n - 1 || (m == n - 1 && n >= 1)) {
+                const double a = (double)(n + m), b = (double)(n - m);
+                h.rec_a[n][m] = (2.0 * n - 1.0) / std::sqrt(a * b);
+                h.rec_b[n][m] = (n - m >= 2) ? std::sqrt((a - 1.0) * (b - 1.0) / (a * b)) : 0.0;
+            } else {
+                h.rec_a[n][m] = 0.0;
+                h.rec_b[n][m] = 0.0;
+            }
+        }
+        h.diag[n] = n == 0 ? 1.0 : std::sqrt((2.0 * n - 1.0) / (2.0 * n));
+        h.sub[n] = std::sqrt(2.0 * n + 1.0);
+    }
+}
+
+int bit_length(int64_t v) {
+    int b = 0;
+    while (v > 0) { ++b; v >>= 1; }
+    return b;
+}
+
+TreeView view(fmm_ctx* ctx) {
+    TreeView t;
+    t.n = (int)ctx->n;
+    t.nnodes = ctx->nnodes;
+    t.nlevels = ctx->nlevels;
+    t.leaf_size = ctx->cfg.leaf_size;
+    t.level = as<int>(ctx->level);
+    t.begin = as<int>(ctx->begin);
+    t.end = as<int>(ctx->end);
+    t.parent = as<int>(ctx->parent);
+    t.first_child = as<int>(ctx->first_child);
+    t.nchild = as<int>(ctx->nchild);
+    return t;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+// directed, sorted, CSR-indexed form of pair list `which`
+int build_directed(fmm_ctx* ctx, int which, cudaStream_t st) {
+    const int64_t np = ctx->npairs[which];
+    const size_t keys_bytes = sizeof(uint64_t) * (size_t)(2 * np + 1);
+    int rc;
+    if ((rc = ensure(ctx, ctx->dkeys[which], keys_bytes)) != FMM_OK) return rc;
+    if ((rc = ensure(ctx, ctx->dalt, keys_bytes)) != FMM_OK) return rc;
+    if ((rc = ensure(ctx, ctx->doff[which], sizeof(uint32_t) * (size_t)(ctx->nnodes + 2))) != FMM_OK) return rc;
+    if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(2 * np + 1))) != FMM_OK) return rc;
+    CK(cudaMemsetAsync(ctx->dcount.ptr, 0, sizeof(unsigned long long), st));
+    pairs_to_directed(as<int2>(ctx->lists[which]), np, ctx->nb, as<uint64_t>(ctx->dkeys[which]),
+                      as<unsigned long long>(ctx->dcount), st);
+    const int in1 = radix_sort(as<uint64_t>(ctx->dkeys[which]), nullptr, as<uint64_t>(ctx->dalt), nullptr,
+                               2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st);
+    if (in1) {
+        CK(cudaMemcpyAsync(ctx->dkeys[which].ptr, ctx->dalt.ptr, sizeof(uint64_t) * (size_t)(2 * np),
+                           cudaMemcpyDeviceToDevice, st));
+    }
+    unsigned long long nself = 0;
+    CK(cudaMemcpyAsync(&nself, ctx->dcount.ptr, sizeof(nself), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->ndirected[which] = 2 * np - (int64_t)nself;
+    directed_offsets(as<uint64_t>(ctx->dkeys[which]), ctx->ndirected[which], ctx->nb, ctx->nnodes,
+                     as<uint32_t>(ctx->doff[which]), st);
+    return FMM_OK;
+}
+
+int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
+    TreeView t = view(ctx);
+    const int p = ctx->cfg.p;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        int rc;
+        if ((rc = ensure(ctx, ctx->front0, sizeof(int2) * (size_t)ctx->front_cap)) != FMM_OK) return rc;
+        if ((rc = ensure(ctx, ctx->front1, sizeof(int2) * (size_t)ctx->front_cap)) != FMM_OK) return rc;
+        for (int l = 2 * mode; l < 2 * mode + 2; ++l)
+            if ((rc = ensure(ctx, ctx->lists[l], sizeof(int2) * (size_t)ctx->list_cap[l])) != FMM_OK) return rc;
+        WalkBuffers wb;
+        wb.front0 = as<int2>(ctx->front0);
+        wb.front1 = as<int2>(ctx->front1);
+        wb.front_cap = ctx->front_cap;
+        for (int l = 0; l < 4; ++l) {
+            wb.out[l] = as<int2>(ctx->lists[l]);
+            wb.out_cap[l] = ctx->list_cap[l];
+        }
+        // the binomial row C(p, k) follows the sub-diagonal table (see fmm_create)
+        const double* binom_row = ctx->tb.sub + (kMaxP + 1);
+        CK(cudaMemsetAsync(&ctx->ds->err, 0, sizeof(unsigned), st));
+        const int it = dual_tree_walk(mode, t, as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->Pk),
+                                      as<float>(ctx->fmin), p, ctx->cfg.eps, binom_row, wb, ctx->ds,
+                                      ctx->h_ds, st);
+        if (it == FMM_ERR_CAPACITY) {
+            ctx->front_cap *= 4;
+            ctx->list_cap[2 * mode] *= 4;
+            ctx->list_cap[2 * mode + 1] *= 4;
+            ctx->stats.regrows++;
+            continue;
+        }
+        if (it < 0) return fail(ctx, it, "dual-tree walk failed");
+        ctx->stats.walk_iters += it;
+        unsigned long long cnt[4];
+        CK(cudaMemcpyAsync(cnt, ctx->ds->list_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        bool over = false;
+        for (int l = 2 * mode; l < 2 * mode + 2; ++l) {
+            if ((int64_t)cnt[l] > ctx->list_cap[l]) over = true;
+            ctx->npairs[l] = (int64_t)cnt[l];
+        }
+        if (over) {
+            for (int l = 2 * mode; l < 2 * mode + 2; ++l)
+                while (ctx->list_cap[l] < ctx->npairs[l]) ctx->list_cap[l] *= 2;
+            ctx->stats.regrows++;
+            continue;
+        }
+        return FMM_OK;
+    }
+    return fail(ctx, FMM_ERR_CAPACITY, "interaction lists outgrew their capacity");
+}
+
+int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
+                 const double* m, double* ax, double* ay, double* az, double* pot, cudaStream_t st) {
+    const int p = ctx->cfg.p;
+    const bool mixed = ctx->cfg.precision == FMM_PRECISION_MIXED;
+    std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+    g_launches = 0;
+    ctx->stats.n = n;
+    ctx->n = n;
+    if (n == 0) return FMM_OK;
+    int rc;
+    // ---- per-body workspace
+    const size_t N = (size_t)n;
+    const int nchunks = tree_nchunks(n);
+    if ((rc = ensure(ctx, ctx->k0, 8 * N)) || (rc = ensure(ctx, ctx->k1, 8 * N)) ||
+        (rc = ensure(ctx, ctx->v0, 4 * N)) || (rc = ensure(ctx, ctx->v1, 4 * N)) ||
+        (rc = ensure(ctx, ctx->hist, 4 * radix_hist_words(n))) || (rc = ensure(ctx, ctx->xs, 8 * N)) ||
+        (rc = ensure(ctx, ctx->ys, 8 * N)) || (rc = ensure(ctx, ctx->zs, 8 * N)) ||
+        (rc = ensure(ctx, ctx->ms, 8 * N)) || (rc = ensure(ctx, ctx->xf, 16 * N)) ||
+        (rc = ensure(ctx, ctx->prel, 16 * N)) || (rc = ensure(ctx, ctx->lcp, N)) ||
+        (rc = ensure(ctx, ctx->win, N)) || (rc = ensure(ctx, ctx->hi, N)) ||
+        (rc = ensure(ctx, ctx->chunk, 4 * ((size_t)(kMaxLevel + 1) * nchunks + 2))) ||
+        (rc = ensure(ctx, ctx->f, 4 * N)) || (rc = ensure(ctx, ctx->bbox, 8 * 6 * 304)))
+        return rc;
+    CK(cudaEventRecord(ctx->ev[0], st));
+    CK(cudaMemsetAsync(&ctx->ds->err, 0, sizeof(unsigned), st));
+    TreeBuffers tb{};
+    tb.x = x; tb.y = y; tb.z = z; tb.m = m; tb.n = n; tb.leaf_size = ctx->cfg.leaf_size;
+    tb.bbox_part = as<double>(ctx->bbox);
+    tb.k0 = as<uint64_t>(ctx->k0); tb.k1 = as<uint64_t>(ctx->k1);
+    tb.v0 = as<uint32_t>(ctx->v0); tb.v1 = as<uint32_t>(ctx->v1);
+    tb.hist = as<uint32_t>(ctx->hist);
+    tb.xs = as<double>(ctx->xs); tb.ys = as<double>(ctx->ys); tb.zs = as<double>(ctx->zs);
+    tb.ms = as<double>(ctx->ms); tb.xf = as<float4>(ctx->xf);
+    tb.lcp = as<uint8_t>(ctx->lcp); tb.win = as<uint8_t>(ctx->win); tb.hi = as<uint8_t>(ctx->hi);
+    tb.chunk_cnt = as<uint32_t>(ctx->chunk);
+    tb.ds = ctx->ds;
+    int in1 = 0;
+    tree_build_count(tb, &in1, st);
+    ctx->sorted_in_1 = in1;
+    uint32_t total = 0;
+    unsigned err = 0;
+    CK(cudaMemcpyAsync(&total, as<uint32_t>(ctx->chunk) + (size_t)(kMaxLevel + 1) * nchunks, 4,
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&err, &ctx->ds->err, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err & kErrNonfinite) return fail(ctx, FMM_ERR_NONFINITE, "non-finite position or mass, or a mass <= 0");
+    if (err & kErrCoincident) return fail(ctx, FMM_ERR_COINCIDENT, "two bodies share the same position");
+    const int nnodes = (int)total;
+    ctx->nnodes = nnodes;
+    const size_t K = (size_t)nnodes;
+    const size_t nr = (size_t)ncoef_real(p);
+    if ((rc = ensure(ctx, ctx->level, 4 * K)) || (rc = ensure(ctx, ctx->begin, 4 * K)) ||
+        (rc = ensure(ctx, ctx->end, 4 * K)) || (rc = ensure(ctx, ctx->parent, 4 * K)) ||
+        (rc = ensure(ctx, ctx->first_child, 4 * K)) || (rc = ensure(ctx, ctx->nchild, 4 * K)) ||
+        (rc = ensure(ctx, ctx->M, 8 * K)) || (rc = ensure(ctx, ctx->S, 24 * K)) ||
+        (rc = ensure(ctx, ctx->zc, 24 * K)) || (rc = ensure(ctx, ctx->r, 8 * K)) ||
+        (rc = ensure(ctx, ctx->Pk, 8 * K * (p + 1))) || (rc = ensure(ctx, ctx->mult, 8 * K * nr)) ||
+        (rc = ensure(ctx, ctx->fmin, 4 * K)) || (rc = ensure(ctx, ctx->fscratch, 4 * (2 * K + N))))
+        return rc;
+    if (mixed) {
+        if ((rc = ensure(ctx, ctx->mult32, 4 * K * nr)) || (rc = ensure(ctx, ctx->loc32, 4 * K * nr))) return rc;
+        if (!m2l32_supported(p) && (rc = ensure(ctx, ctx->loc, 8 * K * nr))) return rc;
+    } else {
+        if ((rc = ensure(ctx, ctx->loc, 8 * K * nr))) return rc;
+    }
+    tb.level = as<int>(ctx->level); tb.begin = as<int>(ctx->begin); tb.end = as<int>(ctx->end);
+    tb.parent = as<int>(ctx->parent); tb.first_child = as<int>(ctx->first_child);
+    tb.nchild = as<int>(ctx->nchild); tb.node_cap = nnodes;
+    tree_build_emit(tb, st);
+    CK(cudaMemcpyAsync(ctx->h_ds, ctx->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::memcpy(ctx->h_level_start, ctx->h_ds->level_start, sizeof(ctx->h_level_start));
+    int nl = 1;
+    for (int L = 1; L <= kMaxLevel; ++L)
+        if (ctx->h_level_start[L] < nnodes) nl = L + 1;
+    ctx->nlevels = nl;
+    ctx->nb = bit_length(nnodes);
+    TreeView t = view(ctx);
+    const uint64_t* keys = as<uint64_t>(in1 ? ctx->k1 : ctx->k0);
+    tree_build_phase2(tb, keys, nnodes, ctx->h_level_start, nl, st);
+    cell_geometry(t, as<double>(ctx->xs), as<double>(ctx->ys), as<double>(ctx->zs), as<double>(ctx->ms),
+                  ctx->h_level_start, as<double>(ctx->M), as<double>(ctx->S), as<double>(ctx->zc),
+                  as<double>(ctx->r), st);
+    CK(cudaEventRecord(ctx->ev[1], st));
+    // ---- upward pass
+    upward_pass(t, ctx->h_level_start, p, as<double>(ctx->xs), as<double>(ctx->ys), as<double>(ctx->zs),
+                as<double>(ctx->ms), as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->mult),
+                as<double>(ctx->Pk), ctx->tb, st);
+    CK(cudaEventRecord(ctx->ev[2], st));
+    // ---- scalar-force estimate
+    if (ctx->front_cap == 0) {
+        const int64_t base = 64 * (int64_t)nnodes + 4096;
+        ctx->front_cap = base;
+        ctx->list_cap[0] = ctx->list_cap[1] = base;
+        ctx->list_cap[2] = ctx->list_cap[3] = 4 * base;
+        if (ctx->cfg.fault_inject & 1u) {
+            ctx->front_cap = 16;
+            for (int l = 0; l < 4; ++l) ctx->list_cap[l] = 16;
+        }
+    }
+    if ((rc = ensure(ctx, ctx->dcount, 64))) return rc;
+    if ((rc = run_walk(ctx, 0, st))) return rc;
+    if ((rc = build_directed(ctx, 0, st)) || (rc = build_directed(ctx, 1, st))) return rc;
+    scalar_force(t, as<double>(ctx->zc), as<double>(ctx->M), as<float4>(ctx->xf), as<uint64_t>(ctx->dkeys[0]),
+                 as<uint32_t>(ctx->doff[0]), as<uint64_t>(ctx->dkeys[1]), as<uint32_t>(ctx->doff[1]), ctx->nb,
+                 as<float>(ctx->fscratch), as<float>(ctx->f), as<float>(ctx->fmin), st);
+    CK(cudaEventRecord(ctx->ev[3], st));
+    // ---- error-controlled walk
+    if ((rc = run_walk(ctx, 1, st))) return rc;
+    if ((rc = build_directed(ctx, 2, st)) || (rc = build_directed(ctx, 3, st))) return rc;
+    CK(cudaMemsetAsync(as<unsigned long long>(ctx->dcount) + 1, 0, sizeof(unsigned long long), st));
+    count_p2p_interactions(as<uint64_t>(ctx->dkeys[3]), ctx->ndirected[3], ctx->nb, as<int>(ctx->begin),
+                           as<int>(ctx->end), as<unsigned long long>(ctx->dcount) + 1, st);
+    CK(cudaEventRecord(ctx->ev[4], st));
+    // ---- far field
+    const uint64_t* mk = as<uint64_t>(ctx->dkeys[2]);
+    const uint32_t* mo = as<uint32_t>(ctx->doff[2]);
+    if (mixed && m2l32_supported(p)) {
+        multipoles_to_f32(as<double>(ctx->mult), as<float>(ctx->mult32), (int64_t)(K * nr), st);
+        m2l_f32(nnodes, p, mk, mo, ctx->nb, as<float>(ctx->mult32), as<double>(ctx->zc), as<double>(ctx->r),
+                as<float>(ctx->loc32), st);
+    } else {
+        m2l_f64(nnodes, p, mk, mo, ctx->nb, as<double>(ctx->mult), as<double>(ctx->zc), as<double>(ctx->r),
+                as<double>(ctx->loc), ctx->tb, st);
+        if (mixed) multipoles_to_f32(as<double>(ctx->loc), as<float>(ctx->loc32), (int64_t)(K * nr), st);
+    }
+    CK(cudaEventRecord(ctx->ev[5], st));
+    if (mixed)
+        downward_pass_f32(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->r), as<float>(ctx->loc32), st);
+    else
+        downward_pass_f64(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->loc),
+                          ctx->tb, st);
+    CK(cudaEventRecord(ctx->ev[6], st));
+    // ---- leaves
+    LeafArgs la{};
+    la.t = t; la.p = p; la.G = ctx->cfg.G;
+    la.xs = as<double>(ctx->xs); la.ys = as<double>(ctx->ys); la.zs = as<double>(ctx->zs); la.ms = as<double>(ctx->ms);
+    la.zc = as<double>(ctx->zc); la.r = as<double>(ctx->r);
+    la.p2p_keys = as<uint64_t>(ctx->dkeys[3]); la.p2p_off = as<uint32_t>(ctx->doff[3]); la.nb = ctx->nb;
+    la.perm = as<uint32_t>(in1 ? ctx->v1 : ctx->v0);
+    la.ax = ax; la.ay = ay; la.az = az; la.pot = pot;
+    la.tb = ctx->tb;
+    if (mixed) {
+        leaf_relative_f32(t, la.xs, la.ys, la.zs, la.ms, la.zc, as<float4>(ctx->prel), st);
+        la.prel = as<float4>(ctx->prel);
+        la.loc = ctx->loc32.ptr;
+        leaf_eval_f32(la, st);
+    } else {
+        la.loc = ctx->loc.ptr;
+        leaf_eval_f64(la, st);
+    }
+    CK(cudaEventRecord(ctx->ev[7], st));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpy(&err, &ctx->ds->err, 4, cudaMemcpyDeviceToHost));
+    if (err & kErrCapacity) return fail(ctx, FMM_ERR_CAPACITY, "an internal list overflowed");
+    unsigned long long inter = 0;
+    CK(cudaMemcpy(&inter, as<unsigned long long>(ctx->dcount) + 1, 8, cudaMemcpyDeviceToHost));
+    ctx->stats.p2p_interactions = (int64_t)inter;
+    // stats
+    fmm_stats& s = ctx->stats;
+    s.nnodes = nnodes;
+    s.nlevels = nl;
+    s.n_far = ctx->npairs[0];
+    s.n_near = ctx->npairs[1];
+    s.n_m2l = ctx->npairs[2];
+    s.n_p2p = ctx->npairs[3];
+    s.ms_tree = elapsed(ctx->ev[0], ctx->ev[1]);
+    s.ms_upward = elapsed(ctx->ev[1], ctx->ev[2]);
+    s.ms_estimate = elapsed(ctx->ev[2], ctx->ev[3]);
+    s.ms_walk = elapsed(ctx->ev[3], ctx->ev[4]);
+    s.ms_m2l = elapsed(ctx->ev[4], ctx->ev[5]);
+    s.ms_downward = elapsed(ctx->ev[5], ctx->ev[6]);
+    s.ms_leaf = elapsed(ctx->ev[6], ctx->ev[7]);
+    s.ms_total = elapsed(ctx->ev[0], ctx->ev[7]);
+    s.kernel_launches = g_launches;
+    return FMM_OK;
+}
+
+int check_cfg(const fmm_config* c, std::string& why) {
+    if (!c) { why = "cfg is NULL"; return FMM_ERR_ARG; }
+    if (c->p < 1 || c->p > kMaxP) { why = "p must be in [1, 30]"; return FMM_ERR_ARG; }
+    if (!(c->eps >= 0.0) || !std::isfinite(c->eps)) { why = "eps must be finite and >= 0"; return FMM_ERR_ARG; }
+    if (c->leaf_size < 1 || c->leaf_size > kMaxLeaf) { why = "leaf_size must be in [1, 256]"; return FMM_ERR_ARG; }
+    if (c->precision != FMM_PRECISION_FP64 && c->precision != FMM_PRECISION_MIXED) { why = "unknown precision"; return FMM_ERR_ARG; }
+    if (c->precision == FMM_PRECISION_MIXED && c->p > kMaxPF32) { why = "mixed precision supports p <= 16"; return FMM_ERR_ARG; }
+    if (!std::isfinite(c->G)) { why = "G must be finite"; return FMM_ERR_ARG; }
+    return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fmm_create(fmm_ctx** out, const fmm_config* cfg) {
+    if (!out) { g_create_error = "out is NULL"; return FMM_ERR_ARG; }
+    *out = nullptr;
+    std::string why;
+    int rc = check_cfg(cfg, why);
+    if (rc != FMM_OK) { g_create_error = why; return rc; }
+    fmm_ctx* ctx = new fmm_ctx();
+    ctx->cfg = *cfg;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "no CUDA device";
+        delete ctx;
+        return FMM_ERR_CUDA;
+    }
+    build_host_tables(ctx->ht);
+    // global-memory tables: swap cos, swap sin, w, iw, fact, rec_a, rec_b, diag, sub, binom row
+    const size_t ncos = sizeof(kSwapCos) / sizeof(double), nsin = sizeof(kSwapSin) / sizeof(double);
+    const size_t nw = (size_t)(kMaxP + 2) * (kMaxP + 2), nrec = (size_t)(kMaxP + 1) * (kMaxP + 1);
+    const size_t nfact = 2 * kMaxP + 4, nd = kMaxP + 1;
+    std::vector<double> blob;
+    blob.insert(blob.end(), kSwapCos, kSwapCos + ncos);
+    blob.insert(blob.end(), kSwapSin, kSwapSin + nsin);
+    blob.insert(blob.end(), &ctx->ht.w[0][0], &ctx->ht.w[0][0] + nw);
+    blob.insert(blob.end(), &ctx->ht.iw[0][0], &ctx->ht.iw[0][0] + nw);
+    blob.insert(blob.end(), ctx->ht.fact, ctx->ht.fact + nfact);
+    blob.insert(blob.end(), &ctx->ht.rec_a[0][0], &ctx->ht.rec_a[0][0] + nrec);
+    blob.insert(blob.end(), &ctx->ht.rec_b[0][0], &ctx->ht.rec_b[0][0] + nrec);
+    blob.insert(blob.end(), ctx->ht.diag, ctx->ht.diag + nd);
+    blob.insert(blob.end(), ctx->ht.sub, ctx->ht.sub + nd);
+    blob.insert(blob.end(), &ctx->ht.binom[cfg->p][0], &ctx->ht.binom[cfg->p][0] + nd);
+    if (ensure(ctx, ctx->tables, blob.size() * sizeof(double)) != FMM_OK ||
+        cudaMemcpy(ctx->tables.ptr, blob.data(), blob.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMalloc(&ctx->ds, sizeof(DevScalars)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_ds, sizeof(DevScalars)) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "device allocation failed in fmm_create";
+        fmm_destroy(ctx);
+        return FMM_ERR_OOM;
+    }
+    cudaMemset(ctx->ds, 0, sizeof(DevScalars));
+    const double* base = reinterpret_cast<const double*>(ctx->tables.ptr);
+    size_t o = 0;
+    ctx->tb.swap_cos = base + o; o += ncos;
+    ctx->tb.swap_sin = base + o; o += nsin;
+    ctx->tb.w = base + o; o += nw;
+    ctx->tb.iw = base + o; o += nw;
+    ctx->tb.fact = base + o; o += nfact;
+    ctx->tb.rec_a = base + o; o += nrec;
+    ctx->tb.rec_b = base + o; o += nrec;
+    ctx->tb.diag = base + o; o += nd;
+    ctx->tb.sub = base + o; o += nd;
+    upload_expansion_tables(ctx->ht);
+    upload_m2l_tables(ctx->ht, kSwapCos, kSwapSin);
+    upload_leaf_tables(ctx->ht);
+    for (auto& e : ctx->ev) cudaEventCreate(&e);
+    if (cudaGetLastError() != cudaSuccess) {
+        g_create_error = "CUDA error while uploading tables";
+        fmm_destroy(ctx);
+        return FMM_ERR_CUDA;
+    }
+    *out = ctx;
+    return FMM_OK;
+}
+
+void fmm_destroy(fmm_ctx* ctx) {
+    if (!ctx) return;
+    Buf* all[] = {&ctx->tables, &ctx->k0, &ctx->k1, &ctx->v0, &ctx->v1, &ctx->hist, &ctx->xs, &ctx->ys,
+                  &ctx->zs, &ctx->ms, &ctx->xf, &ctx->prel, &ctx->lcp, &ctx->win, &ctx->hi, &ctx->chunk,
+                  &ctx->f, &ctx->bbox, &ctx->level, &ctx->begin, &ctx->end, &ctx->parent,
+                  &ctx->first_child, &ctx->nchild, &ctx->M, &ctx->S, &ctx->zc, &ctx->r, &ctx->Pk,
+                  &ctx->mult, &ctx->mult32, &ctx->loc, &ctx->loc32, &ctx->fmin, &ctx->fscratch,
+                  &ctx->front0, &ctx->front1, &ctx->dalt, &ctx->dcount};
+    for (Buf* b : all) release(*b);
+    for (int l = 0; l < 4; ++l) {
+        release(ctx->lists[l]);
+        release(ctx->dkeys[l]);
+        release(ctx->doff[l]);
+        release(ctx->hin[l]);
+        release(ctx->hout[l]);
+    }
+    if (ctx->ds) cudaFree(ctx->ds);
+    if (ctx->h_ds) cudaFreeHost(ctx->h_ds);
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+int fmm_solve(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z, const double* m,
+              double* ax, double* ay, double* az, double* pot, void* cuda_stream) {
+    if (!ctx) return FMM_ERR_ARG;
+    if (n < 0 || n > (int64_t)1 << 30) return fail(ctx, FMM_ERR_ARG, "n must be in [0, 2^30]");
+    if (n > 0 && (!x || !y || !z || !m || !ax || !ay || !az))
+        return fail(ctx, FMM_ERR_ARG, "NULL input or output pointer");
+    cudaSetDevice(ctx->device);
+    return solve_device(ctx, n, x, y, z, m, ax, ay, az, pot, (cudaStream_t)cuda_stream);
+}
+
+int fmm_solve_host(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
+                   const double* m, double* ax, double* ay, double* az, double* pot, void* cuda_stream) {
+    if (!ctx) return FMM_ERR_ARG;
+    if (n < 0 || n > (int64_t)1 << 30) return fail(ctx, FMM_ERR_ARG, "n must be in [0, 2^30]");
+    if (n == 0) return FMM_OK;
+    if (!x || !y || !z || !m || !ax || !ay || !az) return fail(ctx, FMM_ERR_ARG, "NULL input or output pointer");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t bytes = 8 * (size_t)n;
+    int rc;
+    for (int i = 0; i < 4; ++i)
+        if ((rc = ensure(ctx, ctx->hin[i], bytes)) || (rc = ensure(ctx, ctx->hout[i], bytes))) return rc;
+    const double* in[4] = {x, y, z, m};
+    for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(ctx->hin[i].ptr, in[i], bytes, cudaMemcpyHostToDevice, st));
+    rc = solve_device(ctx, n, as<double>(ctx->hin[0]), as<double>(ctx->hin[1]), as<double>(ctx->hin[2]),
+                      as<double>(ctx->hin[3]), as<double>(ctx->hout[0]), as<double>(ctx->hout[1]),
+                      as<double>(ctx->hout[2]), pot ? as<double>(ctx->hout[3]) : nullptr, st);
+    if (rc != FMM_OK) return rc;
+    double* outp[4] = {ax, ay, az, pot};
+    for (int i = 0; i < 4; ++i)
+        if (outp[i]) CK(cudaMemcpyAsync(outp[i], ctx->hout[i].ptr, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return FMM_OK;
+}
+
+int fmm_solve_batch(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, const double* x,
+                    const double* y, const double* z, const double* m, double* ax, double* ay, double* az,
+                    double* pot, void* cuda_stream) {
+    if (!ctx) return FMM_ERR_ARG;
+    if (nclusters < 0 || (nclusters > 0 && !offsets)) return fail(ctx, FMM_ERR_ARG, "bad cluster offsets");
+    if (nclusters > 0 && offsets[0] != 0) return fail(ctx, FMM_ERR_ARG, "offsets[0] must be 0");
+    for (int32_t c = 0; c < nclusters; ++c)
+        if (offsets[c + 1] < offsets[c]) return fail(ctx, FMM_ERR_ARG, "offsets must be non-decreasing");
+    fmm_stats total{};
+    for (int32_t c = 0; c < nclusters; ++c) {
+        const int64_t o = offsets[c], n = offsets[c + 1] - offsets[c];
+        const int rc = fmm_solve(ctx, n, x + o, y + o, z + o, m + o, ax + o, ay + o, az + o,
+                                 pot ? pot + o : nullptr, cuda_stream);
+        if (rc != FMM_OK) return rc;
+        total.n += ctx->stats.n;
+        total.nnodes += ctx->stats.nnodes;
+        total.n_m2l += ctx->stats.n_m2l;
+        total.n_p2p += ctx->stats.n_p2p;
+        total.ms_total += ctx->stats.ms_total;
+        total.kernel_launches += ctx->stats.kernel_launches;
+    }
+    ctx->stats = total;
+    return FMM_OK;
+}
+
+int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z, const double* m,
+               int64_t ntargets, const int64_t* targets, double* ax, double* ay, double* az, double* pot,
+               void* cuda_stream) {
+    if (!ctx) return FMM_ERR_ARG;
+    if (n < 0 || ntargets < 0) return fail(ctx, FMM_ERR_ARG, "negative size");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    direct_sum_f64(n, x, y, z, m, ctx->cfg.G, targets ? ntargets : n, targets, ax, ay, az, pot, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return FMM_OK;
+}
+
+int fmm_get_stats(const fmm_ctx* ctx, fmm_stats* out) {
+    if (!ctx || !out) return FMM_ERR_ARG;
+    *out = ctx->stats;
+    return FMM_OK;
+}
+
+int fmm_export_tree(const fmm_ctx* cctx, uint64_t* keys, int64_t* perm, int32_t* level, int32_t* begin,
+                    int32_t* end, int32_t* parent, int32_t* first_child, int32_t* nchild) {
+    fmm_ctx* ctx = const_cast<fmm_ctx*>(cctx);
+    if (!ctx) return FMM_ERR_ARG;
+    const size_t n = (size_t)ctx->n, K = (size_t)ctx->nnodes;
+    if (keys) CK(cudaMemcpy(keys, (ctx->sorted_in_1 ? ctx->k1 : ctx->k0).ptr, 8 * n, cudaMemcpyDeviceToHost));
+    if (perm) {
+        std::vector<uint32_t> p32(n);
+        CK(cudaMemcpy(p32.data(), (ctx->sorted_in_1 ? ctx->v1 : ctx->v0).ptr, 4 * n, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) perm[i] = p32[i];
+    }
+    struct { int32_t* dst; Buf* src; } arr[] = {{level, &ctx->level}, {begin, &ctx->begin}, {end, &ctx->end},
+                                                {parent, &ctx->parent}, {first_child, &ctx->first_child},
+                                                {nchild, &ctx->nchild}};
+    for (auto& a : arr)
+        if (a.dst) CK(cudaMemcpy(a.dst, a.src->ptr, 4 * K, cudaMemcpyDeviceToHost));
+    return FMM_OK;
+}
+
+int fmm_export_geometry(const fmm_ctx* cctx, double* M, double* z, double* r, double* P, float* fmin, float* f) {
+    fmm_ctx* ctx = const_cast<fmm_ctx*>(cctx);
+    if (!ctx) return FMM_ERR_ARG;
+    const size_t K = (size_t)ctx->nnodes;
+    if (M) CK(cudaMemcpy(M, ctx->M.ptr, 8 * K, cudaMemcpyDeviceToHost));
+    if (z) CK(cudaMemcpy(z, ctx->zc.ptr, 24 * K, cudaMemcpyDeviceToHost));
+    if (r) CK(cudaMemcpy(r, ctx->r.ptr, 8 * K, cudaMemcpyDeviceToHost));
+    if (P) CK(cudaMemcpy(P, ctx->Pk.ptr, 8 * K * (size_t)(ctx->cfg.p + 1), cudaMemcpyDeviceToHost));
+    if (fmin) CK(cudaMemcpy(fmin, ctx->fmin.ptr, 4 * K, cudaMemcpyDeviceToHost));
+    if (f) CK(cudaMemcpy(f, ctx->f.ptr, 4 * (size_t)ctx->n, cudaMemcpyDeviceToHost));
+    return FMM_OK;
+}
+
+int fmm_export_pairs(const fmm_ctx* cctx, int which, int64_t* count, int32_t* pairs) {
+    fmm_ctx* ctx = const_cast<fmm_ctx*>(cctx);
+    if (!ctx || which < 0 || which > 3 || !count) return FMM_ERR_ARG;
+    *count = ctx->npairs[which];
+    if (pairs && ctx->npairs[which] > 0)
+        CK(cudaMemcpy(pairs, ctx->lists[which].ptr, 8 * (size_t)ctx->npairs[which], cudaMemcpyDeviceToHost));
+    return FMM_OK;
+}
+
+int fmm_export_swap(int64_t* ncos, int64_t* nsin, double* cos_blocks, double* sin_blocks) {
+    const int64_t nc = (int64_t)(sizeof(kSwapCos) / sizeof(double)), ns = (int64_t)(sizeof(kSwapSin) / sizeof(double));
+    if (ncos) *ncos = nc;
+    if (nsin) *nsin = ns;
+    if (cos_blocks) std::memcpy(cos_blocks, kSwapCos, sizeof(kSwapCos));
+    if (sin_blocks) std::memcpy(sin_blocks, kSwapSin, sizeof(kSwapSin));
+    return FMM_OK;
+}
+
+const char* fmm_last_error(const fmm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,361 @@
+// Upward and downward passes on hat-normalised expansions.
+//
+// The library stores multipoles and locals in the basis
+//   Shat_n^m(r) = sqrt((n+m)!(n-m)!) Upsilon_n^m(r)   (Schmidt semi-normalised r^n Y_n^m)
+// scaled by the cell size s (its radius r_A, Sec. 2.3):
+//   Mhat_n^m = sum_i m_i Shat_n^m((x_i - z_A)/s_A)        = M_n^m w_n^m / s_A^n
+//   Fhat_n^m = F_n^m s_B^n / w_n^m
+// with M, F the moments and local coefficients of Sec. 2.2 and w_n^m =
+// sqrt((n+m)!(n-m)!). Every hat coefficient is bounded by the cell mass (or
+// the local field), so the same code runs in FP32 without overflow.
+// The degree norms of Sec. 2.3 become P_n = s_A^n sqrt(sum_m |Mhat_n^m|^2).
+//
+// Real layout of a vector: degree n at offset n^2 as [Re m=0, Re 1, Im 1, ...].
+#include "gbfmm_internal.cuh"
+
+namespace gbfmm {
+
+namespace {
+
+__constant__ float c_w32[kMaxPF32 + 2][kMaxPF32 + 2];
+__constant__ float c_iw32[kMaxPF32 + 2][kMaxPF32 + 2];
+__constant__ float c_rec_a32[kMaxPF32 + 1][kMaxPF32 + 1];
+__constant__ float c_rec_b32[kMaxPF32 + 1][kMaxPF32 + 1];
+__constant__ float c_diag32[kMaxPF32 + 1];
+__constant__ float c_sub32[kMaxPF32 + 1];
+
+__host__ __device__ constexpr int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+
+template <typename T>
+struct Cx { T re, im; };
+
+template <typename T>
+__device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+// Table access for both precisions: FP64 from global tables, FP32 from constants.
+struct TabF64 {
+    const double *w, *iw, *rec_a, *rec_b, *diag, *sub;
+    __device__ double W(int n, int m) const { return w[n * (kMaxP + 2) + m]; }
+    __device__ double IW(int n, int m) const { return iw[n * (kMaxP + 2) + m]; }
+    __device__ double A(int n, int m) const { return rec_a[n * (kMaxP + 1) + m]; }
+    __device__ double B(int n, int m) const { return rec_b[n * (kMaxP + 1) + m]; }
+    __device__ double D(int m) const { return diag[m]; }
+    __device__ double Sb(int m) const { return sub[m]; }
+};
+struct TabF32 {
+    __device__ float W(int n, int m) const { return c_w32[n][m]; }
+    __device__ float IW(int n, int m) const { return c_iw32[n][m]; }
+    __device__ float A(int n, int m) const { return c_rec_a32[n][m]; }
+    __device__ float B(int n, int m) const { return c_rec_b32[n][m]; }
+    __device__ float D(int m) const { return c_diag32[m]; }
+    __device__ float Sb(int m) const { return c_sub32[m]; }
+};
+
+// All Shat_n^m(x,y,z), 0 <= m <= n <= p, into out[tri(n,m)] (sequential).
+template <typename T, typename Tab>
+__device__ void shat_all(int p, T x, T y, T z, const Tab& tb, Cx<T>* out) {
+    const T r2 = x * x + y * y + z * z;
+    Cx<T> d{T(1), T(0)};
+    const Cx<T> xp{x, y};
+    for (int m = 0; m <= p; ++m) {
+        if (m > 0) {
+            d = cmul(d, xp);
+            d.re *= tb.D(m);
+            d.im *= tb.D(m);
+        }
+        out[tri(m, m)] = d;
+        if (m + 1 <= p) out[tri(m + 1, m)] = {tb.Sb(m) * z * d.re, tb.Sb(m) * z * d.im};
+        for (int n = m + 2; n <= p; ++n) {
+            const T a = tb.A(n, m) * z, b = tb.B(n, m) * r2;
+            const Cx<T> u = out[tri(n - 1, m)], v = out[tri(n - 2, m)];
+            out[tri(n, m)] = {a * u.re - b * v.re, a * u.im - b * v.im};
+        }
+    }
+}
+
+// conjugate-symmetric access X_n^m, m in [-n, n], to a tri-stored vector
+template <typename T>
+__device__ __forceinline__ Cx<T> tri_get(const Cx<T>* a, int n, int m) {
+    if (m >= 0) return a[tri(n, m)];
+    Cx<T> v = a[tri(n, -m)];
+    return ((-m) & 1) ? Cx<T>{-v.re, v.im} : Cx<T>{v.re, -v.im};
+}
+// same for the real layout
+template <typename T>
+__device__ __forceinline__ Cx<T> real_get(const T* a, int n, int m) {
+    const int am = m < 0 ? -m : m;
+    Cx<T> v{a[hre(n, am)], am ? a[him(n, am)] : T(0)};
+    if (m >= 0) return v;
+    return (am & 1) ? Cx<T>{-v.re, v.im} : Cx<T>{v.re, -v.im};
+}
+
+// ---- P2M: one warp per leaf; lanes own an order m, groups of lanes own bodies
+__global__ void __launch_bounds__(128) k_p2m(TreeView t, int p, TabF64 tb,
+                                              const double* __restrict__ xs,
+                                              const double* __restrict__ ys,
+                                              const double* __restrict__ zs,
+                                              const double* __restrict__ ms,
+                                              const double* __restrict__ zc,
+                                              const double* __restrict__ rr,
+                                              double* __restrict__ mult) {
+    extern __shared__ double sh_p2m[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gsize = (p + 1 <= 8) ? 8 : ((p + 1 <= 16) ? 16 : 32);
+    const int ngroups = 32 / gsize;
+    const int g = lane / gsize, m = lane % gsize;
+    const int nc = tri(p + 1, 0);
+    Cx<double>* acc = reinterpret_cast<Cx<double>*>(sh_p2m) + (size_t)wib * ngroups * nc;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int k = blockIdx.x * (blockDim.x >> 5) + wib; k < t.nnodes; k += nwarps) {
+        if (t.nchild[k] != 0) continue;
+        for (int i = lane; i < ngroups * nc; i += 32) acc[i] = {0.0, 0.0};
+        __syncwarp();
+        const double s = hat_scale(rr[k]);
+        const double cx = zc[3 * k], cy = zc[3 * k + 1], cz = zc[3 * k + 2];
+        Cx<double>* my = acc + g * nc;
+        for (int i = t.begin[k] + g; i < t.end[k]; i += ngroups) {
+            if (m > p) continue;
+            const double x = (xs[i] - cx) / s, y = (ys[i] - cy) / s, z = (zs[i] - cz) / s;
+            const double w = ms[i];
+            const double r2 = x * x + y * y + z * z;
+            Cx<double> d{1.0, 0.0};
+            const Cx<double> xp{x, y};
+            for (int q = 1; q <= m; ++q) {
+                d = cmul(d, xp);
+                d.re *= tb.D(q);
+                d.im *= tb.D(q);
+            }
+            Cx<double> v2{0.0, 0.0}, v1 = d;
+            my[tri(m, m)].re += w * d.re;
+            my[tri(m, m)].im += w * d.im;
+            for (int n = m + 1; n <= p; ++n) {
+                Cx<double> v;
+                if (n == m + 1) {
+                    v = {tb.Sb(m) * z * v1.re, tb.Sb(m) * z * v1.im};
+                } else {
+                    const double a = tb.A(n, m) * z, b = tb.B(n, m) * r2;
+                    v = {a * v1.re - b * v2.re, a * v1.im - b * v2.im};
+                }
+                my[tri(n, m)].re += w * v.re;
+                my[tri(n, m)].im += w * v.im;
+                v2 = v1;
+                v1 = v;
+            }
+        }
+        __syncwarp();
+        double* out = mult + (size_t)ncoef_real(p) * k;
+        for (int q = lane; q < nc; q += 32) {
+            Cx<double> s2 = acc[q];
+            for (int gg = 1; gg < ngroups; ++gg) {
+                s2.re += acc[gg * nc + q].re;
+                s2.im += acc[gg * nc + q].im;
+            }
+            int n = 0;
+            while (tri(n + 1, 0) <= q) ++n;
+            const int mm = q - tri(n, 0);
+            out[hre(n, mm)] = s2.re;
+            if (mm) out[him(n, mm)] = s2.im;
+        }
+        __syncwarp();
+    }
+}
+
+// ---- M2M (FP64): one block per parent, one thread per output (n, m >= 0)
+//   Mhat_n^m(P) = sum_C sum_{k,l} Shat_k^l(b) beta sigma^{n-k} Mhat_{n-k}^{m-l}(C),
+//   b = (z_C - z_P)/s_P, sigma = s_C/s_P, beta = w_n^m / (w_k^l w_{n-k}^{m-l}).
+__global__ void k_m2m(TreeView t, int k0, int p, TabF64 tb, const double* __restrict__ zc,
+                      const double* __restrict__ rr, double* __restrict__ mult) {
+    extern __shared__ double sh_m2m[];
+    const int P = k0 + blockIdx.x;
+    if (t.nchild[P] == 0) return;
+    const int nc = tri(p + 1, 0), nr = ncoef_real(p);
+    const int c0 = t.first_child[P], ncld = t.nchild[P];
+    Cx<double>* S = reinterpret_cast<Cx<double>*>(sh_m2m);          // 8 * nc
+    double* Mc = sh_m2m + 2 * 8 * nc;                                 // 8 * nr
+    double* sig = Mc + 8 * nr;                                        // 8 * (p+1)
+    const double sP = hat_scale(rr[P]);
+    for (int c = threadIdx.x; c < ncld; c += blockDim.x) {
+        const int C = c0 + c;
+        const double bx = (zc[3 * C] - zc[3 * P]) / sP, by = (zc[3 * C + 1] - zc[3 * P + 1]) / sP,
+                     bz = (zc[3 * C + 2] - zc[3 * P + 2]) / sP;
+        shat_all<double>(p, bx, by, bz, tb, S + c * nc);
+        const double sg = hat_scale(rr[C]) / sP;
+        double pw = 1.0;
+        for (int j = 0; j <= p; ++j) { sig[c * (p + 1) + j] = pw; pw *= sg; }
+    }
+    for (int i = threadIdx.x; i < ncld * nr; i += blockDim.x)
+        Mc[i] = mult[(size_t)nr * (c0 + i / nr) + (i % nr)];
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+        int n = 0;
+        while (tri(n + 1, 0) <= q) ++n;
+        const int m = q - tri(n, 0);
+        double are = 0.0, aim = 0.0;
+        for (int c = 0; c < ncld; ++c) {
+            const Cx<double>* Sc = S + c * nc;
+            const double* M = Mc + c * nr;
+            for (int k = 0; k <= n; ++k) {
+                const double sgp = sig[c * (p + 1) + (n - k)];
+                for (int l = -k; l <= k; ++l) {
+                    const int ml = m - l;
+                    if (ml > n - k || ml < -(n - k)) continue;
+                    const double beta = tb.W(n, m) * tb.IW(k, l < 0 ? -l : l) * tb.IW(n - k, ml < 0 ? -ml : ml);
+                    const Cx<double> prod = cmul(tri_get(Sc, k, l), real_get(M, n - k, ml));
+                    are += beta * sgp * prod.re;
+                    aim += beta * sgp * prod.im;
+                }
+            }
+        }
+        double* out = mult + (size_t)nr * P;
+        out[hre(n, m)] = are;
+        if (m) out[him(n, m)] = aim;
+    }
+}
+
+// P_n = s^n sqrt(sum_{m=-n}^{n} |Mhat_n^m|^2)  (Sec. 2.3)
+__global__ void k_pnorm(int nnodes, int p, const double* __restrict__ mult,
+                        const double* __restrict__ rr, double* __restrict__ Pk) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnodes) return;
+    const double* M = mult + (size_t)ncoef_real(p) * k;
+    const double s = hat_scale(rr[k]);
+    double sp = 1.0;
+    for (int n = 0; n <= p; ++n) {
+        double acc = M[hre(n, 0)] * M[hre(n, 0)];
+        for (int m = 1; m <= n; ++m) acc += 2.0 * (M[hre(n, m)] * M[hre(n, m)] + M[him(n, m)] * M[him(n, m)]);
+        Pk[(size_t)(p + 1) * k + n] = sp * sqrt(acc);
+        sp *= s;
+    }
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+// ---- L2L: one block per child, one thread per output (n, m >= 0)
+//   Fhat_n^m(C) += sum_{k<=p-n} sum_l conj(Shat_k^l(b)) beta' sigma^n Fhat_{n+k}^{m+l}(P),
+//   b = (z_C - z_P)/s_P, sigma = s_C/s_P, beta' = w_{n+k}^{m+l} / (w_k^l w_n^m).
+template <typename T, typename Tab>
+__global__ void k_l2l(TreeView t, int k0, int k1, int p, Tab tb, const double* __restrict__ zc,
+                      const double* __restrict__ rr, T* __restrict__ loc) {
+    extern __shared__ __align__(16) unsigned char sh_l2l_raw[];
+    const int C = k0 + blockIdx.x;
+    if (C >= k1) return;
+    const int P = t.parent[C];
+    const int nc = tri(p + 1, 0), nr = ncoef_real(p);
+    Cx<T>* S = reinterpret_cast<Cx<T>*>(sh_l2l_raw);
+    T* Fp = reinterpret_cast<T*>(S + nc);
+    T* sig = Fp + nr;
+    const double sP = hat_scale(rr[P]);
+    if (threadIdx.x == 0) {
+        const T bx = (T)((zc[3 * C] - zc[3 * P]) / sP), by = (T)((zc[3 * C + 1] - zc[3 * P + 1]) / sP),
+                bz = (T)((zc[3 * C + 2] - zc[3 * P + 2]) / sP);
+        shat_all<T>(p, bx, by, bz, tb, S);
+        const T sg = (T)(hat_scale(rr[C]) / sP);
+        T pw = T(1);
+        for (int j = 0; j <= p; ++j) { sig[j] = pw; pw *= sg; }
+    }
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) Fp[i] = loc[(size_t)nr * P + i];
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+        int n = 0;
+        while (tri(n + 1, 0) <= q) ++n;
+        const int m = q - tri(n, 0);
+        T are = T(0), aim = T(0);
+        for (int k = 0; k <= p - n; ++k) {
+            for (int l = -k; l <= k; ++l) {
+                const int ml = m + l;
+                const T beta = tb.W(n + k, ml < 0 ? -ml : ml) * tb.IW(k, l < 0 ? -l : l) * tb.IW(n, m);
+                Cx<T> sv = tri_get(S, k, l);
+                sv.im = -sv.im;
+                const Cx<T> prod = cmul(sv, real_get(Fp, n + k, ml));
+                are += beta * prod.re;
+                aim += beta * prod.im;
+            }
+        }
+        T* out = loc + (size_t)nr * C;
+        out[hre(n, m)] += sig[n] * are;
+        if (m) out[him(n, m)] += sig[n] * aim;
+    }
+}
+
+inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+TabF64 tab64(const DevTables& tb) { return TabF64{tb.w, tb.iw, tb.rec_a, tb.rec_b, tb.diag, tb.sub}; }
+}  // namespace
+
+void upload_expansion_tables(const HostTables& h) {
+    float w[kMaxPF32 + 2][kMaxPF32 + 2], iw[kMaxPF32 + 2][kMaxPF32 + 2];
+    float a[kMaxPF32 + 1][kMaxPF32 + 1], b[kMaxPF32 + 1][kMaxPF32 + 1];
+    float d[kMaxPF32 + 1], s[kMaxPF32 + 1];
+    for (int n = 0; n < kMaxPF32 + 2; ++n)
+        for (int m = 0; m < kMaxPF32 + 2; ++m) { w[n][m] = (float)h.w[n][m]; iw[n][m] = (float)h.iw[n][m]; }
+    for (int n = 0; n <= kMaxPF32; ++n) {
+        for (int m = 0; m <= kMaxPF32; ++m) { a[n][m] = (float)h.rec_a[n][m]; b[n][m] = (float)h.rec_b[n][m]; }
+        d[n] = (float)h.diag[n];
+        s[n] = (float)h.sub[n];
+    }
+    cudaMemcpyToSymbol(c_w32, w, sizeof(w));
+    cudaMemcpyToSymbol(c_iw32, iw, sizeof(iw));
+    cudaMemcpyToSymbol(c_rec_a32, a, sizeof(a));
+    cudaMemcpyToSymbol(c_rec_b32, b, sizeof(b));
+    cudaMemcpyToSymbol(c_diag32, d, sizeof(d));
+    cudaMemcpyToSymbol(c_sub32, s, sizeof(s));
+}
+
+void upward_pass(const TreeView& t, const int* h_level_start, int p, const double* xs,
+                 const double* ys, const double* zs, const double* ms, const double* zc,
+                 const double* r, double* mult, double* Pk, const DevTables& tbl, cudaStream_t st) {
+    const TabF64 tb = tab64(tbl);
+    const int nc = tri(p + 1, 0), nr = ncoef_real(p);
+    const int gsize = (p + 1 <= 8) ? 8 : ((p + 1 <= 16) ? 16 : 32);
+    const size_t sh_p2m = (size_t)4 * (32 / gsize) * nc * sizeof(double) * 2;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    (k_p2m<<<152 * 8, 128, sh_p2m, st>>>(t, p, tb, xs, ys, zs, ms, zc, r, mult), note_launch());
+    const size_t sh_m2m = ((size_t)2 * 8 * nc + 8 * nr + 8 * (p + 1)) * sizeof(double);
+    for (int L = t.nlevels - 2; L >= 0; --L) {
+        const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
+        if (k1 > k0) (k_m2m<<<k1 - k0, 64, sh_m2m, st>>>(t, k0, p, tb, zc, r, mult), note_launch());
+    }
+    (k_pnorm<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, p, mult, r, Pk), note_launch());
+}
+
+void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStream_t st) {
+    if (count > 0) (k_to_f32<<<blocks_for(count, 256), 256, 0, st>>>(mult, mult32, count), note_launch());
+}
+
+void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const double* zc,
+                       const double* r, double* loc, const DevTables& tbl, cudaStream_t st) {
+    const TabF64 tb = tab64(tbl);
+    const int nc = tri(p + 1, 0), nr = ncoef_real(p);
+    const size_t sh = (size_t)(2 * nc + nr + p + 1) * sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_l2l<double, TabF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        attr_set = true;
+    }
+    for (int L = 1; L < t.nlevels; ++L) {
+        const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
+        if (k1 > k0) (k_l2l<double, TabF64><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, tb, zc, r, loc), note_launch());
+    }
+}
+
+void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const double* zc,
+                       const double* r, float* loc, cudaStream_t st) {
+    const int nc = tri(p + 1, 0), nr = ncoef_real(p);
+    const size_t sh = (size_t)(2 * nc + nr + p + 1) * sizeof(float);
+    for (int L = 1; L < t.nlevels; ++L) {
+        const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
+        if (k1 > k0) (k_l2l<float, TabF32><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, TabF32{}, zc, r, loc), note_launch());
+    }
+}
+
+}  // namespace gbfmm

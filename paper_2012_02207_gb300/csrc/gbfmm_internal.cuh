@@ -1,0 +1,215 @@
+// Internal declarations of the gbfmm GPU library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "gbfmm.h"
+
+namespace gbfmm {
+
+constexpr int kMaxLevel = 21;   // 21 bits per axis in a 63-bit Morton key
+constexpr int kMaxP = 30;       // swap matrices are tabulated to p = 30 (Sec. 2.4)
+constexpr int kMaxPF32 = 16;    // largest order of the FP32 expansion kernels
+constexpr int kMaxLeaf = 256;
+constexpr int kMaxWalkIters = 192;
+
+// error bits raised by kernels (never a trap)
+enum : unsigned {
+    kErrCapacity = 1u,
+    kErrCoincident = 2u,
+    kErrNonfinite = 4u,
+    kErrTimeout = 8u,
+};
+
+// real layout of a hat coefficient vector: degree n starts at n*n with
+// [Re m=0, Re m=1, Im m=1, ..., Re m=n, Im m=n]; (p+1)^2 reals in all.
+__host__ __device__ constexpr int hre(int n, int m) { return n * n + (m == 0 ? 0 : 2 * m - 1); }
+__host__ __device__ constexpr int him(int n, int m) { return n * n + 2 * m; }
+__host__ __device__ constexpr int ncoef_real(int p) { return (p + 1) * (p + 1); }
+
+// Device-resident scalars of one context (counters, box, tree sizes).
+struct DevScalars {
+    double box[8];                 // cx, cy, cz, h, lox, loy, loz, size
+    unsigned err;                  // kErr* bits
+    int pad;
+    unsigned long long cnt[kMaxWalkIters + 2];  // walk frontier sizes per iteration
+    unsigned long long list_cnt[4];             // far, near, m2l, p2p
+    int nnodes;
+    int level_start[kMaxLevel + 3];
+};
+
+// Host tables of normalisation constants for hat-normalised harmonics
+// Shat_n^m = sqrt((n+m)!(n-m)!) Upsilon_n^m.
+struct HostTables {
+    double w[kMaxP + 2][kMaxP + 2];    // sqrt((n+m)!(n-m)!)
+    double iw[kMaxP + 2][kMaxP + 2];   // 1 / w
+    double fact[2 * kMaxP + 4];
+    double binom[kMaxP + 1][kMaxP + 1];
+    double rec_a[kMaxP + 1][kMaxP + 1];  // (2n-1)/sqrt((n+m)(n-m))
+    double rec_b[kMaxP + 1][kMaxP + 1];  // sqrt((n+m-1)(n-m-1)/((n+m)(n-m)))
+    double diag[kMaxP + 1];              // sqrt((2m-1)/(2m))
+    double sub[kMaxP + 1];               // sqrt(2m+1)
+};
+
+// Device pointers of the global-memory tables (FP64, p <= 30).
+struct DevTables {
+    const double* swap_cos;   // generator layout
+    const double* swap_sin;
+    const double* w;          // (kMaxP+2)^2
+    const double* iw;
+    const double* fact;
+    const double* rec_a;      // (kMaxP+1)^2
+    const double* rec_b;
+    const double* diag;
+    const double* sub;
+};
+
+inline size_t swap_cos_offset(int n) { return (size_t)n * (n + 1) * (2 * n + 1) / 6; }  // sum_{k<n}(k+1)^2
+inline size_t swap_sin_offset(int n) { return (size_t)(n - 1) * n * (2 * n - 1) / 6; }  // sum_{k<n} k^2
+
+// Tree arrays (device), nodes numbered level by level, key order inside a level.
+struct TreeView {
+    int n;
+    int nnodes;
+    int nlevels;
+    int leaf_size;
+    const int* level;
+    const int* begin;
+    const int* end;
+    const int* parent;
+    const int* first_child;
+    const int* nchild;
+};
+
+// Every kernel launch of the library calls note_launch(); fmm_get_stats
+// reports the count of the last solve.
+void note_launch();
+
+// ---------------------------------------------------------------- sort.cu
+// Stable LSD radix sort of 64-bit keys (optionally with 32-bit values) on the
+// low `bits` bits. Ping-pongs between buffers; returns 1 if the sorted data
+// ends in (k1, v1), 0 if in (k0, v0). hist needs radix_hist_words(n) words.
+size_t radix_hist_words(int64_t n);
+int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bits,
+               uint32_t* hist, cudaStream_t st);
+// single-block exclusive scan of count uint32 values in place; total -> *total (device)
+void scan_exclusive_u32(uint32_t* data, int64_t count, uint32_t* total, cudaStream_t st);
+
+// ---------------------------------------------------------------- tree.cu
+struct TreeBuffers {
+    // inputs
+    const double *x, *y, *z, *m;
+    int64_t n;
+    int leaf_size;
+    // scratch / outputs
+    double* bbox_part;     // 6 * nblocks_bbox
+    uint64_t *k0, *k1;
+    uint32_t *v0, *v1;
+    uint32_t* hist;
+    double *xs, *ys, *zs, *ms;   // sorted bodies
+    float4* xf;                  // cube-centred FP32 coordinates + mass (scalar-force estimate)
+    uint8_t *lcp, *win, *hi;     // per body
+    uint32_t* chunk_cnt;         // 23 * nchunks (+1 total)
+    int *level, *begin, *end, *parent, *first_child, *nchild;
+    int64_t node_cap;
+    DevScalars* ds;
+};
+// keys -> sort -> gather -> node-start counts and their scan; the node
+// total lands at chunk_cnt[22 * nchunks]. sorted_in_1 tells where the sorted
+// keys/perm ended up.
+void tree_build_count(TreeBuffers& b, int* sorted_in_1, cudaStream_t st);
+// node level/begin arrays and ds->level_start, ds->nnodes
+void tree_build_emit(TreeBuffers& b, cudaStream_t st);
+int tree_nchunks(int64_t n);
+void tree_build_phase2(TreeBuffers& b, const uint64_t* keys, int nnodes, const int* h_level_start,
+                       int nlevels, cudaStream_t st);
+// Cell geometry (Sec. 2.3 readings): M, S, z (centre of mass), r (size).
+void cell_geometry(const TreeView& t, const double* xs, const double* ys, const double* zs,
+                   const double* ms, const int* h_level_start, double* M, double* S, double* zc,
+                   double* r, cudaStream_t st);
+
+// ---------------------------------------------------------------- walk.cu
+struct WalkBuffers {
+    int2 *front0, *front1;
+    int64_t front_cap;
+    int2* out[4];          // far, near, m2l, p2p
+    int64_t out_cap[4];
+};
+// Dual-tree walk from (root, root). mode 0: theta < 1 (lists far/near);
+// mode 1: the error-controlled MAC (lists m2l/p2p). Returns iterations or a
+// negative fmm_status. Counts land in ds->list_cnt.
+int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* r, const double* P,
+                   const float* fmin, int p, double eps, const double* binom_row, WalkBuffers& wb,
+                   DevScalars* ds, DevScalars* h_ds, cudaStream_t st);
+// Scalar-force estimate f (Sec. 2.3) from the theta-walk lists given as
+// per-target CSR (sorted directed keys target<<nb | source).
+void scalar_force(const TreeView& t, const double* zc, const double* M, const float4* xf,
+                  const uint64_t* far_keys, const uint32_t* far_off, const uint64_t* near_keys,
+                  const uint32_t* near_off, int nb, float* farf, float* f, float* fmin,
+                  cudaStream_t st);
+// directed entries of a pair list: (B<-A) and (A<-B), self pairs once.
+void pairs_to_directed(const int2* pairs, int64_t npairs, int nb, uint64_t* keys,
+                       unsigned long long* count, cudaStream_t st);
+// CSR offsets (nnodes + 1) of sorted directed keys.
+void directed_offsets(const uint64_t* keys, int64_t nkeys, int nb, int nnodes, uint32_t* off,
+                      cudaStream_t st);
+
+// ---------------------------------------------------------- expansions.cu
+void upload_expansion_tables(const HostTables& h);
+// FP64 hat multipoles: P2M at leaves, M2M level by level; P_k per node.
+void upward_pass(const TreeView& t, const int* h_level_start, int p, const double* xs,
+                 const double* ys, const double* zs, const double* ms, const double* zc,
+                 const double* r, double* mult, double* Pk, const DevTables& tb, cudaStream_t st);
+void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStream_t st);
+// L2L level by level (FP64 or FP32 locals).
+void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const double* zc,
+                       const double* r, double* loc, const DevTables& tb, cudaStream_t st);
+void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const double* zc,
+                       const double* r, float* loc, cudaStream_t st);
+
+// ----------------------------------------------------------------- m2l.cu
+void upload_m2l_tables(const HostTables& h, const double* swap_cos, const double* swap_sin);
+// Rotation-accelerated M2L (Sec. 2.4), gathered per target over the sorted
+// directed list; writes the locals of every node (zero without sources).
+void m2l_f64(int nnodes, int p, const uint64_t* keys, const uint32_t* off, int nb,
+             const double* mult, const double* zc, const double* r, double* loc,
+             const DevTables& tb, cudaStream_t st);
+void m2l_f32(int nnodes, int p, const uint64_t* keys, const uint32_t* off, int nb,
+             const float* mult, const double* zc, const double* r, float* loc, cudaStream_t st);
+
+// ----------------------------------------------------------------- p2p.cu
+void upload_leaf_tables(const HostTables& h);
+// Leaf evaluation: L2P of the leaf's local expansion plus P2P over its
+// source leaves; writes G-scaled results to the caller's arrays via perm.
+struct LeafArgs {
+    TreeView t;
+    int p;
+    double G;
+    const double *xs, *ys, *zs, *ms;
+    const double *zc, *r;
+    const uint64_t* p2p_keys;
+    const uint32_t* p2p_off;
+    int nb;
+    const uint32_t* perm;
+    double *ax, *ay, *az, *pot;
+    const void* loc;   // FP64 or FP32 locals
+    const float4* prel;  // leaf-relative FP32 bodies (mixed)
+    DevTables tb;
+};
+void leaf_eval_f64(const LeafArgs& a, cudaStream_t st);
+void leaf_eval_f32(const LeafArgs& a, cudaStream_t st);
+void count_p2p_interactions(const uint64_t* keys, int64_t nk, int nb, const int* begin, const int* end,
+                            unsigned long long* out, cudaStream_t st);
+void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, const double* zs,
+                       const double* ms, const double* zc, float4* prel, cudaStream_t st);
+void direct_sum_f64(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                    double G, int64_t ntgt, const int64_t* tgt, double* ax, double* ay, double* az,
+                    double* pot, cudaStream_t st);
+
+// hat scale of a cell: its size r, or a tiny positive stand-in for r = 0
+__host__ __device__ inline double hat_scale(double r) { return r > 0.0 ? r : 1e-30; }
+
+}  // namespace gbfmm

@@ -1,0 +1,153 @@
+// Stable LSD radix sort of 64-bit keys with optional 32-bit payloads.
+//
+// Three kernels per 8-bit digit: a per-tile histogram, one exclusive scan of
+// the digit-major histogram table, and a scatter that ranks each key among
+// the earlier keys of its tile with the same digit (warp match + per-warp
+// digit counters), so equal keys keep their order.
+#include "gbfmm_internal.cuh"
+
+namespace gbfmm {
+
+namespace {
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;                   // keys per thread
+constexpr int kTile = kThreads * kItems;     // 4096 keys per block
+constexpr int kWarpItems = kTile / kWarps;   // 512 contiguous keys per warp
+
+__global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ keys, int64_t n,
+                                                   int shift, uint32_t* __restrict__ hist,
+                                                   int nblocks) {
+    __shared__ uint32_t h[256];
+    for (int i = threadIdx.x; i < 256; i += kThreads) h[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+#pragma unroll 4
+    for (int k = 0; k < kItems; ++k) {
+        int64_t i = base + (int64_t)k * kThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += kThreads) hist[(int64_t)d * nblocks + blockIdx.x] = h[d];
+}
+
+__global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict__ kin,
+                                                      const uint32_t* __restrict__ vin,
+                                                      uint64_t* __restrict__ kout,
+                                                      uint32_t* __restrict__ vout, int64_t n,
+                                                      int shift, const uint32_t* __restrict__ offs,
+                                                      int nblocks) {
+    __shared__ uint32_t wcount[kWarps][256];
+    __shared__ uint32_t boff[256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&wcount[0][0])[i] = 0;
+    for (int d = threadIdx.x; d < 256; d += kThreads) boff[d] = offs[(int64_t)d * nblocks + blockIdx.x];
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)warp * kWarpItems;
+    uint64_t key[kItems];
+    uint32_t val[kItems], rank[kItems], dig[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        const bool valid = i < n;
+        key[r] = valid ? kin[i] : 0ull;
+        val[r] = (valid && vin) ? vin[i] : 0u;
+        const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 255u : 0xFFFFFFFFu;
+        dig[r] = d;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = valid ? wcount[warp][d] : 0u;
+        rank[r] = before + __popc(peers & ((1u << lane) - 1u));
+        __syncwarp();
+        if (valid && lane == 31 - __clz(peers)) wcount[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;  // kThreads == 256 digits
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t t = wcount[w][d];
+            wcount[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        if (i < n) {
+            const uint32_t d = dig[r];
+            const uint32_t pos = boff[d] + wcount[warp][d] + rank[r];
+            kout[pos] = key[r];
+            if (vout) vout[pos] = val[r];
+        }
+    }
+}
+
+// Single-block exclusive scan: each of 1024 threads owns a contiguous chunk.
+__global__ void __launch_bounds__(1024) k_scan(uint32_t* data, int64_t count, uint32_t* total) {
+    __shared__ uint32_t warp_sums[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t chunk = (count + 1023) / 1024;
+    const int64_t lo = (int64_t)tid * chunk;
+    const int64_t hi = lo + chunk < count ? lo + chunk : count;
+    uint32_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += data[i];
+    uint32_t incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t ws = warp_sums[lane];
+        uint32_t wi = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += v;
+        }
+        warp_sums[lane] = wi - ws;
+        if (lane == 31 && total) *total = wi;
+    }
+    __syncthreads();
+    uint32_t run = warp_sums[warp] + incl - s;
+    for (int64_t i = lo; i < hi; ++i) {
+        const uint32_t v = data[i];
+        data[i] = run;
+        run += v;
+    }
+}
+}  // namespace
+
+size_t radix_hist_words(int64_t n) {
+    const int64_t nb = (n + kTile - 1) / kTile;
+    return (size_t)(256 * (nb > 0 ? nb : 1) + 1);
+}
+
+void scan_exclusive_u32(uint32_t* data, int64_t count, uint32_t* total, cudaStream_t st) {
+    (k_scan<<<1, 1024, 0, st>>>(data, count, total), note_launch());
+}
+
+int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bits,
+               uint32_t* hist, cudaStream_t st) {
+    if (n <= 1 || bits <= 0) return 0;
+    const int nblocks = (int)((n + kTile - 1) / kTile);
+    int cur = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
+        uint64_t* ki = cur ? k1 : k0;
+        uint32_t* vi = cur ? v1 : v0;
+        uint64_t* ko = cur ? k0 : k1;
+        uint32_t* vo = cur ? v0 : v1;
+        (k_hist<<<nblocks, kThreads, 0, st>>>(ki, n, shift, hist, nblocks), note_launch());
+        (k_scan<<<1, 1024, 0, st>>>(hist, (int64_t)256 * nblocks, nullptr), note_launch());
+        (k_scatter<<<nblocks, kThreads, 0, st>>>(ki, vi, ko, vo, n, shift, hist, nblocks), note_launch());
+        cur ^= 1;
+    }
+    return cur;
+}
+
+}  // namespace gbfmm

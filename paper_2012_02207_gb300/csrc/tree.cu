@@ -1,0 +1,385 @@
+// Bounding cube, Morton keys, octree and cell geometry.
+//
+// Compiled with -fmad=false: every floating-point operation here is one IEEE
+// operation in program order (no fused multiply-add), so the centres, sizes
+// and keys are exactly those of a plain sequential evaluation of the same
+// formulas.
+//
+// Octree (Fig. 1, Sec. 2.1; readings R1, R2): a node is split while it holds
+// more than leaf_size bodies and is above level 21; empty children are
+// omitted; nodes are numbered level by level, in key order inside a level.
+// The build needs no per-level loop: with lcp_i the number of leading 3-bit
+// digits shared by keys i-1 and i, and D_i the deepest level at which some
+// window of leaf_size+1 consecutive keys containing i shares its prefix, a
+// node of level L starts at body i exactly when lcp_i < L <= min(D_i+1, 21)
+// (the root at i = 0, L = 0). Counting those starts per chunk of bodies and
+// scanning the (level, chunk) table gives every node its index directly.
+#include "gbfmm_internal.cuh"
+
+namespace gbfmm {
+
+namespace {
+constexpr int kChunk = 256;  // bodies per thread in the node enumeration
+
+__global__ void k_bbox_partial(const double* __restrict__ x, const double* __restrict__ y,
+                               const double* __restrict__ z, const double* __restrict__ m,
+                               int64_t n, double* __restrict__ part, unsigned* err) {
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v[3] = {x[i], y[i], z[i]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (!isfinite(v[d])) bad = true;
+            mn[d] = fmin(mn[d], v[d]);
+            mx[d] = fmax(mx[d], v[d]);
+        }
+        const double mi = m[i];
+        if (!(mi > 0.0) || !isfinite(mi)) bad = true;
+    }
+    __shared__ double s[6][256];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        s[d][threadIdx.x] = mn[d];
+        s[3 + d][threadIdx.x] = mx[d];
+    }
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                s[d][threadIdx.x] = fmin(s[d][threadIdx.x], s[d][threadIdx.x + w]);
+                s[3 + d][threadIdx.x] = fmax(s[3 + d][threadIdx.x], s[3 + d][threadIdx.x + w]);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) part[6 * blockIdx.x + threadIdx.x] = s[threadIdx.x][0];
+    if (bad) atomicOr(err, kErrNonfinite);
+}
+
+// Cube (reading R1): centre c = (min+max)/2 per axis, half-size h = the
+// largest (max-min)/2 (h = 1 if all bodies coincide, e.g. n = 1).
+__global__ void k_bbox_final(const double* __restrict__ part, int nparts, DevScalars* ds) {
+    if (threadIdx.x != 0) return;
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nparts; ++b)
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fmin(mn[d], part[6 * b + d]);
+            mx[d] = fmax(mx[d], part[6 * b + 3 + d]);
+        }
+    double h = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        ds->box[d] = 0.5 * (mn[d] + mx[d]);
+        const double hd = 0.5 * (mx[d] - mn[d]);
+        if (hd > h) h = hd;
+    }
+    if (h == 0.0) h = 1.0;
+    ds->box[3] = h;
+    for (int d = 0; d < 3; ++d) ds->box[4 + d] = ds->box[d] - h;
+    ds->box[7] = 2.0 * h;
+}
+
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {  // 21 bits -> every third bit
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t quantise(double v, double lo, double size) {
+    const double t = (v - lo) / size;
+    double f = floor(t * 2097152.0);
+    f = f < 0.0 ? 0.0 : (f > 2097151.0 ? 2097151.0 : f);
+    return (uint64_t)f;
+}
+
+// Morton key: x in the high bit of each 3-bit digit, then y, then z.
+__global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
+                       const double* __restrict__ z, int64_t n, const DevScalars* __restrict__ ds,
+                       uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double size = ds->box[7];
+    const uint64_t qx = quantise(x[i], ds->box[4], size);
+    const uint64_t qy = quantise(y[i], ds->box[5], size);
+    const uint64_t qz = quantise(z[i], ds->box[6], size);
+    keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    idx[i] = (uint32_t)i;
+}
+
+__global__ void k_gather(const double* __restrict__ x, const double* __restrict__ y,
+                         const double* __restrict__ z, const double* __restrict__ m,
+                         const uint32_t* __restrict__ perm, int64_t n,
+                         const DevScalars* __restrict__ ds, double* __restrict__ xs,
+                         double* __restrict__ ys, double* __restrict__ zs, double* __restrict__ ms,
+                         float4* __restrict__ xf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    const double a = x[j], b = y[j], c = z[j], w = m[j];
+    xs[i] = a; ys[i] = b; zs[i] = c; ms[i] = w;
+    xf[i] = make_float4((float)(a - ds->box[0]), (float)(b - ds->box[1]), (float)(c - ds->box[2]),
+                        (float)w);
+}
+
+// lcp_i (levels shared by keys i-1 and i) and the coincident-body check.
+__global__ void k_lcp(const uint64_t* __restrict__ keys, const double* __restrict__ xs,
+                      const double* __restrict__ ys, const double* __restrict__ zs, int64_t n,
+                      uint8_t* __restrict__ lcp, unsigned* err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (i == 0) { lcp[0] = 0; return; }
+    const uint64_t k = keys[i];
+    const uint64_t d = k ^ keys[i - 1];
+    lcp[i] = d ? (uint8_t)((__clzll((long long)d) - 1) / 3) : (uint8_t)kMaxLevel;
+    if (d == 0) {
+        // equal keys: compare with the earlier bodies of the run (bounded)
+        const double a = xs[i], b = ys[i], c = zs[i];
+        int steps = 0;
+        for (int64_t j = i - 1; j >= 0 && keys[j] == k && steps < 4096; --j, ++steps)
+            if (xs[j] == a && ys[j] == b && zs[j] == c) { atomicOr(err, kErrCoincident); break; }
+    }
+}
+
+// W_a = min(lcp[a+1 .. a+leaf]) for a in [0, n-1-leaf].
+__global__ void k_window_min(const uint8_t* __restrict__ lcp, int64_t n, int leaf,
+                             uint8_t* __restrict__ win) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a > n - 1 - leaf) return;
+    uint8_t w = kMaxLevel;
+    for (int k = 1; k <= leaf; ++k) { const uint8_t v = lcp[a + k]; w = v < w ? v : w; }
+    win[a] = w;
+}
+
+// hi_i = min(D_i + 1, 21) with D_i the max of W over the windows holding i.
+__global__ void k_window_max(const uint8_t* __restrict__ win, int64_t n, int leaf,
+                             uint8_t* __restrict__ hi) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (n <= leaf) { hi[i] = 0; return; }
+    const int64_t a0 = i - leaf > 0 ? i - leaf : 0;
+    const int64_t a1 = i < n - 1 - leaf ? i : n - 1 - leaf;
+    int d = 0;
+    for (int64_t a = a0; a <= a1; ++a) d = win[a] > d ? win[a] : d;
+    hi[i] = (uint8_t)(d + 1 < kMaxLevel ? d + 1 : kMaxLevel);
+}
+
+__device__ __forceinline__ int start_lo(const uint8_t* lcp, int64_t i) { return i == 0 ? -1 : (int)lcp[i]; }
+
+// per (level, chunk) node-start counts, level-major
+__global__ void k_level_count(const uint8_t* __restrict__ lcp, const uint8_t* __restrict__ hi,
+                              int64_t n, int nchunks, uint32_t* __restrict__ cnt) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    uint32_t local[kMaxLevel + 1];
+#pragma unroll
+    for (int L = 0; L <= kMaxLevel; ++L) local[L] = 0;
+    const int64_t b = (int64_t)c * kChunk;
+    const int64_t e = b + kChunk < n ? b + kChunk : n;
+    for (int64_t i = b; i < e; ++i) {
+        const int lo = start_lo(lcp, i), h = hi[i];
+#pragma unroll
+        for (int L = 0; L <= kMaxLevel; ++L) local[L] += (L > lo && L <= h) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int L = 0; L <= kMaxLevel; ++L) cnt[(int64_t)L * nchunks + c] = local[L];
+}
+
+__global__ void k_level_emit(const uint8_t* __restrict__ lcp, const uint8_t* __restrict__ hi,
+                             int64_t n, int nchunks, const uint32_t* __restrict__ off,
+                             int* __restrict__ level, int* __restrict__ begin, int64_t node_cap,
+                             unsigned* err) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    uint32_t next[kMaxLevel + 1];
+#pragma unroll
+    for (int L = 0; L <= kMaxLevel; ++L) next[L] = off[(int64_t)L * nchunks + c];
+    const int64_t b = (int64_t)c * kChunk;
+    const int64_t e = b + kChunk < n ? b + kChunk : n;
+    for (int64_t i = b; i < e; ++i) {
+        const int lo = start_lo(lcp, i), h = hi[i];
+#pragma unroll
+        for (int L = 0; L <= kMaxLevel; ++L) {
+            if (L > lo && L <= h) {
+                const uint32_t k = next[L]++;
+                if ((int64_t)k < node_cap) { level[k] = L; begin[k] = (int)i; }
+                else atomicOr(err, kErrCapacity);
+            }
+        }
+    }
+}
+
+__global__ void k_level_starts(const uint32_t* __restrict__ off, int nchunks, const uint32_t* total,
+                               DevScalars* ds) {
+    const int L = threadIdx.x;
+    if (L <= kMaxLevel) ds->level_start[L] = (int)off[(int64_t)L * nchunks];
+    if (L == 0) {
+        ds->level_start[kMaxLevel + 1] = (int)*total;
+        ds->nnodes = (int)*total;
+    }
+}
+
+// end, parent and children of every node by binary searches.
+__global__ void k_finalize(const uint64_t* __restrict__ keys, int64_t n, int leaf, int nnodes,
+                           const DevScalars* __restrict__ ds, const int* __restrict__ level,
+                           const int* __restrict__ begin, int* __restrict__ end,
+                           int* __restrict__ parent, int* __restrict__ first_child,
+                           int* __restrict__ nchild) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnodes) return;
+    const int L = level[k];
+    const int b = begin[k];
+    int e = (int)n;
+    if (L > 0) {
+        const int shift = 3 * (kMaxLevel - L);
+        const uint64_t pre = keys[b] >> shift;
+        int lo = b + 1, hi = (int)n;  // first index with a larger prefix
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((keys[mid] >> shift) > pre) hi = mid; else lo = mid + 1;
+        }
+        e = lo;
+        int plo = ds->level_start[L - 1], phi = ds->level_start[L];  // last parent begin <= b
+        while (phi - plo > 1) {
+            const int mid = (plo + phi) >> 1;
+            if (begin[mid] <= b) plo = mid; else phi = mid;
+        }
+        parent[k] = plo;
+    } else {
+        parent[k] = -1;
+    }
+    end[k] = e;
+    if (e - b > leaf && L < kMaxLevel) {
+        const int c0 = ds->level_start[L + 1], c1 = ds->level_start[L + 2];
+        int lo = c0, hi = c1;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (begin[mid] < b) lo = mid + 1; else hi = mid; }
+        const int f = lo;
+        hi = c1;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (begin[mid] < e) lo = mid + 1; else hi = mid; }
+        first_child[k] = f;
+        nchild[k] = lo - f;
+    } else {
+        first_child[k] = -1;
+        nchild[k] = 0;
+    }
+}
+
+// Leaf geometry: sums over the leaf's bodies in sorted order.
+__global__ void k_geometry_leaves(TreeView t, const double* __restrict__ xs,
+                                  const double* __restrict__ ys, const double* __restrict__ zs,
+                                  const double* __restrict__ ms, double* __restrict__ M,
+                                  double* __restrict__ S, double* __restrict__ zc,
+                                  double* __restrict__ r) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= t.nnodes || t.nchild[k] != 0) return;
+    double Mk = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+    const int b = t.begin[k], e = t.end[k];
+    for (int i = b; i < e; ++i) {
+        const double mi = ms[i];
+        Mk = Mk + mi;
+        Sx = Sx + mi * xs[i];
+        Sy = Sy + mi * ys[i];
+        Sz = Sz + mi * zs[i];
+    }
+    const double zx = Sx / Mk, zy = Sy / Mk, zz = Sz / Mk;
+    double rr = 0.0;
+    for (int i = b; i < e; ++i) {
+        const double dx = xs[i] - zx, dy = ys[i] - zy, dz = zs[i] - zz;
+        const double d = sqrt(dx * dx + dy * dy + dz * dz);
+        if (d > rr) rr = d;
+    }
+    M[k] = Mk;
+    S[3 * k] = Sx; S[3 * k + 1] = Sy; S[3 * k + 2] = Sz;
+    zc[3 * k] = zx; zc[3 * k + 1] = zy; zc[3 * k + 2] = zz;
+    r[k] = rr;
+}
+
+// Internal geometry of one level: sums over children in order.
+__global__ void k_geometry_internal(TreeView t, int k0, int k1, double* __restrict__ M,
+                                    double* __restrict__ S, double* __restrict__ zc,
+                                    double* __restrict__ r) {
+    const int k = k0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= k1 || t.nchild[k] == 0) return;
+    const int c0 = t.first_child[k], c1 = c0 + t.nchild[k];
+    double Mk = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+    for (int c = c0; c < c1; ++c) {
+        Mk = Mk + M[c];
+        Sx = Sx + S[3 * c];
+        Sy = Sy + S[3 * c + 1];
+        Sz = Sz + S[3 * c + 2];
+    }
+    const double zx = Sx / Mk, zy = Sy / Mk, zz = Sz / Mk;
+    double rr = 0.0;
+    for (int c = c0; c < c1; ++c) {
+        const double dx = zc[3 * c] - zx, dy = zc[3 * c + 1] - zy, dz = zc[3 * c + 2] - zz;
+        const double d = sqrt(dx * dx + dy * dy + dz * dz) + r[c];
+        if (d > rr) rr = d;
+    }
+    M[k] = Mk;
+    S[3 * k] = Sx; S[3 * k + 1] = Sy; S[3 * k + 2] = Sz;
+    zc[3 * k] = zx; zc[3 * k + 1] = zy; zc[3 * k + 2] = zz;
+    r[k] = rr;
+}
+
+inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+}  // namespace
+
+int tree_nchunks(int64_t n) { return (int)((n + kChunk - 1) / kChunk); }
+
+void tree_build_count(TreeBuffers& b, int* sorted_in_1, cudaStream_t st) {
+    const int64_t n = b.n;
+    const int nbb = 152 * 2;
+    (k_bbox_partial<<<nbb, 256, 0, st>>>(b.x, b.y, b.z, b.m, n, b.bbox_part, &b.ds->err), note_launch());
+    (k_bbox_final<<<1, 32, 0, st>>>(b.bbox_part, nbb, b.ds), note_launch());
+    (k_keys<<<blocks_for(n, 256), 256, 0, st>>>(b.x, b.y, b.z, n, b.ds, b.k0, b.v0), note_launch());
+    const int in1 = radix_sort(b.k0, b.v0, b.k1, b.v1, n, 63, b.hist, st);
+    *sorted_in_1 = in1;
+    const uint64_t* keys = in1 ? b.k1 : b.k0;
+    const uint32_t* perm = in1 ? b.v1 : b.v0;
+    (k_gather<<<blocks_for(n, 256), 256, 0, st>>>(b.x, b.y, b.z, b.m, perm, n, b.ds, b.xs, b.ys, b.zs,
+                                                 b.ms, b.xf), note_launch());
+    (k_lcp<<<blocks_for(n, 256), 256, 0, st>>>(keys, b.xs, b.ys, b.zs, n, b.lcp, &b.ds->err), note_launch());
+    if (n > b.leaf_size)
+        (k_window_min<<<blocks_for(n - b.leaf_size, 256), 256, 0, st>>>(b.lcp, n, b.leaf_size, b.win), note_launch());
+    (k_window_max<<<blocks_for(n, 256), 256, 0, st>>>(b.win, n, b.leaf_size, b.hi), note_launch());
+    const int nchunks = tree_nchunks(n);
+    (k_level_count<<<blocks_for(nchunks, 128), 128, 0, st>>>(b.lcp, b.hi, n, nchunks, b.chunk_cnt), note_launch());
+    const int64_t cells = (int64_t)(kMaxLevel + 1) * nchunks;
+    scan_exclusive_u32(b.chunk_cnt, cells, b.chunk_cnt + cells, st);
+}
+
+void tree_build_emit(TreeBuffers& b, cudaStream_t st) {
+    const int64_t n = b.n;
+    const int nchunks = tree_nchunks(n);
+    const int64_t cells = (int64_t)(kMaxLevel + 1) * nchunks;
+    (k_level_emit<<<blocks_for(nchunks, 128), 128, 0, st>>>(b.lcp, b.hi, n, nchunks, b.chunk_cnt,
+                                                           b.level, b.begin, b.node_cap, &b.ds->err), note_launch());
+    (k_level_starts<<<1, 32, 0, st>>>(b.chunk_cnt, nchunks, b.chunk_cnt + cells, b.ds), note_launch());
+}
+
+void tree_build_phase2(TreeBuffers& b, const uint64_t* keys, int nnodes, const int* h_level_start,
+                       int nlevels, cudaStream_t st) {
+    (void)h_level_start;
+    (void)nlevels;
+    (k_finalize<<<blocks_for(nnodes, 128), 128, 0, st>>>(keys, b.n, b.leaf_size, nnodes, b.ds, b.level,
+                                                        b.begin, b.end, b.parent, b.first_child,
+                                                        b.nchild), note_launch());
+}
+
+void cell_geometry(const TreeView& t, const double* xs, const double* ys, const double* zs,
+                   const double* ms, const int* h_level_start, double* M, double* S, double* zc,
+                   double* r, cudaStream_t st) {
+    (k_geometry_leaves<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, xs, ys, zs, ms, M, S, zc, r), note_launch());
+    for (int L = t.nlevels - 2; L >= 0; --L) {
+        const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
+        if (k1 > k0)
+            (k_geometry_internal<<<blocks_for(k1 - k0, 128), 128, 0, st>>>(t, k0, k1, M, S, zc, r), note_launch());
+    }
+}
+
+}  // namespace gbfmm

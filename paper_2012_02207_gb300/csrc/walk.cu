@@ -1,0 +1,309 @@
+// Dual-tree walks and the scalar-force estimate.
+//
+// Compiled with -fmad=false: the MAC and the estimate f are evaluated with
+// one IEEE operation per source operation, in program order, so the
+// decisions are a plain function of the cell data.
+//
+// The walk (Sec. 2.1; reading R9) runs level-synchronously: each launch
+// classifies every pair of the current frontier and appends, with
+// warp-aggregated atomics, the accepted pairs, the leaf pairs and the child
+// pairs of the next frontier. The order of the lists is therefore not fixed;
+// everything downstream sorts them by (target, source) first.
+#include "gbfmm_internal.cuh"
+
+namespace gbfmm {
+
+namespace {
+
+struct WalkCells {
+    const int* nchild;
+    const int* first_child;
+    const double* zc;
+    const double* r;
+    const double* P;
+    const float* fmin;
+    const double* binom;  // C(p, k), k = 0..p
+    int p;
+    double eps;
+};
+
+// E_{A->B} M_A / r^2 of Sec. 2.3 (reading R8), Horner over k ascending.
+__device__ double mac_lhs(const WalkCells& c, int a, double ra, double rb, double r, double r2) {
+    const double sum = ra + rb;
+    const double pre = (sum > 0.0) ? 8.0 * (ra > rb ? ra : rb) / sum : 4.0;
+    const double* Pa = c.P + (size_t)(c.p + 1) * a;
+    double h = 0.0;
+    for (int k = 0; k <= c.p; ++k) h = h * rb + c.binom[k] * Pa[k];
+    double rp = 1.0;
+    for (int k = 0; k < c.p; ++k) rp = rp * r;
+    return pre * h / (rp * r2);
+}
+
+// Append cnt items per lane to a list; returns the lane's first slot. All
+// 32 lanes of the warp must call it.
+__device__ __forceinline__ unsigned long long warp_alloc(unsigned long long* counter, unsigned cnt) {
+    const int lane = threadIdx.x & 31;
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + (incl - cnt);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_walk_step(WalkCells c, const int2* __restrict__ fin,
+                                                   const unsigned long long* cnt_in,
+                                                   int2* __restrict__ fout,
+                                                   unsigned long long* cnt_out, int64_t cap_out,
+                                                   int2* __restrict__ acc_list,
+                                                   unsigned long long* cnt_acc, int64_t cap_acc,
+                                                   int2* __restrict__ leaf_list,
+                                                   unsigned long long* cnt_leaf, int64_t cap_leaf,
+                                                   unsigned* err) {
+    const int64_t nin_raw = (int64_t)*cnt_in;
+    const int64_t nin = nin_raw < cap_out ? nin_raw : cap_out;  // both frontiers hold cap_out pairs
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp0 * 32; base < nin; base += nwarps * 32) {
+        const int64_t q = base + lane;
+        int a = 0, b = 0;
+        unsigned n_next = 0, n_acc = 0, n_leaf = 0;
+        int split_kind = 0;  // 1: self children pairs, 2: split a, 3: split b
+        if (q < nin) {
+            const int2 pr = fin[q];
+            a = pr.x;
+            b = pr.y;
+            const int nca = c.nchild[a], ncb = c.nchild[b];
+            if (a == b) {
+                if (nca == 0) n_leaf = 1;
+                else { split_kind = 1; n_next = (unsigned)(nca * (nca + 1) / 2); }
+            } else {
+                const double* za = c.zc + 3 * a;
+                const double* zb = c.zc + 3 * b;
+                const double dx = zb[0] - za[0], dy = zb[1] - za[1], dz = zb[2] - za[2];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                const double r = sqrt(r2);
+                const double ra = c.r[a], rb = c.r[b];
+                bool accept = ra + rb < r;  // theta = (r_A + r_B)/r < 1 (reading R6)
+                if (MODE == 1 && accept) {
+                    const double lab = mac_lhs(c, a, ra, rb, r, r2);
+                    const double lba = mac_lhs(c, b, rb, ra, r, r2);
+                    accept = lab < c.eps * (double)c.fmin[b] && lba < c.eps * (double)c.fmin[a];
+                }
+                if (accept) n_acc = 1;
+                else if (nca == 0 && ncb == 0) n_leaf = 1;
+                else {
+                    const bool split_a = (ncb == 0) ? true : ((nca == 0) ? false : (ra >= rb));
+                    split_kind = split_a ? 2 : 3;
+                    n_next = (unsigned)(split_a ? nca : ncb);
+                }
+            }
+        }
+        const unsigned long long so = warp_alloc(cnt_out, n_next);
+        const unsigned long long sa = warp_alloc(cnt_acc, n_acc);
+        const unsigned long long sl = warp_alloc(cnt_leaf, n_leaf);
+        if (n_acc) {
+            if ((int64_t)sa < cap_acc) acc_list[sa] = make_int2(a, b); else atomicOr(err, kErrCapacity);
+        }
+        if (n_leaf) {
+            if ((int64_t)sl < cap_leaf) leaf_list[sl] = make_int2(a, b); else atomicOr(err, kErrCapacity);
+        }
+        if (n_next) {
+            if ((int64_t)(so + n_next) > cap_out) {
+                atomicOr(err, kErrCapacity);
+            } else {
+                unsigned long long o = so;
+                if (split_kind == 1) {
+                    const int c0 = c.first_child[a], nc = c.nchild[a];
+                    for (int i = 0; i < nc; ++i)
+                        for (int j = i; j < nc; ++j) fout[o++] = make_int2(c0 + i, c0 + j);
+                } else if (split_kind == 2) {
+                    const int c0 = c.first_child[a], nc = c.nchild[a];
+                    for (int i = 0; i < nc; ++i) fout[o++] = make_int2(c0 + i, b);
+                } else {
+                    const int c0 = c.first_child[b], nc = c.nchild[b];
+                    for (int i = 0; i < nc; ++i) fout[o++] = make_int2(a, c0 + i);
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_walk_init(int2* f0, unsigned long long* cnt, unsigned long long* list_cnt,
+                            int iters, int mode) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) f0[0] = make_int2(0, 0);
+    if (i < iters) cnt[i] = (i == 0) ? 1ull : 0ull;
+    if (i < 2) list_cnt[2 * mode + i] = 0ull;
+}
+
+// directed keys target << nb | source
+__global__ void k_directed(const int2* __restrict__ pairs, int64_t np, int nb,
+                           uint64_t* __restrict__ keys, unsigned long long* count) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // two slots per pair; self pairs fill one and leave a marker the sort drops
+    if (q >= np) return;
+    const int2 pr = pairs[q];
+    const uint64_t a = (uint64_t)pr.x, b = (uint64_t)pr.y;
+    keys[2 * q] = (b << nb) | a;
+    keys[2 * q + 1] = (pr.x == pr.y) ? ~0ull : ((a << nb) | b);
+    if (pr.x == pr.y) atomicAdd(count, 1ull);
+}
+
+__global__ void k_offsets(const uint64_t* __restrict__ keys, int64_t nk, int nb, int nnodes,
+                          uint32_t* __restrict__ off) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > nk) return;
+    const int64_t t = (i < nk) ? (int64_t)(keys[i] >> nb) : (int64_t)nnodes;
+    const int64_t tp = (i > 0) ? (int64_t)(keys[i - 1] >> nb) : -1;
+    for (int64_t u = tp + 1; u <= t && u <= nnodes; ++u) off[u] = (uint32_t)i;
+}
+
+// far part of the estimate: per cell, M_A / r^2 summed over theta-partners in
+// ascending order, r^2 from the FP32-rounded centre offsets.
+__global__ void k_far_f(int nnodes, const double* __restrict__ zc, const double* __restrict__ M,
+                        const uint64_t* __restrict__ keys, const uint32_t* __restrict__ off, int nb,
+                        float* __restrict__ farf) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nnodes) return;
+    const uint64_t mask = (1ull << nb) - 1ull;
+    const double bx = zc[3 * b], by = zc[3 * b + 1], bz = zc[3 * b + 2];
+    float acc = 0.0f;
+    for (uint32_t q = off[b]; q < off[b + 1]; ++q) {
+        const int a = (int)(keys[q] & mask);
+        const float dx = (float)(zc[3 * a] - bx), dy = (float)(zc[3 * a + 1] - by),
+                    dz = (float)(zc[3 * a + 2] - bz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        acc = acc + (float)M[a] / r2;
+    }
+    farf[b] = acc;
+}
+
+// g(k) = g(parent) + far(k), accumulated from the root down the ancestor chain
+__global__ void k_push_down(TreeView t, const float* __restrict__ farf, float* __restrict__ g) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= t.nnodes) return;
+    int chain[kMaxLevel + 1];
+    int len = 0;
+    for (int a = k; a >= 0; a = t.parent[a]) chain[len++] = a;
+    float acc = farf[chain[len - 1]];
+    for (int i = len - 2; i >= 0; --i) acc = acc + farf[chain[i]];
+    g[k] = acc;
+}
+
+// near part per body: partner leaves ascending, their bodies in order, j != i
+__global__ void k_near_f(TreeView t, const float4* __restrict__ xf, const uint64_t* __restrict__ keys,
+                         const uint32_t* __restrict__ off, int nb, const int* __restrict__ leaf_of,
+                         const float* __restrict__ g, float* __restrict__ f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= t.n) return;
+    const int b = leaf_of[i];
+    const uint64_t mask = (1ull << nb) - 1ull;
+    const float4 pi = xf[i];
+    float acc = 0.0f;
+    for (uint32_t q = off[b]; q < off[b + 1]; ++q) {
+        const int a = (int)(keys[q] & mask);
+        const int j0 = t.begin[a], j1 = t.end[a];
+        for (int j = j0; j < j1; ++j) {
+            if (j == i) continue;
+            const float4 pj = xf[j];
+            const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 > 0.0f) acc = acc + pj.w / r2;
+        }
+    }
+    f[i] = g[b] + acc;
+}
+
+__global__ void k_leaf_of(TreeView t, int* __restrict__ leaf_of) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= t.nnodes || t.nchild[k] != 0) return;
+    for (int i = t.begin[k]; i < t.end[k]; ++i) leaf_of[i] = k;
+}
+
+__global__ void k_fmin(TreeView t, const float* __restrict__ f, float* __restrict__ fmin) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= t.nnodes) return;
+    const int b = t.begin[k], e = t.end[k];
+    float mn = f[b];
+    for (int i = b + 1; i < e; ++i) mn = f[i] < mn ? f[i] : mn;
+    fmin[k] = mn;
+}
+
+inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+}  // namespace
+
+int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* r, const double* P,
+                   const float* fmin, int p, double eps, const double* binom_row, WalkBuffers& wb,
+                   DevScalars* ds, DevScalars* h_ds, cudaStream_t st) {
+    WalkCells c{t.nchild, t.first_child, zc, r, P, fmin, binom_row, p, eps};
+    (k_walk_init<<<1, 256, 0, st>>>(wb.front0, ds->cnt, ds->list_cnt, kMaxWalkIters + 2, mode), note_launch());
+    int2* acc_list = wb.out[mode == 0 ? 0 : 2];
+    int2* leaf_list = wb.out[mode == 0 ? 1 : 3];
+    const int64_t cap_acc = wb.out_cap[mode == 0 ? 0 : 2];
+    const int64_t cap_leaf = wb.out_cap[mode == 0 ? 1 : 3];
+    unsigned long long* cnt_acc = ds->list_cnt + (mode == 0 ? 0 : 2);
+    unsigned long long* cnt_leaf = ds->list_cnt + (mode == 0 ? 1 : 3);
+    const int grid = 152 * 8;
+    int it = 0;
+    const int kCheck = 6;
+    while (it < kMaxWalkIters) {
+        for (int s = 0; s < kCheck && it < kMaxWalkIters; ++s, ++it) {
+            int2* fi = (it & 1) ? wb.front1 : wb.front0;
+            int2* fo = (it & 1) ? wb.front0 : wb.front1;
+            if (mode == 0)
+                (k_walk_step<0><<<grid, 256, 0, st>>>(c, fi, ds->cnt + it, fo, ds->cnt + it + 1,
+                                                     wb.front_cap, acc_list, cnt_acc, cap_acc,
+                                                     leaf_list, cnt_leaf, cap_leaf, &ds->err), note_launch());
+            else
+                (k_walk_step<1><<<grid, 256, 0, st>>>(c, fi, ds->cnt + it, fo, ds->cnt + it + 1,
+                                                     wb.front_cap, acc_list, cnt_acc, cap_acc,
+                                                     leaf_list, cnt_leaf, cap_leaf, &ds->err), note_launch());
+        }
+        unsigned long long nxt = 0;
+        unsigned err = 0;
+        if (cudaMemcpyAsync(&nxt, ds->cnt + it, sizeof(nxt), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&err, &ds->err, sizeof(err), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        if (err & kErrCapacity) return FMM_ERR_CAPACITY;
+        if (nxt == 0) break;
+    }
+    if (it >= kMaxWalkIters) return FMM_ERR_CAPACITY;
+    (void)h_ds;
+    return it;
+}
+
+void pairs_to_directed(const int2* pairs, int64_t npairs, int nb, uint64_t* keys,
+                       unsigned long long* count, cudaStream_t st) {
+    if (npairs > 0) (k_directed<<<blocks_for(npairs, 256), 256, 0, st>>>(pairs, npairs, nb, keys, count), note_launch());
+}
+
+void directed_offsets(const uint64_t* keys, int64_t nkeys, int nb, int nnodes, uint32_t* off,
+                      cudaStream_t st) {
+    (k_offsets<<<blocks_for(nkeys + 1, 256), 256, 0, st>>>(keys, nkeys, nb, nnodes, off), note_launch());
+}
+
+void scalar_force(const TreeView& t, const double* zc, const double* M, const float4* xf,
+                  const uint64_t* far_keys, const uint32_t* far_off, const uint64_t* near_keys,
+                  const uint32_t* near_off, int nb, float* farf, float* f, float* fmin,
+                  cudaStream_t st) {
+    // farf doubles as scratch: [0, nnodes) far sums, [nnodes, 2 nnodes) pushed-down g,
+    // and the leaf index of every body after that.
+    float* g = farf + t.nnodes;
+    int* leaf_of = reinterpret_cast<int*>(farf + 2 * (size_t)t.nnodes);
+    (k_far_f<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, zc, M, far_keys, far_off, nb, farf), note_launch());
+    (k_push_down<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, farf, g), note_launch());
+    (k_leaf_of<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, leaf_of), note_launch());
+    (k_near_f<<<blocks_for(t.n, 128), 128, 0, st>>>(t, xf, near_keys, near_off, nb, leaf_of, g, f), note_launch());
+    (k_fmin<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, f, fmin), note_launch());
+}
+
+}  // namespace gbfmm

@@ -1,0 +1,194 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bit-exact: Morton keys, sort permutation, octree, cell masses, centres and
+sizes, the FP32 scalar-force estimate and its per-cell minimum, and all four
+interaction lists (as sets of oriented pairs). Floating point: FP64 forces
+against the oracle FMM, mixed-precision forces against the oracle's FP64
+direct sum.
+"""
+import numpy as np
+import pytest
+
+import ics
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2012_02207_gb300 as gb  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def to_dev(pos, m):
+    cols = [torch.tensor(np.ascontiguousarray(pos[:, d]), dtype=torch.float64, device=DEV) for d in range(3)]
+    return cols + [torch.tensor(np.ascontiguousarray(m), dtype=torch.float64, device=DEV)]
+
+
+def solve(pos, m, **kw):
+    f = gb.FMM(**kw)
+    ax, ay, az, pot = f.solve(*to_dev(pos, m))
+    torch.cuda.synchronize()
+    acc = torch.stack([ax, ay, az], 1).cpu().numpy()
+    return f, acc, pot.cpu().numpy()
+
+
+def sorted_pairs(a):
+    a = np.asarray(a, dtype=np.int64)
+    if len(a) == 0:
+        return a.reshape(0, 2)
+    return a[np.lexsort((a[:, 1], a[:, 0]))]
+
+
+CASES = [(1, 64), (2, 64), (3, 64), (63, 64), (64, 64), (65, 64), (1000, 8), (4096, 64), (20000, 16)]
+
+
+@pytest.mark.parametrize("n,leaf", CASES)
+def test_tree_geometry_estimate_and_lists_bit_exact(n, leaf):
+    pos, _, m = ics.plummer(n, 500 + n)
+    if n >= 1000:
+        m = ics.kroupa_masses(n, 600 + n)
+    p, eps = 6, 1e-6
+    f, acc, pot = solve(pos, m, p=p, eps=eps, leaf_size=leaf, precision="fp64")
+    run = oracle.OracleRun(pos, m, p=p, eps=eps, leaf_size=leaf, stage=oracle.STAGE_LISTS)
+    ot, og = run.tree(), run.geometry()
+    gt, gg = f.export_tree(), f.export_geometry()
+    assert np.array_equal(gt["keys"], ot["keys"])
+    assert np.array_equal(gt["perm"], ot["perm"])
+    for k in ("level", "begin", "end", "parent", "first_child", "nchild"):
+        assert np.array_equal(gt[k], ot[k]), k
+    assert np.array_equal(gg["M"], og["M"])
+    assert np.array_equal(gg["z"], og["z"])
+    assert np.array_equal(gg["r"], og["r"])
+    assert np.array_equal(gg["f"], og["f"])
+    assert np.array_equal(gg["fmin"], og["fmin"])
+    scale = np.maximum(np.abs(og["P"]).max(axis=1, keepdims=True), 1e-300)
+    assert np.all(np.abs(gg["P"] - og["P"]) <= 1e-12 * scale)
+    for which in ("far", "near", "m2l", "p2p"):
+        assert np.array_equal(sorted_pairs(f.export_pairs(which)), sorted_pairs(run.pairs(which))), which
+
+
+@pytest.mark.parametrize("n,p,eps", [(4096, 8, 1e-7), (20000, 6, 1e-6), (20000, 10, 1e-8), (3000, 14, 1e-5), (2000, 20, 1e-9)])
+def test_fp64_forces_match_oracle_fmm(n, p, eps):
+    pos, _, m = ics.plummer(n, 7 + n + p)
+    _, acc, pot = solve(pos, m, p=p, eps=eps, precision="fp64")
+    oacc, opot = oracle.fmm(pos, m, p=p, eps=eps)
+    # per-body relative error; bodies near the centre have |a| << sum |a_j|, so
+    # the error is also measured against the scalar force estimate (reading R16)
+    run = oracle.OracleRun(pos, m, p=p, eps=eps, stage=oracle.STAGE_F)
+    fi = np.empty(n)
+    fi[run.tree()["perm"]] = run.geometry()["f"]
+    d = np.linalg.norm(acc - oacc, axis=1)
+    assert np.max(d / fi) <= 1e-12
+    assert np.max(d / np.linalg.norm(oacc, axis=1)) <= 1e-10
+    assert np.max(np.abs(pot - opot) / np.abs(opot)) <= 1e-12
+
+
+@pytest.mark.parametrize("n,p,eps", [(4096, 8, 1e-7), (30000, 10, 1e-7), (30000, 6, 1e-7), (30000, 14, 1e-7), (30000, 4, 3e-8), (30000, 12, 1e-7)])
+def test_mixed_precision_error_vs_direct(n, p, eps):
+    pos, _, _ = ics.plummer(n, 11)
+    m = ics.kroupa_masses(n, 12)
+    _, acc, pot = solve(pos, m, p=p, eps=eps, precision="mixed")
+    _, acc64, _ = solve(pos, m, p=p, eps=eps, precision="fp64")
+    dacc, dpot = oracle.direct(pos, m)
+    s_mixed = oracle.error_stats(acc, dacc)
+    s_fp64 = oracle.error_stats(acc64, dacc)
+    # FP32 terms add at most a few 1e-7 to the FP64 truncation error
+    assert s_mixed["rms"] <= s_fp64["rms"] + 5e-7, (s_mixed, s_fp64)
+    assert s_mixed["median"] <= s_fp64["median"] + 1e-7, (s_mixed, s_fp64)
+    assert np.max(np.abs(pot - dpot) / np.abs(dpot)) <= 1e-5
+
+
+def test_edge_cases():
+    f = gb.FMM(p=4, eps=1e-6, precision="mixed")
+    one = to_dev(np.array([[0.1, 0.2, 0.3]]), np.array([2.0]))
+    ax, ay, az, pot = f.solve(*one)
+    assert ax.item() == 0.0 and ay.item() == 0.0 and az.item() == 0.0 and pot.item() == 0.0
+    pos = np.array([[0.0, 0.0, 0.0], [1.0, 2.0, 2.0]])
+    for prec in ("mixed", "fp64"):
+        _, acc, pot = solve(pos, np.array([2.0, 3.0]), p=4, G=1.5, precision=prec)
+        assert np.allclose(acc[0], 1.5 * 3.0 * pos[1] / 27.0, rtol=1e-6)
+        assert np.allclose(acc[1], -1.5 * 2.0 * pos[1] / 27.0, rtol=1e-6)
+        assert np.allclose(pot, [-1.5, -1.0], rtol=1e-6)
+    with pytest.raises(gb.FmmError) as e:
+        f.solve(*to_dev(np.array([[0.0, 0, 0], [1.0, 0, 0], [0.0, 0, 0]]), np.ones(3)))
+    assert e.value.status == -5
+    with pytest.raises(gb.FmmError) as e:
+        f.solve(*to_dev(np.array([[0.0, 0, 0], [np.nan, 0, 0]]), np.ones(2)))
+    assert e.value.status == -4
+    with pytest.raises(gb.FmmError) as e:
+        f.solve(*to_dev(np.array([[0.0, 0, 0], [1.0, 0, 0]]), np.array([1.0, -1.0])))
+    assert e.value.status == -4
+    # the context stays usable after errors
+    _, acc, _ = solve(pos, np.array([2.0, 3.0]), p=4)
+    assert np.isfinite(acc).all()
+    empty = [torch.zeros(0, dtype=torch.float64, device=DEV) for _ in range(4)]
+    f.solve(*empty)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_deterministic_and_capacity_regrow(prec):
+    pos, _, m = ics.plummer(30000, 3)
+    f, a1, p1 = solve(pos, m, p=8, eps=1e-7, precision=prec)
+    d = to_dev(pos, m)
+    ax, ay, az, pot = f.solve(*d)
+    a2 = torch.stack([ax, ay, az], 1).cpu().numpy()
+    assert np.array_equal(a1, a2) and np.array_equal(p1, pot.cpu().numpy())
+    g, a3, p3 = solve(pos, m, p=8, eps=1e-7, precision=prec, fault_inject=1)
+    assert g.stats()["regrows"] > 0
+    assert np.array_equal(a1, a3) and np.array_equal(p1, p3)
+
+
+def test_host_entry_point_matches_device():
+    pos, _, m = ics.plummer(5000, 17)
+    f, acc, pot = solve(pos, m, p=8, eps=1e-7)
+    acc_h, pot_h = f.solve_host(pos, m)
+    assert np.array_equal(acc, acc_h) and np.array_equal(pot, pot_h)
+
+
+def test_batch_matches_separate_solves():
+    offsets, pos, m, sizes, _ = ics.ensemble(6, 9, log2n_lo=6, log2n_hi=12)
+    f = gb.FMM(p=8, eps=1e-7)
+    ax, ay, az, pot = f.solve_batch(offsets, *to_dev(pos, m))
+    acc = torch.stack([ax, ay, az], 1).cpu().numpy()
+    for c in range(len(sizes)):
+        sl = slice(offsets[c], offsets[c + 1])
+        _, a1, p1 = solve(pos[sl], m[sl], p=8, eps=1e-7)
+        assert np.array_equal(acc[sl], a1)
+        assert np.array_equal(pot.cpu().numpy()[sl], p1)
+
+
+def test_direct_kernel_matches_oracle_direct():
+    pos, _, m = ics.plummer(3000, 5)
+    f = gb.FMM()
+    tg = torch.tensor([0, 17, 999, 2999], dtype=torch.int64, device=DEV)
+    ax, ay, az, pot = f.direct(*to_dev(pos, m), targets=tg)
+    acc = torch.stack([ax, ay, az], 1).cpu().numpy()
+    oacc, opot = oracle.direct(pos, m, targets=tg.cpu().numpy())
+    assert np.allclose(acc, oacc, rtol=1e-13, atol=0)
+    assert np.allclose(pot.cpu().numpy(), opot, rtol=1e-13, atol=0)
+
+
+@pytest.mark.slow
+def test_full_size_mixed_solve_tree_lists_and_sampled_forces():
+    """N = 2^20 Kroupa Plummer sphere in the benchmark's configuration: the
+    tree and the lists are bit-exact against the oracle, and forces on a
+    sample of bodies match the FP64 direct sum."""
+    n, p, eps = 1 << 20, 10, 1e-7
+    pos, m = ics.config_inputs("kroupa1m")
+    f, acc, pot = solve(pos, m, p=p, eps=eps, precision="mixed")
+    run = oracle.OracleRun(pos, m, p=p, eps=eps, stage=oracle.STAGE_LISTS)
+    ot, gt = run.tree(), f.export_tree()
+    for k in ("keys", "perm", "level", "begin", "end", "parent", "first_child", "nchild"):
+        assert np.array_equal(gt[k], ot[k]), k
+    og, gg = run.geometry(), f.export_geometry()
+    assert np.array_equal(gg["f"], og["f"]) and np.array_equal(gg["fmin"], og["fmin"])
+    for which in ("m2l", "p2p"):
+        assert np.array_equal(sorted_pairs(f.export_pairs(which)), sorted_pairs(run.pairs(which))), which
+    sample = np.random.default_rng(0).choice(n, 2000, replace=False)
+    dacc, dpot = oracle.direct(pos, m, targets=sample)
+    s = oracle.error_stats(acc[sample], dacc)
+    assert s["median"] < 1e-7 and s["p99"] < 3e-6, s
