@@ -10,6 +10,7 @@
 // sizes); everything else stays on the device.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -58,7 +59,9 @@ struct fmm_ctx {
     Buf k0, k1, v0, v1, hist, xs, ys, zs, ms, xf, prel, lcp, win, hi, chunk, f, bbox;
     // per-node
     Buf level, begin, end, parent, first_child, nchild, M, S, zc, r, Pk, mult, mult32, loc, loc32,
-        fmin, fscratch;
+        fmin, fscratch, zhi, zlo;
+    // P2P work items
+    Buf item_first, slot_first, item_leaf, leaf_of, part_hi, part_lo, work;
     // walk and lists
     Buf front0, front1, lists[4], dkeys[4], dalt, doff[4], dcount;
     int64_t front_cap = 0, list_cap[4] = {0, 0, 0, 0};
@@ -166,7 +169,9 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
-// directed, sorted, CSR-indexed form of pair list `which`
+// directed, sorted, CSR-indexed form of pair list `which`: every unordered
+// pair (A, B) gives the keys B<<nb|A and A<<nb|B; a self pair gives one key
+// and an all-ones marker that sorts last and is ignored.
 int build_directed(fmm_ctx* ctx, int which, cudaStream_t st) {
     const int64_t np = ctx->npairs[which];
     const size_t keys_bytes = sizeof(uint64_t) * (size_t)(2 * np + 1);
@@ -175,20 +180,13 @@ int build_directed(fmm_ctx* ctx, int which, cudaStream_t st) {
     if ((rc = ensure(ctx, ctx->dalt, keys_bytes)) != FMM_OK) return rc;
     if ((rc = ensure(ctx, ctx->doff[which], sizeof(uint32_t) * (size_t)(ctx->nnodes + 2))) != FMM_OK) return rc;
     if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(2 * np + 1))) != FMM_OK) return rc;
-    CK(cudaMemsetAsync(ctx->dcount.ptr, 0, sizeof(unsigned long long), st));
     pairs_to_directed(as<int2>(ctx->lists[which]), np, ctx->nb, as<uint64_t>(ctx->dkeys[which]),
-                      as<unsigned long long>(ctx->dcount), st);
+                      as<unsigned long long>(ctx->dcount) + 2 + which, st);
     const int in1 = radix_sort(as<uint64_t>(ctx->dkeys[which]), nullptr, as<uint64_t>(ctx->dalt), nullptr,
                                2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st);
-    if (in1) {
-        CK(cudaMemcpyAsync(ctx->dkeys[which].ptr, ctx->dalt.ptr, sizeof(uint64_t) * (size_t)(2 * np),
-                           cudaMemcpyDeviceToDevice, st));
-    }
-    unsigned long long nself = 0;
-    CK(cudaMemcpyAsync(&nself, ctx->dcount.ptr, sizeof(nself), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    ctx->ndirected[which] = 2 * np - (int64_t)nself;
-    directed_offsets(as<uint64_t>(ctx->dkeys[which]), ctx->ndirected[which], ctx->nb, ctx->nnodes,
+    if (in1) std::swap(ctx->dkeys[which], ctx->dalt);
+    ctx->ndirected[which] = 2 * np;
+    directed_offsets(as<uint64_t>(ctx->dkeys[which]), 2 * np, ctx->nb, ctx->nnodes,
                      as<uint32_t>(ctx->doff[which]), st);
     return FMM_OK;
 }
@@ -196,7 +194,7 @@ int build_directed(fmm_ctx* ctx, int which, cudaStream_t st) {
 int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
     TreeView t = view(ctx);
     const int p = ctx->cfg.p;
-    for (int attempt = 0; attempt < 4; ++attempt) {
+    for (int attempt = 0; attempt < 12; ++attempt) {
         int rc;
         if ((rc = ensure(ctx, ctx->front0, sizeof(int2) * (size_t)ctx->front_cap)) != FMM_OK) return rc;
         if ((rc = ensure(ctx, ctx->front1, sizeof(int2) * (size_t)ctx->front_cap)) != FMM_OK) return rc;
@@ -217,9 +215,14 @@ int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
                                       as<float>(ctx->fmin), p, ctx->cfg.eps, binom_row, wb, ctx->ds,
                                       ctx->h_ds, st);
         if (it == FMM_ERR_CAPACITY) {
-            ctx->front_cap *= 4;
-            ctx->list_cap[2 * mode] *= 4;
-            ctx->list_cap[2 * mode + 1] *= 4;
+            // the counters kept counting past the capacity: grow to what was asked for
+            CK(cudaMemcpyAsync(ctx->h_ds, ctx->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            unsigned long long fmax = 0;
+            for (int i = 0; i < kMaxWalkIters + 2; ++i) fmax = ctx->h_ds->cnt[i] > fmax ? ctx->h_ds->cnt[i] : fmax;
+            ctx->front_cap = std::max<int64_t>(4 * ctx->front_cap, 2 * (int64_t)fmax);
+            for (int l = 2 * mode; l < 2 * mode + 2; ++l)
+                ctx->list_cap[l] = std::max<int64_t>(4 * ctx->list_cap[l], 2 * (int64_t)ctx->h_ds->list_cnt[l]);
             ctx->stats.regrows++;
             continue;
         }
@@ -301,7 +304,10 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
         (rc = ensure(ctx, ctx->M, 8 * K)) || (rc = ensure(ctx, ctx->S, 24 * K)) ||
         (rc = ensure(ctx, ctx->zc, 24 * K)) || (rc = ensure(ctx, ctx->r, 8 * K)) ||
         (rc = ensure(ctx, ctx->Pk, 8 * K * (p + 1))) || (rc = ensure(ctx, ctx->mult, 8 * K * nr)) ||
-        (rc = ensure(ctx, ctx->fmin, 4 * K)) || (rc = ensure(ctx, ctx->fscratch, 4 * (2 * K + N))))
+        (rc = ensure(ctx, ctx->fmin, 4 * K)) || (rc = ensure(ctx, ctx->fscratch, 4 * (2 * K + N))) ||
+        (rc = ensure(ctx, ctx->zhi, 16 * K)) || (rc = ensure(ctx, ctx->zlo, 16 * K)) ||
+        (rc = ensure(ctx, ctx->item_first, 4 * (K + 2))) || (rc = ensure(ctx, ctx->slot_first, 4 * (K + 2))) ||
+        (rc = ensure(ctx, ctx->leaf_of, 4 * N)) || (rc = ensure(ctx, ctx->work, 64)))
         return rc;
     if (mixed) {
         if ((rc = ensure(ctx, ctx->mult32, 4 * K * nr)) || (rc = ensure(ctx, ctx->loc32, 4 * K * nr))) return rc;
@@ -327,6 +333,7 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
     cell_geometry(t, as<double>(ctx->xs), as<double>(ctx->ys), as<double>(ctx->zs), as<double>(ctx->ms),
                   ctx->h_level_start, as<double>(ctx->M), as<double>(ctx->S), as<double>(ctx->zc),
                   as<double>(ctx->r), st);
+    node_centres_f32(nnodes, as<double>(ctx->zc), as<double>(ctx->r), as<float4>(ctx->zhi), as<float4>(ctx->zlo), st);
     CK(cudaEventRecord(ctx->ev[1], st));
     // ---- upward pass
     upward_pass(t, ctx->h_level_start, p, as<double>(ctx->xs), as<double>(ctx->ys), as<double>(ctx->zs),
@@ -345,17 +352,17 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
         }
     }
     if ((rc = ensure(ctx, ctx->dcount, 64))) return rc;
+    CK(cudaMemsetAsync(ctx->dcount.ptr, 0, 64, st));
     if ((rc = run_walk(ctx, 0, st))) return rc;
     if ((rc = build_directed(ctx, 0, st)) || (rc = build_directed(ctx, 1, st))) return rc;
     scalar_force(t, as<double>(ctx->zc), as<double>(ctx->M), as<float4>(ctx->xf), as<uint64_t>(ctx->dkeys[0]),
                  as<uint32_t>(ctx->doff[0]), as<uint64_t>(ctx->dkeys[1]), as<uint32_t>(ctx->doff[1]), ctx->nb,
-                 as<float>(ctx->fscratch), as<float>(ctx->f), as<float>(ctx->fmin), st);
+                 ctx->h_level_start, as<float>(ctx->fscratch), as<float>(ctx->f), as<float>(ctx->fmin), st);
     CK(cudaEventRecord(ctx->ev[3], st));
     // ---- error-controlled walk
     if ((rc = run_walk(ctx, 1, st))) return rc;
     if ((rc = build_directed(ctx, 2, st)) || (rc = build_directed(ctx, 3, st))) return rc;
-    CK(cudaMemsetAsync(as<unsigned long long>(ctx->dcount) + 1, 0, sizeof(unsigned long long), st));
-    count_p2p_interactions(as<uint64_t>(ctx->dkeys[3]), ctx->ndirected[3], ctx->nb, as<int>(ctx->begin),
+    count_p2p_interactions(as<uint64_t>(ctx->dkeys[3]), ctx->ndirected[3], ctx->nb, nnodes, as<int>(ctx->begin),
                            as<int>(ctx->end), as<unsigned long long>(ctx->dcount) + 1, st);
     CK(cudaEventRecord(ctx->ev[4], st));
     // ---- far field
@@ -363,7 +370,7 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
     const uint32_t* mo = as<uint32_t>(ctx->doff[2]);
     if (mixed && m2l32_supported(p)) {
         multipoles_to_f32(as<double>(ctx->mult), as<float>(ctx->mult32), (int64_t)(K * nr), st);
-        m2l_f32(nnodes, p, mk, mo, ctx->nb, as<float>(ctx->mult32), as<double>(ctx->zc), as<double>(ctx->r),
+        m2l_f32(nnodes, p, mk, mo, ctx->nb, as<float>(ctx->mult32), as<float4>(ctx->zhi), as<float4>(ctx->zlo),
                 as<float>(ctx->loc32), st);
     } else {
         m2l_f64(nnodes, p, mk, mo, ctx->nb, as<double>(ctx->mult), as<double>(ctx->zc), as<double>(ctx->r),
@@ -377,24 +384,38 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
         downward_pass_f64(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->loc),
                           ctx->tb, st);
     CK(cudaEventRecord(ctx->ev[6], st));
-    // ---- leaves
+    // ---- leaves: P2P work items, then L2P + partials per body
+    uint32_t* item_first = as<uint32_t>(ctx->item_first);
+    uint32_t* slot_first = as<uint32_t>(ctx->slot_first);
+    uint32_t* totals = as<uint32_t>(ctx->work) + 4;
+    leaf_items_plan(t, as<uint32_t>(ctx->doff[3]), item_first, slot_first, totals, st);
+    uint32_t htot[2] = {0, 0};
+    CK(cudaMemcpyAsync(htot, totals, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if ((rc = ensure(ctx, ctx->item_leaf, 4 * (size_t)(htot[0] + 1))) ||
+        (rc = ensure(ctx, ctx->part_hi, 16 * (size_t)(htot[1] + 1))) ||
+        (rc = ensure(ctx, ctx->part_lo, 16 * (size_t)(htot[1] + 1))))
+        return rc;
+    leaf_items_fill(t, item_first, as<int>(ctx->item_leaf), as<int>(ctx->leaf_of), st);
     LeafArgs la{};
     la.t = t; la.p = p; la.G = ctx->cfg.G;
     la.xs = as<double>(ctx->xs); la.ys = as<double>(ctx->ys); la.zs = as<double>(ctx->zs); la.ms = as<double>(ctx->ms);
     la.zc = as<double>(ctx->zc); la.r = as<double>(ctx->r);
+    la.zhi = as<float4>(ctx->zhi); la.zlo = as<float4>(ctx->zlo);
     la.p2p_keys = as<uint64_t>(ctx->dkeys[3]); la.p2p_off = as<uint32_t>(ctx->doff[3]); la.nb = ctx->nb;
     la.perm = as<uint32_t>(in1 ? ctx->v1 : ctx->v0);
     la.ax = ax; la.ay = ay; la.az = az; la.pot = pot;
+    la.part_hi = as<double2>(ctx->part_hi); la.part_lo = as<double2>(ctx->part_lo);
     la.tb = ctx->tb;
     if (mixed) {
         leaf_relative_f32(t, la.xs, la.ys, la.zs, la.ms, la.zc, as<float4>(ctx->prel), st);
         la.prel = as<float4>(ctx->prel);
         la.loc = ctx->loc32.ptr;
-        leaf_eval_f32(la, st);
     } else {
         la.loc = ctx->loc.ptr;
-        leaf_eval_f64(la, st);
     }
+    leaf_eval(la, mixed, as<int>(ctx->item_leaf), item_first, slot_first, (int)htot[0],
+              as<unsigned>(ctx->work), as<int>(ctx->leaf_of), st);
     CK(cudaEventRecord(ctx->ev[7], st));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
@@ -490,7 +511,6 @@ int fmm_create(fmm_ctx** out, const fmm_config* cfg) {
     ctx->tb.diag = base + o; o += nd;
     ctx->tb.sub = base + o; o += nd;
     upload_expansion_tables(ctx->ht);
-    upload_m2l_tables(ctx->ht, kSwapCos, kSwapSin);
     upload_leaf_tables(ctx->ht);
     for (auto& e : ctx->ev) cudaEventCreate(&e);
     if (cudaGetLastError() != cudaSuccess) {
@@ -509,7 +529,9 @@ void fmm_destroy(fmm_ctx* ctx) {
                   &ctx->f, &ctx->bbox, &ctx->level, &ctx->begin, &ctx->end, &ctx->parent,
                   &ctx->first_child, &ctx->nchild, &ctx->M, &ctx->S, &ctx->zc, &ctx->r, &ctx->Pk,
                   &ctx->mult, &ctx->mult32, &ctx->loc, &ctx->loc32, &ctx->fmin, &ctx->fscratch,
-                  &ctx->front0, &ctx->front1, &ctx->dalt, &ctx->dcount};
+                  &ctx->front0, &ctx->front1, &ctx->dalt, &ctx->dcount, &ctx->zhi, &ctx->zlo,
+                  &ctx->item_first, &ctx->slot_first, &ctx->item_leaf, &ctx->leaf_of, &ctx->part_hi,
+                  &ctx->part_lo, &ctx->work};
     for (Buf* b : all) release(*b);
     for (int l = 0; l < 4; ++l) {
         release(ctx->lists[l]);

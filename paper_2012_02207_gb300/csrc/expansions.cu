@@ -282,6 +282,20 @@ __global__ void k_l2l(TreeView t, int k0, int k1, int p, Tab tb, const double* _
     }
 }
 
+__global__ void k_node_centres(int nnodes, const double* __restrict__ zc, const double* __restrict__ rr,
+                               float4* __restrict__ zhi, float4* __restrict__ zlo) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnodes) return;
+    float h[3], l[3];
+    for (int d = 0; d < 3; ++d) {
+        const double z = zc[3 * k + d];
+        h[d] = (float)z;
+        l[d] = (float)(z - (double)h[d]);
+    }
+    zhi[k] = make_float4(h[0], h[1], h[2], (float)hat_scale(rr[k]));
+    zlo[k] = make_float4(l[0], l[1], l[2], 0.0f);
+}
+
 inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 
 TabF64 tab64(const DevTables& tb) { return TabF64{tb.w, tb.iw, tb.rec_a, tb.rec_b, tb.diag, tb.sub}; }
@@ -326,6 +340,10 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
         if (k1 > k0) (k_m2m<<<k1 - k0, 64, sh_m2m, st>>>(t, k0, p, tb, zc, r, mult), note_launch());
     }
     (k_pnorm<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, p, mult, r, Pk), note_launch());
+}
+
+void node_centres_f32(int nnodes, const double* zc, const double* r, float4* zhi, float4* zlo, cudaStream_t st) {
+    (k_node_centres<<<blocks_for(nnodes, 128), 128, 0, st>>>(nnodes, zc, r, zhi, zlo), note_launch());
 }
 
 void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStream_t st) {

@@ -97,6 +97,10 @@ int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n
                uint32_t* hist, cudaStream_t st);
 // single-block exclusive scan of count uint32 values in place; total -> *total (device)
 void scan_exclusive_u32(uint32_t* data, int64_t count, uint32_t* total, cudaStream_t st);
+// the same for large tables (multi-block); scratch: scan_scratch_words(count) words
+size_t scan_scratch_words(int64_t count);
+void scan_exclusive_u32_large(uint32_t* data, int64_t count, uint32_t* total, uint32_t* scratch,
+                              cudaStream_t st);
 
 // ---------------------------------------------------------------- tree.cu
 struct TreeBuffers {
@@ -148,8 +152,8 @@ int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* 
 // per-target CSR (sorted directed keys target<<nb | source).
 void scalar_force(const TreeView& t, const double* zc, const double* M, const float4* xf,
                   const uint64_t* far_keys, const uint32_t* far_off, const uint64_t* near_keys,
-                  const uint32_t* near_off, int nb, float* farf, float* f, float* fmin,
-                  cudaStream_t st);
+                  const uint32_t* near_off, int nb, const int* h_level_start, float* farf, float* f,
+                  float* fmin, cudaStream_t st);
 // directed entries of a pair list: (B<-A) and (A<-B), self pairs once.
 void pairs_to_directed(const int2* pairs, int64_t npairs, int nb, uint64_t* keys,
                        unsigned long long* count, cudaStream_t st);
@@ -164,6 +168,10 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
                  const double* ys, const double* zs, const double* ms, const double* zc,
                  const double* r, double* mult, double* Pk, const DevTables& tb, cudaStream_t st);
 void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStream_t st);
+// double-float node centres (hi, lo) and the FP32 hat scale in zhi.w
+void node_centres_f32(int nnodes, const double* zc, const double* r, float4* zhi, float4* zlo, cudaStream_t st);
+// per-node minimum of the scalar-force estimate (leaves over bodies, then levels upward)
+
 // L2L level by level (FP64 or FP32 locals).
 void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const double* zc,
                        const double* r, double* loc, const DevTables& tb, cudaStream_t st);
@@ -171,25 +179,29 @@ void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const
                        const double* r, float* loc, cudaStream_t st);
 
 // ----------------------------------------------------------------- m2l.cu
-void upload_m2l_tables(const HostTables& h, const double* swap_cos, const double* swap_sin);
 // Rotation-accelerated M2L (Sec. 2.4), gathered per target over the sorted
 // directed list; writes the locals of every node (zero without sources).
 void m2l_f64(int nnodes, int p, const uint64_t* keys, const uint32_t* off, int nb,
              const double* mult, const double* zc, const double* r, double* loc,
              const DevTables& tb, cudaStream_t st);
 void m2l_f32(int nnodes, int p, const uint64_t* keys, const uint32_t* off, int nb,
-             const float* mult, const double* zc, const double* r, float* loc, cudaStream_t st);
+             const float* mult, const float4* zhi, const float4* zlo, float* loc, cudaStream_t st);
+bool m2l32_supported(int p);
 
 // ----------------------------------------------------------------- p2p.cu
+constexpr int kLeavesPerItem = 64;  // source leaves per P2P work item
 void upload_leaf_tables(const HostTables& h);
-// Leaf evaluation: L2P of the leaf's local expansion plus P2P over its
-// source leaves; writes G-scaled results to the caller's arrays via perm.
+// Leaf evaluation: P2P over bounded work items (target leaf, up to
+// kLeavesPerItem source leaves) written as per-body partials, then per body
+// L2P of its leaf's local expansion plus its partials in item order; G-scaled
+// results go to the caller's arrays through perm.
 struct LeafArgs {
     TreeView t;
     int p;
     double G;
     const double *xs, *ys, *zs, *ms;
     const double *zc, *r;
+    const float4 *zhi, *zlo;  // double-float node centres; zhi.w = hat scale
     const uint64_t* p2p_keys;
     const uint32_t* p2p_off;
     int nb;
@@ -197,12 +209,16 @@ struct LeafArgs {
     double *ax, *ay, *az, *pot;
     const void* loc;   // FP64 or FP32 locals
     const float4* prel;  // leaf-relative FP32 bodies (mixed)
+    double2 *part_hi, *part_lo;  // P2P partials: (ax, ay), (az, pot)
     DevTables tb;
 };
-void leaf_eval_f64(const LeafArgs& a, cudaStream_t st);
-void leaf_eval_f32(const LeafArgs& a, cudaStream_t st);
-void count_p2p_interactions(const uint64_t* keys, int64_t nk, int nb, const int* begin, const int* end,
-                            unsigned long long* out, cudaStream_t st);
+void leaf_items_plan(const TreeView& t, const uint32_t* p2p_off, uint32_t* item_first, uint32_t* slot_first,
+                     uint32_t* totals, cudaStream_t st);
+void leaf_items_fill(const TreeView& t, const uint32_t* item_first, int* item_leaf, int* leaf_of, cudaStream_t st);
+void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_t* item_first,
+               const uint32_t* slot_first, int nitems, unsigned* work, const int* leaf_of, cudaStream_t st);
+void count_p2p_interactions(const uint64_t* keys, int64_t nk, int nb, int nnodes, const int* begin,
+                            const int* end, unsigned long long* out, cudaStream_t st);
 void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, const double* zs,
                        const double* ms, const double* zc, float4* prel, cudaStream_t st);
 void direct_sum_f64(int64_t n, const double* x, const double* y, const double* z, const double* m,

@@ -140,6 +140,18 @@ def hat_blocks(n, blocks):
     return out
 
 
+def translation_coefficients(pmax):
+    """(n+k)!/(w_n^m w_k^m) with w_n^m = sqrt((n+m)!(n-m)!), correctly rounded."""
+    out = {}
+    for n in range(pmax + 1):
+        for k in range(pmax + 1):
+            for m in range(min(n, k) + 1):
+                q = Fraction(factorial(n + k) ** 2,
+                             factorial(n + m) * factorial(n - m) * factorial(k + m) * factorial(k - m))
+                out[(n, k, m)] = signed_sqrt_to_float(1, q)
+    return out
+
+
 def main(pmax=PMAX, out=sys.stdout):
     U = regular_polys(pmax)
     cos_vals, sin_vals = [], []
@@ -158,6 +170,7 @@ def main(pmax=PMAX, out=sys.stdout):
         for i in range(0, len(vals), 4):
             w("  " + ", ".join(float.hex(v) for v in vals[i:i + 4]) + ",\n")
         w("};\n")
+
 
 
 if __name__ == "__main__":

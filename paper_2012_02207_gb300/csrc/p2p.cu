@@ -104,105 +104,219 @@ __device__ void l2p_hat(int p, const T* __restrict__ F, T x, T y, T z, T inv_s, 
     az = g0 * inv_s;
 }
 
-__global__ void __launch_bounds__(128) k_leaf_f32(LeafArgs a) {
+// ---------------------------------------------------------------------------
+// P2P over work items. Item (B, j) covers the sources q in
+// [off[B] + j*kLeavesPerItem, ...) of target leaf B (at most kLeavesPerItem
+// source leaves), so no warp carries more than a bounded share of a dense
+// leaf's work. Warps fetch items dynamically. Each item writes one partial
+// sum per target body; k_leaf_reduce adds the partials of a body in item
+// order (deterministic) together with the L2P far field.
+
+// Knuth's two-sum: (hi, lo) += b with the rounding error kept in lo.
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float b) {
+    const float s = hi + b;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (b - bb);
+    hi = s;
+    lo += err;
+}
+
+template <typename T>
+struct Body4 { T x, y, z, w; };
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __restrict__ item_leaf,
+                                                    const uint32_t* __restrict__ item_first,
+                                                    const uint32_t* __restrict__ slot_first,
+                                                    int nitems, unsigned* __restrict__ work) {
+    __shared__ Body4<T> stage[4][64];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    Body4<T>* sm = stage[wib];
     const uint64_t mask = (1ull << a.nb) - 1ull;
-    const int nr = ncoef_real(a.p);
-    const float* locs = reinterpret_cast<const float*>(a.loc);
-    const TabL32 tb;
-    for (int b = blockIdx.x * (blockDim.x >> 5) + wib; b < a.t.nnodes; b += nwarps) {
-        if (a.t.nchild[b] != 0) continue;
-        const int b0 = a.t.begin[b], b1 = a.t.end[b];
-        const double zbx = a.zc[3 * b], zby = a.zc[3 * b + 1], zbz = a.zc[3 * b + 2];
-        const float inv_s = (float)(1.0 / hat_scale(a.r[b]));
-        const float* F = locs + (size_t)nr * b;
-        const uint32_t q0 = a.p2p_off[b], q1 = a.p2p_off[b + 1];
-        for (int t0 = b0; t0 < b1; t0 += 32) {
-            const int i = t0 + lane;
-            const bool act = i < b1;
-            const float4 ti = act ? a.prel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float phi = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-            if (act) l2p_hat<float>(a.p, F, ti.x * inv_s, ti.y * inv_s, ti.z * inv_s, inv_s, tb, phi, fx, fy, fz);
-            double sx = fx, sy = fy, sz = fz, sp = phi;
-            for (uint32_t q = q0; q < q1; ++q) {
-                const int src = (int)(a.p2p_keys[q] & mask);
-                const float ox = (float)(a.zc[3 * src] - zbx), oy = (float)(a.zc[3 * src + 1] - zby),
-                            oz = (float)(a.zc[3 * src + 2] - zbz);
-                const int j0 = a.t.begin[src], j1 = a.t.end[src];
-                float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
-                for (int j = j0; j < j1; ++j) {
-                    const float4 s = a.prel[j];
-                    const float dx = (s.x + ox) - ti.x, dy = (s.y + oy) - ti.y, dz = (s.z + oz) - ti.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    const float rinv = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
-                    const float mr = s.w * rinv;
-                    const float mr3 = mr * rinv * rinv;
-                    px += mr3 * dx;
-                    py += mr3 * dy;
-                    pz += mr3 * dz;
-                    pp += mr;
-                }
-                sx += px; sy += py; sz += pz; sp -= pp;
-            }
+    for (;;) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(work, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if ((int)it >= nitems) break;
+        const int B = item_leaf[it];
+        const int j = (int)(it - item_first[B]);
+        const uint32_t q0 = a.p2p_off[B] + (uint32_t)j * kLeavesPerItem;
+        const uint32_t qe = a.p2p_off[B + 1];
+        const uint32_t q1 = q0 + kLeavesPerItem < qe ? q0 + kLeavesPerItem : qe;
+        const int b0 = a.t.begin[B], nB = a.t.end[B] - b0;
+        const uint32_t slot0 = slot_first[B] + (uint32_t)j * (uint32_t)nB;
+        const float4 bh = a.zhi[B], bl = a.zlo[B];
+        for (int tc = 0; tc < nB; tc += 32) {
+            const int nt = nB - tc < 32 ? nB - tc : 32;
+            const int G = 32 / nt;            // lanes per target
+            const int t = lane / G, sub = lane - t * G;
+            const bool act = t < nt;
+            T tx = T(0), ty = T(0), tz = T(0);
             if (act) {
-                const uint32_t o = a.perm[i];
-                a.ax[o] = a.G * sx;
-                a.ay[o] = a.G * sy;
-                a.az[o] = a.G * sz;
-                if (a.pot) a.pot[o] = a.G * sp;
+                if (sizeof(T) == 4) {
+                    const float4 v = a.prel[b0 + tc + t];
+                    tx = (T)v.x; ty = (T)v.y; tz = (T)v.z;
+                } else {
+                    tx = (T)a.xs[b0 + tc + t]; ty = (T)a.ys[b0 + tc + t]; tz = (T)a.zs[b0 + tc + t];
+                }
+            }
+            float hx = 0.f, hy = 0.f, hz = 0.f, hp = 0.f, lx = 0.f, ly = 0.f, lz = 0.f, lp = 0.f;
+            double dx64 = 0.0, dy64 = 0.0, dz64 = 0.0, dp64 = 0.0;
+            for (uint32_t q = q0; q < q1; ++q) {
+                const int A = (int)(a.p2p_keys[q] & mask);
+                const int a0 = a.t.begin[A], nA = a.t.end[A] - a0;
+                float ox = 0.f, oy = 0.f, oz = 0.f;
+                if (sizeof(T) == 4) {
+                    const float4 ah = a.zhi[A], al = a.zlo[A];
+                    ox = (ah.x - bh.x) + (al.x - bl.x);
+                    oy = (ah.y - bh.y) + (al.y - bl.y);
+                    oz = (ah.z - bh.z) + (al.z - bl.z);
+                }
+                for (int s0 = 0; s0 < nA; s0 += 64) {
+                    const int ns = nA - s0 < 64 ? nA - s0 : 64;
+                    __syncwarp();
+                    for (int l = lane; l < ns; l += 32) {
+                        Body4<T> v;
+                        if (sizeof(T) == 4) {
+                            const float4 u = a.prel[a0 + s0 + l];
+                            v = {(T)(u.x + ox), (T)(u.y + oy), (T)(u.z + oz), (T)u.w};
+                        } else {
+                            const int jj = a0 + s0 + l;
+                            v = {(T)a.xs[jj], (T)a.ys[jj], (T)a.zs[jj], (T)a.ms[jj]};
+                        }
+                        sm[l] = v;
+                    }
+                    __syncwarp();
+                    if (!act) continue;
+                    T px = T(0), py = T(0), pz = T(0), pp = T(0);
+#pragma unroll 4
+                    for (int k = sub; k < ns; k += G) {
+                        const Body4<T> sv = sm[k];
+                        const T dx = sv.x - tx, dy = sv.y - ty, dz = sv.z - tz;
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        T rinv;
+                        if (sizeof(T) == 4) rinv = (r2 > T(0)) ? (T)rsqrtf((float)r2) : T(0);
+                        else rinv = (r2 > T(0)) ? T(1) / (T)sqrt((double)r2) : T(0);
+                        const T mr = sv.w * rinv;
+                        const T mr3 = mr * rinv * rinv;
+                        px += mr3 * dx;
+                        py += mr3 * dy;
+                        pz += mr3 * dz;
+                        pp += mr;
+                    }
+                    if (sizeof(T) == 4) {
+                        two_sum(hx, lx, (float)px);
+                        two_sum(hy, ly, (float)py);
+                        two_sum(hz, lz, (float)pz);
+                        two_sum(hp, lp, (float)pp);
+                    } else {
+                        dx64 += (double)px; dy64 += (double)py; dz64 += (double)pz; dp64 += (double)pp;
+                    }
+                }
+            }
+            // combine the G sub-lanes of each target in sub-lane order
+            const int leader = t * G;
+            for (int s = 1; s < G; ++s) {
+                const int src = leader + s < 32 ? leader + s : 31;
+                if (sizeof(T) == 4) {
+                    const float vx = __shfl_sync(0xffffffffu, hx, src), vy = __shfl_sync(0xffffffffu, hy, src),
+                                vz = __shfl_sync(0xffffffffu, hz, src), vp = __shfl_sync(0xffffffffu, hp, src);
+                    const float wx = __shfl_sync(0xffffffffu, lx, src), wy = __shfl_sync(0xffffffffu, ly, src),
+                                wz = __shfl_sync(0xffffffffu, lz, src), wp = __shfl_sync(0xffffffffu, lp, src);
+                    if (sub == 0 && act) {
+                        two_sum(hx, lx, vx); lx += wx;
+                        two_sum(hy, ly, vy); ly += wy;
+                        two_sum(hz, lz, vz); lz += wz;
+                        two_sum(hp, lp, vp); lp += wp;
+                    }
+                } else {
+                    const double vx = __shfl_sync(0xffffffffu, dx64, src), vy = __shfl_sync(0xffffffffu, dy64, src),
+                                 vz = __shfl_sync(0xffffffffu, dz64, src), vp = __shfl_sync(0xffffffffu, dp64, src);
+                    if (sub == 0 && act) { dx64 += vx; dy64 += vy; dz64 += vz; dp64 += vp; }
+                }
+            }
+            if (act && sub == 0) {
+                const uint32_t slot = slot0 + (uint32_t)(tc + t);
+                if (sizeof(T) == 4) {
+                    a.part_hi[slot] = make_double2((double)hx + (double)lx, (double)hy + (double)ly);
+                    a.part_lo[slot] = make_double2((double)hz + (double)lz, (double)hp + (double)lp);
+                } else {
+                    a.part_hi[slot] = make_double2(dx64, dy64);
+                    a.part_lo[slot] = make_double2(dz64, dp64);
+                }
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(64) k_leaf_f64(LeafArgs a) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    const uint64_t mask = (1ull << a.nb) - 1ull;
+// One thread per body: L2P of its leaf's local expansion plus the P2P
+// partials of its leaf's items in item order; G-scaled, to the caller's order.
+template <typename T>
+__global__ void __launch_bounds__(128) k_leaf_reduce(LeafArgs a, const int* __restrict__ leaf_of,
+                                                      const uint32_t* __restrict__ item_first,
+                                                      const uint32_t* __restrict__ slot_first) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.t.n) return;
+    const int B = leaf_of[i];
+    const int b0 = a.t.begin[B], nB = a.t.end[B] - b0;
     const int nr = ncoef_real(a.p);
-    const double* locs = reinterpret_cast<const double*>(a.loc);
-    const TabL64 tb{a.tb.w, a.tb.iw, a.tb.rec_a, a.tb.rec_b, a.tb.diag, a.tb.sub};
-    for (int b = blockIdx.x * (blockDim.x >> 5) + wib; b < a.t.nnodes; b += nwarps) {
-        if (a.t.nchild[b] != 0) continue;
-        const int b0 = a.t.begin[b], b1 = a.t.end[b];
-        const double zbx = a.zc[3 * b], zby = a.zc[3 * b + 1], zbz = a.zc[3 * b + 2];
-        const double inv_s = 1.0 / hat_scale(a.r[b]);
-        const double* F = locs + (size_t)nr * b;
-        const uint32_t q0 = a.p2p_off[b], q1 = a.p2p_off[b + 1];
-        for (int t0 = b0; t0 < b1; t0 += 32) {
-            const int i = t0 + lane;
-            const bool act = i < b1;
-            const double xi = act ? a.xs[i] : 0.0, yi = act ? a.ys[i] : 0.0, zi = act ? a.zs[i] : 0.0;
-            double phi = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-            if (act) l2p_hat<double>(a.p, F, (xi - zbx) * inv_s, (yi - zby) * inv_s, (zi - zbz) * inv_s, inv_s, tb, phi, sx, sy, sz);
-            double sp = phi;
-            for (uint32_t q = q0; q < q1; ++q) {
-                const int src = (int)(a.p2p_keys[q] & mask);
-                const int j0 = a.t.begin[src], j1 = a.t.end[src];
-                for (int j = j0; j < j1; ++j) {
-                    const double dx = a.xs[j] - xi, dy = a.ys[j] - yi, dz = a.zs[j] - zi;
-                    const double r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 > 0.0) {
-                        const double r = sqrt(r2);
-                        const double mr = a.ms[j] / r;
-                        const double mr3 = mr / r2;
-                        sx += mr3 * dx;
-                        sy += mr3 * dy;
-                        sz += mr3 * dz;
-                        sp -= mr;
-                    }
-                }
-            }
-            if (act) {
-                const uint32_t o = a.perm[i];
-                a.ax[o] = a.G * sx;
-                a.ay[o] = a.G * sy;
-                a.az[o] = a.G * sz;
-                if (a.pot) a.pot[o] = a.G * sp;
-            }
-        }
+    double sx, sy, sz, sp;
+    if (sizeof(T) == 4) {
+        const TabL32 tb;
+        const float4 bh = a.zhi[B];
+        const float inv_s = 1.0f / bh.w;
+        const float4 v = a.prel[i];
+        float phi, fx, fy, fz;
+        l2p_hat<float>(a.p, reinterpret_cast<const float*>(a.loc) + (size_t)nr * B, v.x * inv_s, v.y * inv_s,
+                       v.z * inv_s, inv_s, tb, phi, fx, fy, fz);
+        sx = fx; sy = fy; sz = fz; sp = phi;
+    } else {
+        const TabL64 tb{a.tb.w, a.tb.iw, a.tb.rec_a, a.tb.rec_b, a.tb.diag, a.tb.sub};
+        const double inv_s = 1.0 / hat_scale(a.r[B]);
+        double phi, fx, fy, fz;
+        l2p_hat<double>(a.p, reinterpret_cast<const double*>(a.loc) + (size_t)nr * B,
+                        (a.xs[i] - a.zc[3 * B]) * inv_s, (a.ys[i] - a.zc[3 * B + 1]) * inv_s,
+                        (a.zs[i] - a.zc[3 * B + 2]) * inv_s, inv_s, tb, phi, fx, fy, fz);
+        sx = fx; sy = fy; sz = fz; sp = phi;
     }
+    const uint32_t i0 = item_first[B], i1 = item_first[B + 1];
+    const uint32_t s0 = slot_first[B] + (uint32_t)(i - b0);
+    for (uint32_t it = i0; it < i1; ++it) {
+        const uint32_t slot = s0 + (it - i0) * (uint32_t)nB;
+        const double2 u = a.part_hi[slot], w = a.part_lo[slot];
+        sx += u.x; sy += u.y; sz += w.x; sp -= w.y;
+    }
+    const uint32_t o = a.perm[i];
+    a.ax[o] = a.G * sx;
+    a.ay[o] = a.G * sy;
+    a.az[o] = a.G * sz;
+    if (a.pot) a.pot[o] = a.G * sp;
+}
+
+// work items per leaf: ceil(#source leaves / kLeavesPerItem); slots = items * n_B
+__global__ void k_items_count(TreeView t, const uint32_t* __restrict__ off, uint32_t* __restrict__ nitems,
+                              uint32_t* __restrict__ nslots) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= t.nnodes) return;
+    uint32_t ni = 0;
+    if (t.nchild[b] == 0) {
+        const uint32_t deg = off[b + 1] - off[b];
+        ni = (deg + kLeavesPerItem - 1) / kLeavesPerItem;
+    }
+    nitems[b] = ni;
+    nslots[b] = ni * (uint32_t)(t.end[b] - t.begin[b]);
+}
+
+__global__ void k_items_fill(int nnodes, const uint32_t* __restrict__ item_first, int* __restrict__ item_leaf) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nnodes) return;
+    for (uint32_t it = item_first[b]; it < item_first[b + 1]; ++it) item_leaf[it] = b;
+}
+
+__global__ void k_leaf_of_bodies(TreeView t, int* __restrict__ leaf_of) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= t.nnodes || t.nchild[k] != 0) return;
+    for (int i = t.begin[k]; i < t.end[k]; ++i) leaf_of[i] = k;
 }
 
 __global__ void k_leaf_relative(TreeView t, const double* __restrict__ xs, const double* __restrict__ ys,
@@ -257,12 +371,12 @@ __global__ void __launch_bounds__(256) k_direct(int64_t n, const double* __restr
 }
 
 // directed body-body interactions of the P2P list (self pairs without i = j)
-__global__ void k_count_p2p(const uint64_t* __restrict__ keys, int64_t nk, int nb,
+__global__ void k_count_p2p(const uint64_t* __restrict__ keys, int64_t nk, int nb, int nnodes,
                             const int* __restrict__ begin, const int* __restrict__ end,
                             unsigned long long* out) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long c = 0;
-    if (q < nk) {
+    if (q < nk && (keys[q] >> nb) < (uint64_t)nnodes) {
         const int t = (int)(keys[q] >> nb), s = (int)(keys[q] & ((1ull << nb) - 1ull));
         const unsigned long long nt = (unsigned long long)(end[t] - begin[t]);
         const unsigned long long ns = (unsigned long long)(end[s] - begin[s]);
@@ -276,9 +390,9 @@ __global__ void k_count_p2p(const uint64_t* __restrict__ keys, int64_t nk, int n
 inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 }  // namespace
 
-void count_p2p_interactions(const uint64_t* keys, int64_t nk, int nb, const int* begin, const int* end,
-                            unsigned long long* out, cudaStream_t st) {
-    if (nk > 0) (k_count_p2p<<<blocks_for(nk, 256), 256, 0, st>>>(keys, nk, nb, begin, end, out), note_launch());
+void count_p2p_interactions(const uint64_t* keys, int64_t nk, int nb, int nnodes, const int* begin,
+                            const int* end, unsigned long long* out, cudaStream_t st) {
+    if (nk > 0) (k_count_p2p<<<blocks_for(nk, 256), 256, 0, st>>>(keys, nk, nb, nnodes, begin, end, out), note_launch());
 }
 
 void upload_leaf_tables(const HostTables& h) {
@@ -300,8 +414,31 @@ void upload_leaf_tables(const HostTables& h) {
     cudaMemcpyToSymbol(c_sub32l, s, sizeof(s));
 }
 
-void leaf_eval_f64(const LeafArgs& a, cudaStream_t st) { (k_leaf_f64<<<152 * 16, 64, 0, st>>>(a), note_launch()); }
-void leaf_eval_f32(const LeafArgs& a, cudaStream_t st) { (k_leaf_f32<<<152 * 8, 128, 0, st>>>(a), note_launch()); }
+void leaf_items_plan(const TreeView& t, const uint32_t* p2p_off, uint32_t* item_first, uint32_t* slot_first,
+                     uint32_t* totals, cudaStream_t st) {
+    (k_items_count<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, p2p_off, item_first, slot_first), note_launch());
+    scan_exclusive_u32(item_first, t.nnodes, item_first + t.nnodes, st);
+    scan_exclusive_u32(slot_first, t.nnodes, slot_first + t.nnodes, st);
+    cudaMemcpyAsync(totals, item_first + t.nnodes, 4, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(totals + 1, slot_first + t.nnodes, 4, cudaMemcpyDeviceToDevice, st);
+}
+
+void leaf_items_fill(const TreeView& t, const uint32_t* item_first, int* item_leaf, int* leaf_of, cudaStream_t st) {
+    (k_items_fill<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, item_first, item_leaf), note_launch());
+    (k_leaf_of_bodies<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, leaf_of), note_launch());
+}
+
+void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_t* item_first,
+               const uint32_t* slot_first, int nitems, unsigned* work, const int* leaf_of, cudaStream_t st) {
+    cudaMemsetAsync(work, 0, sizeof(unsigned), st);
+    if (fp32) {
+        (k_p2p_items<float><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        (k_leaf_reduce<float><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch());
+    } else {
+        (k_p2p_items<double><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        (k_leaf_reduce<double><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch());
+    }
+}
 
 void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, const double* zs,
                        const double* ms, const double* zc, float4* prel, cudaStream_t st) {

@@ -121,11 +121,78 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t* data, int64_t count, ui
         run += v;
     }
 }
+// Large scans in three passes: segment sums, a scan of the sums, and a
+// rescan of each segment from its offset.
+constexpr int kSegment = 4096;
+__global__ void __launch_bounds__(256) k_seg_sum(const uint32_t* __restrict__ data, int64_t count,
+                                                 uint32_t* __restrict__ sums) {
+    __shared__ uint32_t red[256];
+    const int64_t base = (int64_t)blockIdx.x * kSegment;
+    uint32_t s = 0;
+    for (int k = threadIdx.x; k < kSegment; k += 256) {
+        const int64_t i = base + k;
+        if (i < count) s += data[i];
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256) k_seg_scan(uint32_t* __restrict__ data, int64_t count,
+                                                  const uint32_t* __restrict__ offs) {
+    __shared__ uint32_t warp_sums[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSegment + (int64_t)threadIdx.x * (kSegment / 256);
+    uint32_t v[kSegment / 256];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kSegment / 256; ++k) {
+        const int64_t i = base + k;
+        v[k] = i < count ? data[i] : 0u;
+        s += v[k];
+    }
+    uint32_t incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    uint32_t wo = 0;
+    for (int w = 0; w < warp; ++w) wo += warp_sums[w];
+    uint32_t run = offs[blockIdx.x] + wo + incl - s;
+#pragma unroll
+    for (int k = 0; k < kSegment / 256; ++k) {
+        const int64_t i = base + k;
+        if (i < count) data[i] = run;
+        run += v[k];
+    }
+}
 }  // namespace
+
+size_t scan_scratch_words(int64_t count) { return (size_t)((count + kSegment - 1) / kSegment + 2); }
+
+void scan_exclusive_u32_large(uint32_t* data, int64_t count, uint32_t* total, uint32_t* scratch,
+                              cudaStream_t st) {
+    if (count <= 65536) {
+        (k_scan<<<1, 1024, 0, st>>>(data, count, total), note_launch());
+        return;
+    }
+    const int nseg = (int)((count + kSegment - 1) / kSegment);
+    (k_seg_sum<<<nseg, 256, 0, st>>>(data, count, scratch), note_launch());
+    (k_scan<<<1, 1024, 0, st>>>(scratch, nseg, total), note_launch());
+    (k_seg_scan<<<nseg, 256, 0, st>>>(data, count, scratch), note_launch());
+}
 
 size_t radix_hist_words(int64_t n) {
     const int64_t nb = (n + kTile - 1) / kTile;
-    return (size_t)(256 * (nb > 0 ? nb : 1) + 1);
+    const int64_t cells = 256 * (nb > 0 ? nb : 1);
+    return (size_t)(cells + 1) + scan_scratch_words(cells);
 }
 
 void scan_exclusive_u32(uint32_t* data, int64_t count, uint32_t* total, cudaStream_t st) {
@@ -143,7 +210,7 @@ int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n
         uint64_t* ko = cur ? k0 : k1;
         uint32_t* vo = cur ? v0 : v1;
         (k_hist<<<nblocks, kThreads, 0, st>>>(ki, n, shift, hist, nblocks), note_launch());
-        (k_scan<<<1, 1024, 0, st>>>(hist, (int64_t)256 * nblocks, nullptr), note_launch());
+        scan_exclusive_u32_large(hist, (int64_t)256 * nblocks, nullptr, hist + (size_t)256 * nblocks + 1, st);
         (k_scatter<<<nblocks, kThreads, 0, st>>>(ki, vi, ko, vo, n, shift, hist, nblocks), note_launch());
         cur ^= 1;
     }

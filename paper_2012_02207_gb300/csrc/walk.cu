@@ -161,8 +161,11 @@ __global__ void k_offsets(const uint64_t* __restrict__ keys, int64_t nk, int nb,
                           uint32_t* __restrict__ off) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i > nk) return;
-    const int64_t t = (i < nk) ? (int64_t)(keys[i] >> nb) : (int64_t)nnodes;
-    const int64_t tp = (i > 0) ? (int64_t)(keys[i - 1] >> nb) : -1;
+    // marker keys (all ones, from self pairs) sort last and count as "past the end"
+    int64_t t = (i < nk) ? (int64_t)(keys[i] >> nb) : (int64_t)nnodes;
+    int64_t tp = (i > 0) ? (int64_t)(keys[i - 1] >> nb) : -1;
+    t = t < nnodes ? t : nnodes;
+    tp = tp < nnodes ? tp : nnodes;
     for (int64_t u = tp + 1; u <= t && u <= nnodes; ++u) off[u] = (uint32_t)i;
 }
 
@@ -228,12 +231,23 @@ __global__ void k_leaf_of(TreeView t, int* __restrict__ leaf_of) {
     for (int i = t.begin[k]; i < t.end[k]; ++i) leaf_of[i] = k;
 }
 
-__global__ void k_fmin(TreeView t, const float* __restrict__ f, float* __restrict__ fmin) {
+// fmin of a leaf over its bodies; of an internal cell over its children
+// (a minimum, so the order does not matter)
+__global__ void k_fmin_leaves(TreeView t, const float* __restrict__ f, float* __restrict__ fmin) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= t.nnodes) return;
+    if (k >= t.nnodes || t.nchild[k] != 0) return;
     const int b = t.begin[k], e = t.end[k];
     float mn = f[b];
     for (int i = b + 1; i < e; ++i) mn = f[i] < mn ? f[i] : mn;
+    fmin[k] = mn;
+}
+
+__global__ void k_fmin_internal(TreeView t, int k0, int k1, float* __restrict__ fmin) {
+    const int k = k0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= k1 || t.nchild[k] == 0) return;
+    const int c0 = t.first_child[k], c1 = c0 + t.nchild[k];
+    float mn = fmin[c0];
+    for (int c = c0 + 1; c < c1; ++c) mn = fmin[c] < mn ? fmin[c] : mn;
     fmin[k] = mn;
 }
 
@@ -293,8 +307,8 @@ void directed_offsets(const uint64_t* keys, int64_t nkeys, int nb, int nnodes, u
 
 void scalar_force(const TreeView& t, const double* zc, const double* M, const float4* xf,
                   const uint64_t* far_keys, const uint32_t* far_off, const uint64_t* near_keys,
-                  const uint32_t* near_off, int nb, float* farf, float* f, float* fmin,
-                  cudaStream_t st) {
+                  const uint32_t* near_off, int nb, const int* h_level_start, float* farf, float* f,
+                  float* fmin, cudaStream_t st) {
     // farf doubles as scratch: [0, nnodes) far sums, [nnodes, 2 nnodes) pushed-down g,
     // and the leaf index of every body after that.
     float* g = farf + t.nnodes;
@@ -303,7 +317,11 @@ void scalar_force(const TreeView& t, const double* zc, const double* M, const fl
     (k_push_down<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, farf, g), note_launch());
     (k_leaf_of<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, leaf_of), note_launch());
     (k_near_f<<<blocks_for(t.n, 128), 128, 0, st>>>(t, xf, near_keys, near_off, nb, leaf_of, g, f), note_launch());
-    (k_fmin<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, f, fmin), note_launch());
+    (k_fmin_leaves<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, f, fmin), note_launch());
+    for (int L = t.nlevels - 2; L >= 0; --L) {
+        const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
+        if (k1 > k0) (k_fmin_internal<<<blocks_for(k1 - k0, 128), 128, 0, st>>>(t, k0, k1, fmin), note_launch());
+    }
 }
 
 }  // namespace gbfmm
