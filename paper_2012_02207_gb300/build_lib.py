@@ -21,7 +21,8 @@ GEN = os.path.join(LIBDIR, "gen")
 LIB = os.path.join(LIBDIR, "libgbfmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NO_FMA = {"tree.cu", "walk.cu"}
-M2L32_ORDERS = [4, 6, 8, 10, 12, 14]  # orders of the FP32 register M2L kernel
+M2L32_ORDERS = [4, 6, 8, 10, 12, 14]
+EXTRA_FLAGS = os.environ.get("GBFMM_NVCC_FLAGS", "").split()  # extra nvcc flags for experiments  # orders of the FP32 register M2L kernel
 SOURCES = ["api.cu", "sort.cu", "tree.cu", "walk.cu", "expansions.cu", "m2l.cu", "p2p.cu"]
 
 
@@ -58,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         subprocess.run([sys.executable, os.path.join(CSRC, "gen_m2l.py")] + [str(p) for p in M2L32_ORDERS],
                        stdout=fh, check=True)
     os.replace(m2l_gen + ".tmp", m2l_gen)
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+    common = ARCH + EXTRA_FLAGS + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-I", os.path.join(ROOT, "include"), "-I", GEN, "-I", CSRC]
     if verbose:
         common += ["-Xptxas", "-v"]

@@ -59,7 +59,7 @@ struct fmm_ctx {
     Buf k0, k1, v0, v1, hist, xs, ys, zs, ms, xf, prel, lcp, win, hi, chunk, f, bbox;
     // per-node
     Buf level, begin, end, parent, first_child, nchild, M, S, zc, r, Pk, mult, mult32, loc, loc32,
-        fmin, fscratch, zhi, zlo;
+        fmin, fscratch, zhi, zlo, contrib, Phat, r32;
     // P2P work items
     Buf item_first, slot_first, item_leaf, leaf_of, part_hi, part_lo, work;
     // walk and lists
@@ -212,8 +212,9 @@ int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
         const double* binom_row = ctx->tb.sub + (kMaxP + 1);
         CK(cudaMemsetAsync(&ctx->ds->err, 0, sizeof(unsigned), st));
         const int it = dual_tree_walk(mode, t, as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->Pk),
-                                      as<float>(ctx->fmin), p, ctx->cfg.eps, binom_row, wb, ctx->ds,
-                                      ctx->h_ds, st);
+                                      as<float>(ctx->fmin), p, ctx->cfg.eps, binom_row, as<float4>(ctx->zhi),
+                                      as<float4>(ctx->zlo), as<float>(ctx->r32), as<float>(ctx->Phat), wb,
+                                      ctx->ds, ctx->h_ds, st);
         if (it == FMM_ERR_CAPACITY) {
             // the counters kept counting past the capacity: grow to what was asked for
             CK(cudaMemcpyAsync(ctx->h_ds, ctx->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
@@ -306,11 +307,14 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
         (rc = ensure(ctx, ctx->Pk, 8 * K * (p + 1))) || (rc = ensure(ctx, ctx->mult, 8 * K * nr)) ||
         (rc = ensure(ctx, ctx->fmin, 4 * K)) || (rc = ensure(ctx, ctx->fscratch, 4 * (2 * K + N))) ||
         (rc = ensure(ctx, ctx->zhi, 16 * K)) || (rc = ensure(ctx, ctx->zlo, 16 * K)) ||
+        (rc = ensure(ctx, ctx->contrib, 8 * K * nr)) || (rc = ensure(ctx, ctx->Phat, 4 * K * (p + 1))) ||
+        (rc = ensure(ctx, ctx->r32, 4 * K)) ||
         (rc = ensure(ctx, ctx->item_first, 4 * (K + 2))) || (rc = ensure(ctx, ctx->slot_first, 4 * (K + 2))) ||
         (rc = ensure(ctx, ctx->leaf_of, 4 * N)) || (rc = ensure(ctx, ctx->work, 64)))
         return rc;
     if (mixed) {
-        if ((rc = ensure(ctx, ctx->mult32, 4 * K * nr)) || (rc = ensure(ctx, ctx->loc32, 4 * K * nr))) return rc;
+        if ((rc = ensure(ctx, ctx->mult32, 4 * K * ((nr + 3) & ~(size_t)3))) || (rc = ensure(ctx, ctx->loc32, 4 * K * nr)))
+            return rc;
         if (!m2l32_supported(p) && (rc = ensure(ctx, ctx->loc, 8 * K * nr))) return rc;
     } else {
         if ((rc = ensure(ctx, ctx->loc, 8 * K * nr))) return rc;
@@ -338,7 +342,7 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
     // ---- upward pass
     upward_pass(t, ctx->h_level_start, p, as<double>(ctx->xs), as<double>(ctx->ys), as<double>(ctx->zs),
                 as<double>(ctx->ms), as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->mult),
-                as<double>(ctx->Pk), ctx->tb, st);
+                as<double>(ctx->Pk), as<float>(ctx->Phat), as<float>(ctx->r32), as<double>(ctx->contrib), ctx->tb, st);
     CK(cudaEventRecord(ctx->ev[2], st));
     // ---- scalar-force estimate
     if (ctx->front_cap == 0) {
@@ -369,7 +373,8 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
     const uint64_t* mk = as<uint64_t>(ctx->dkeys[2]);
     const uint32_t* mo = as<uint32_t>(ctx->doff[2]);
     if (mixed && m2l32_supported(p)) {
-        multipoles_to_f32(as<double>(ctx->mult), as<float>(ctx->mult32), (int64_t)(K * nr), st);
+        multipoles_to_f32_padded(as<double>(ctx->mult), as<float>(ctx->mult32), nnodes, (int)nr,
+                                 (int)((nr + 3) & ~(size_t)3), st);
         m2l_f32(nnodes, p, mk, mo, ctx->nb, as<float>(ctx->mult32), as<float4>(ctx->zhi), as<float4>(ctx->zlo),
                 as<float>(ctx->loc32), st);
     } else {
@@ -529,7 +534,7 @@ void fmm_destroy(fmm_ctx* ctx) {
                   &ctx->f, &ctx->bbox, &ctx->level, &ctx->begin, &ctx->end, &ctx->parent,
                   &ctx->first_child, &ctx->nchild, &ctx->M, &ctx->S, &ctx->zc, &ctx->r, &ctx->Pk,
                   &ctx->mult, &ctx->mult32, &ctx->loc, &ctx->loc32, &ctx->fmin, &ctx->fscratch,
-                  &ctx->front0, &ctx->front1, &ctx->dalt, &ctx->dcount, &ctx->zhi, &ctx->zlo,
+                  &ctx->front0, &ctx->front1, &ctx->dalt, &ctx->dcount, &ctx->zhi, &ctx->zlo, &ctx->contrib, &ctx->Phat, &ctx->r32,
                   &ctx->item_first, &ctx->slot_first, &ctx->item_leaf, &ctx->leaf_of, &ctx->part_hi,
                   &ctx->part_lo, &ctx->work};
     for (Buf* b : all) release(*b);

@@ -91,8 +91,13 @@ __device__ __forceinline__ Cx<T> real_get(const T* a, int n, int m) {
     return (am & 1) ? Cx<T>{-v.re, v.im} : Cx<T>{v.re, -v.im};
 }
 
-// ---- P2M: one warp per leaf; lanes own an order m, groups of lanes own bodies
-__global__ void __launch_bounds__(128) k_p2m(TreeView t, int p, TabF64 tb,
+// ---- P2M (FP64): one warp per leaf, one lane per body. Column by column
+// (order m), each lane runs the hat recurrence for its body and writes
+// m_i Shat_n^m((x_i - z)/s), n = m..p, to a per-warp shared tile
+// [entry][lane]; lane e then adds entry e over the 32 bodies. The body order
+// of every sum is fixed (chunks of 32 in order, lanes in order).
+template <int PM, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_p2m(TreeView t, int p, TabF64 tb,
                                               const double* __restrict__ xs,
                                               const double* __restrict__ ys,
                                               const double* __restrict__ zs,
@@ -100,123 +105,86 @@ __global__ void __launch_bounds__(128) k_p2m(TreeView t, int p, TabF64 tb,
                                               const double* __restrict__ zc,
                                               const double* __restrict__ rr,
                                               double* __restrict__ mult) {
-    extern __shared__ double sh_p2m[];
+    __shared__ double sh_tile[WARPS][2 * (PM + 1)][33];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int gsize = (p + 1 <= 8) ? 8 : ((p + 1 <= 16) ? 16 : 32);
-    const int ngroups = 32 / gsize;
-    const int g = lane / gsize, m = lane % gsize;
-    const int nc = tri(p + 1, 0);
-    Cx<double>* acc = reinterpret_cast<Cx<double>*>(sh_p2m) + (size_t)wib * ngroups * nc;
+    double (*tile)[33] = sh_tile[wib];
+    const int nr = ncoef_real(p);
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int k = blockIdx.x * (blockDim.x >> 5) + wib; k < t.nnodes; k += nwarps) {
         if (t.nchild[k] != 0) continue;
-        for (int i = lane; i < ngroups * nc; i += 32) acc[i] = {0.0, 0.0};
-        __syncwarp();
-        const double s = hat_scale(rr[k]);
+        const double is = 1.0 / hat_scale(rr[k]);
         const double cx = zc[3 * k], cy = zc[3 * k + 1], cz = zc[3 * k + 2];
-        Cx<double>* my = acc + g * nc;
-        for (int i = t.begin[k] + g; i < t.end[k]; i += ngroups) {
-            if (m > p) continue;
-            const double x = (xs[i] - cx) / s, y = (ys[i] - cy) / s, z = (zs[i] - cz) / s;
-            const double w = ms[i];
+        // lane e owns entries e and e + 32 of every column (a column has 2(p-m+1) <= 62 reals)
+        double acc[PM + 1][2];
+#pragma unroll
+        for (int m = 0; m <= PM; ++m) { acc[m][0] = 0.0; acc[m][1] = 0.0; }
+        for (int i0 = t.begin[k]; i0 < t.end[k]; i0 += 32) {
+            const int i = i0 + lane;
+            const bool act = i < t.end[k];
+            const double x = act ? (xs[i] - cx) * is : 0.0, y = act ? (ys[i] - cy) * is : 0.0,
+                         z = act ? (zs[i] - cz) * is : 0.0, w = act ? ms[i] : 0.0;
             const double r2 = x * x + y * y + z * z;
-            Cx<double> d{1.0, 0.0};
-            const Cx<double> xp{x, y};
-            for (int q = 1; q <= m; ++q) {
-                d = cmul(d, xp);
-                d.re *= tb.D(q);
-                d.im *= tb.D(q);
-            }
-            Cx<double> v2{0.0, 0.0}, v1 = d;
-            my[tri(m, m)].re += w * d.re;
-            my[tri(m, m)].im += w * d.im;
-            for (int n = m + 1; n <= p; ++n) {
-                Cx<double> v;
-                if (n == m + 1) {
-                    v = {tb.Sb(m) * z * v1.re, tb.Sb(m) * z * v1.im};
-                } else {
-                    const double a = tb.A(n, m) * z, b = tb.B(n, m) * r2;
-                    v = {a * v1.re - b * v2.re, a * v1.im - b * v2.im};
-                }
-                my[tri(n, m)].re += w * v.re;
-                my[tri(n, m)].im += w * v.im;
-                v2 = v1;
-                v1 = v;
-            }
-        }
-        __syncwarp();
-        double* out = mult + (size_t)ncoef_real(p) * k;
-        for (int q = lane; q < nc; q += 32) {
-            Cx<double> s2 = acc[q];
-            for (int gg = 1; gg < ngroups; ++gg) {
-                s2.re += acc[gg * nc + q].re;
-                s2.im += acc[gg * nc + q].im;
-            }
-            int n = 0;
-            while (tri(n + 1, 0) <= q) ++n;
-            const int mm = q - tri(n, 0);
-            out[hre(n, mm)] = s2.re;
-            if (mm) out[him(n, mm)] = s2.im;
-        }
-        __syncwarp();
-    }
-}
-
-// ---- M2M (FP64): one block per parent, one thread per output (n, m >= 0)
-//   Mhat_n^m(P) = sum_C sum_{k,l} Shat_k^l(b) beta sigma^{n-k} Mhat_{n-k}^{m-l}(C),
-//   b = (z_C - z_P)/s_P, sigma = s_C/s_P, beta = w_n^m / (w_k^l w_{n-k}^{m-l}).
-__global__ void k_m2m(TreeView t, int k0, int p, TabF64 tb, const double* __restrict__ zc,
-                      const double* __restrict__ rr, double* __restrict__ mult) {
-    extern __shared__ double sh_m2m[];
-    const int P = k0 + blockIdx.x;
-    if (t.nchild[P] == 0) return;
-    const int nc = tri(p + 1, 0), nr = ncoef_real(p);
-    const int c0 = t.first_child[P], ncld = t.nchild[P];
-    Cx<double>* S = reinterpret_cast<Cx<double>*>(sh_m2m);          // 8 * nc
-    double* Mc = sh_m2m + 2 * 8 * nc;                                 // 8 * nr
-    double* sig = Mc + 8 * nr;                                        // 8 * (p+1)
-    const double sP = hat_scale(rr[P]);
-    for (int c = threadIdx.x; c < ncld; c += blockDim.x) {
-        const int C = c0 + c;
-        const double bx = (zc[3 * C] - zc[3 * P]) / sP, by = (zc[3 * C + 1] - zc[3 * P + 1]) / sP,
-                     bz = (zc[3 * C + 2] - zc[3 * P + 2]) / sP;
-        shat_all<double>(p, bx, by, bz, tb, S + c * nc);
-        const double sg = hat_scale(rr[C]) / sP;
-        double pw = 1.0;
-        for (int j = 0; j <= p; ++j) { sig[c * (p + 1) + j] = pw; pw *= sg; }
-    }
-    for (int i = threadIdx.x; i < ncld * nr; i += blockDim.x)
-        Mc[i] = mult[(size_t)nr * (c0 + i / nr) + (i % nr)];
-    __syncthreads();
-    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
-        int n = 0;
-        while (tri(n + 1, 0) <= q) ++n;
-        const int m = q - tri(n, 0);
-        double are = 0.0, aim = 0.0;
-        for (int c = 0; c < ncld; ++c) {
-            const Cx<double>* Sc = S + c * nc;
-            const double* M = Mc + c * nr;
-            for (int k = 0; k <= n; ++k) {
-                const double sgp = sig[c * (p + 1) + (n - k)];
-                for (int l = -k; l <= k; ++l) {
-                    const int ml = m - l;
-                    if (ml > n - k || ml < -(n - k)) continue;
-                    const double beta = tb.W(n, m) * tb.IW(k, l < 0 ? -l : l) * tb.IW(n - k, ml < 0 ? -ml : ml);
-                    const Cx<double> prod = cmul(tri_get(Sc, k, l), real_get(M, n - k, ml));
-                    are += beta * sgp * prod.re;
-                    aim += beta * sgp * prod.im;
+            double dre = w, dim = 0.0;  // w * Shat_m^m
+#pragma unroll
+            for (int m = 0; m <= PM; ++m) {
+                if (m <= p) {
+                    if (m > 0) {
+                        const double tq = dre * x - dim * y;
+                        dim = (dre * y + dim * x) * tb.D(m);
+                        dre = tq * tb.D(m);
+                    }
+                    double s1r = dre, s1i = dim, s2r = 0.0, s2i = 0.0;
+                    tile[0][lane] = dre;
+                    tile[1][lane] = dim;
+                    for (int n = m + 1; n <= p; ++n) {
+                        double vr, vi;
+                        if (n == m + 1) {
+                            vr = tb.Sb(m) * z * s1r;
+                            vi = tb.Sb(m) * z * s1i;
+                        } else {
+                            const double a = tb.A(n, m) * z, b = tb.B(n, m) * r2;
+                            vr = a * s1r - b * s2r;
+                            vi = a * s1i - b * s2i;
+                        }
+                        tile[2 * (n - m)][lane] = vr;
+                        tile[2 * (n - m) + 1][lane] = vi;
+                        s2r = s1r; s2i = s1i; s1r = vr; s1i = vi;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int ent = lane + 32 * h;
+                        if (ent < 2 * (p - m + 1)) {
+                            double s = acc[m][h];
+                            for (int l = 0; l < 32; ++l) s += tile[ent][l];
+                            acc[m][h] = s;
+                        }
+                    }
+                    __syncwarp();
                 }
             }
         }
-        double* out = mult + (size_t)nr * P;
-        out[hre(n, m)] = are;
-        if (m) out[him(n, m)] = aim;
+        double* out = mult + (size_t)nr * k;
+#pragma unroll
+        for (int m = 0; m <= PM; ++m) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int ent = lane + 32 * h;
+                if (m <= p && ent < 2 * (p - m + 1)) {
+                    const int n = m + (ent >> 1);
+                    if (ent & 1) { if (m) out[him(n, m)] = acc[m][h]; }
+                    else out[hre(n, m)] = acc[m][h];
+                }
+            }
+        }
     }
 }
 
 // P_n = s^n sqrt(sum_{m=-n}^{n} |Mhat_n^m|^2)  (Sec. 2.3)
+// (also the FP32 copies used by the walk's screen: Phat_n = P_n / s^n and r)
 __global__ void k_pnorm(int nnodes, int p, const double* __restrict__ mult,
-                        const double* __restrict__ rr, double* __restrict__ Pk) {
+                        const double* __restrict__ rr, double* __restrict__ Pk, float* __restrict__ Phat,
+                        float* __restrict__ r32) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nnodes) return;
     const double* M = mult + (size_t)ncoef_real(p) * k;
@@ -225,9 +193,12 @@ __global__ void k_pnorm(int nnodes, int p, const double* __restrict__ mult,
     for (int n = 0; n <= p; ++n) {
         double acc = M[hre(n, 0)] * M[hre(n, 0)];
         for (int m = 1; m <= n; ++m) acc += 2.0 * (M[hre(n, m)] * M[hre(n, m)] + M[him(n, m)] * M[him(n, m)]);
-        Pk[(size_t)(p + 1) * k + n] = sp * sqrt(acc);
+        const double nrm = sqrt(acc);
+        Pk[(size_t)(p + 1) * k + n] = sp * nrm;
+        Phat[(size_t)(p + 1) * k + n] = (float)nrm;
         sp *= s;
     }
+    r32[k] = (float)rr[k];
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -322,28 +293,37 @@ void upload_expansion_tables(const HostTables& h) {
 
 void upward_pass(const TreeView& t, const int* h_level_start, int p, const double* xs,
                  const double* ys, const double* zs, const double* ms, const double* zc,
-                 const double* r, double* mult, double* Pk, const DevTables& tbl, cudaStream_t st) {
+                 const double* r, double* mult, double* Pk, float* Phat, float* r32, double* contrib,
+                 const DevTables& tbl, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
-    const int nc = tri(p + 1, 0), nr = ncoef_real(p);
-    const int gsize = (p + 1 <= 8) ? 8 : ((p + 1 <= 16) ? 16 : 32);
-    const size_t sh_p2m = (size_t)4 * (32 / gsize) * nc * sizeof(double) * 2;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
-    (k_p2m<<<152 * 8, 128, sh_p2m, st>>>(t, p, tb, xs, ys, zs, ms, zc, r, mult), note_launch());
-    const size_t sh_m2m = ((size_t)2 * 8 * nc + 8 * nr + 8 * (p + 1)) * sizeof(double);
-    for (int L = t.nlevels - 2; L >= 0; --L) {
-        const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
-        if (k1 > k0) (k_m2m<<<k1 - k0, 64, sh_m2m, st>>>(t, k0, p, tb, zc, r, mult), note_launch());
-    }
-    (k_pnorm<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, p, mult, r, Pk), note_launch());
+    if (p <= 16)
+        (k_p2m<16, 4><<<152 * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, r, mult), note_launch());
+    else
+        (k_p2m<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, r, mult), note_launch());
+    const int nr = ncoef_real(p);
+    (void)nr;
+    for (int L = t.nlevels - 2; L >= 0; --L)
+        m2m_level_f64(t, h_level_start[L], h_level_start[L + 1], h_level_start[L + 1], h_level_start[L + 2], p,
+                      zc, r, mult, contrib, tbl, st);
+    (k_pnorm<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, p, mult, r, Pk, Phat, r32), note_launch());
 }
 
 void node_centres_f32(int nnodes, const double* zc, const double* r, float4* zhi, float4* zlo, cudaStream_t st) {
     (k_node_centres<<<blocks_for(nnodes, 128), 128, 0, st>>>(nnodes, zc, r, zhi, zlo), note_launch());
+}
+
+__global__ void k_to_f32_strided(const double* __restrict__ a, float* __restrict__ b, int nnodes, int nr,
+                                 int stride) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)nnodes * stride) return;
+    const int64_t k = q / stride;
+    const int j = (int)(q - k * stride);
+    b[q] = j < nr ? (float)a[k * nr + j] : 0.0f;
+}
+
+void multipoles_to_f32_padded(const double* mult, float* mult32, int nnodes, int nr, int stride, cudaStream_t st) {
+    const int64_t n = (int64_t)nnodes * stride;
+    if (n > 0) (k_to_f32_strided<<<(int)((n + 255) / 256), 256, 0, st>>>(mult, mult32, nnodes, nr, stride), note_launch());
 }
 
 void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStream_t st) {

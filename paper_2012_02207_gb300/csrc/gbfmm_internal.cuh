@@ -146,7 +146,8 @@ struct WalkBuffers {
 // mode 1: the error-controlled MAC (lists m2l/p2p). Returns iterations or a
 // negative fmm_status. Counts land in ds->list_cnt.
 int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* r, const double* P,
-                   const float* fmin, int p, double eps, const double* binom_row, WalkBuffers& wb,
+                   const float* fmin, int p, double eps, const double* binom_row, const float4* zhi,
+                   const float4* zlo, const float* r32, const float* Phat, WalkBuffers& wb,
                    DevScalars* ds, DevScalars* h_ds, cudaStream_t st);
 // Scalar-force estimate f (Sec. 2.3) from the theta-walk lists given as
 // per-target CSR (sorted directed keys target<<nb | source).
@@ -166,8 +167,16 @@ void upload_expansion_tables(const HostTables& h);
 // FP64 hat multipoles: P2M at leaves, M2M level by level; P_k per node.
 void upward_pass(const TreeView& t, const int* h_level_start, int p, const double* xs,
                  const double* ys, const double* zs, const double* ms, const double* zc,
-                 const double* r, double* mult, double* Pk, const DevTables& tb, cudaStream_t st);
+                 const double* r, double* mult, double* Pk, float* Phat, float* r32, double* contrib,
+                 const DevTables& tb, cudaStream_t st);
+// rotation-accelerated M2M of one level: children [child0, child1) into their
+// parents [parent0, parent1); contrib: (p+1)^2 doubles per node (scratch)
+void m2m_level_f64(const TreeView& t, int parent0, int parent1, int child0, int child1, int p,
+                   const double* zc, const double* r, double* mult, double* contrib, const DevTables& tb,
+                   cudaStream_t st);
 void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStream_t st);
+// FP32 copy with each node's vector padded to `stride` floats (zeros after nr)
+void multipoles_to_f32_padded(const double* mult, float* mult32, int nnodes, int nr, int stride, cudaStream_t st);
 // double-float node centres (hi, lo) and the FP32 hat scale in zhi.w
 void node_centres_f32(int nnodes, const double* zc, const double* r, float4* zhi, float4* zlo, cudaStream_t st);
 // per-node minimum of the scalar-force estimate (leaves over bodies, then levels upward)

@@ -124,12 +124,64 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float b) {
 template <typename T>
 struct Body4 { T x, y, z, w; };
 
+constexpr int kStageCap = 256;  // bodies staged per pack (source leaves packed back to back)
+
+// Accumulators of one target: FP32 runs of at most kRun terms are folded
+// into (hi, lo) two-sum pairs (FP64 sums in FP64 mode), so the FP32 rounding
+// of near-field terms that cancel stays at the level of a short run.
+constexpr int kRun = 16;
+
+template <typename T>
+struct NearAcc {
+    float hx = 0.f, hy = 0.f, hz = 0.f, hp = 0.f, lx = 0.f, ly = 0.f, lz = 0.f, lp = 0.f;
+    double dx = 0.0, dy = 0.0, dz = 0.0, dp = 0.0;
+    __device__ __forceinline__ void add(T px, T py, T pz, T pp) {
+        if (sizeof(T) == 4) {
+            two_sum(hx, lx, (float)px);
+            two_sum(hy, ly, (float)py);
+            two_sum(hz, lz, (float)pz);
+            two_sum(hp, lp, (float)pp);
+        } else {
+            dx += (double)px; dy += (double)py; dz += (double)pz; dp += (double)pp;
+        }
+    }
+};
+
+template <typename T, bool GUARD>
+__device__ __forceinline__ void p2p_pack(const Body4<T>* __restrict__ sm, int cnt, int sub, int G, T tx, T ty,
+                                         T tz, NearAcc<T>& acc) {
+    for (int k0 = sub; k0 < cnt; k0 += kRun * G) {
+        const int k1 = k0 + kRun * G < cnt ? k0 + kRun * G : cnt;
+        T px = T(0), py = T(0), pz = T(0), pp = T(0);
+#pragma unroll 4
+        for (int k = k0; k < k1; k += G) {
+            const Body4<T> sv = sm[k];
+            const T dx = sv.x - tx, dy = sv.y - ty, dz = sv.z - tz;
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            T rinv;
+            if (sizeof(T) == 4) {
+                rinv = (T)rsqrtf((float)r2);
+                if (GUARD && !(r2 > T(0))) rinv = T(0);  // the body itself
+            } else {
+                rinv = (r2 > T(0)) ? T(1) / (T)sqrt((double)r2) : T(0);
+            }
+            const T mr = sv.w * rinv;
+            const T mr3 = mr * rinv * rinv;
+            px += mr3 * dx;
+            py += mr3 * dy;
+            pz += mr3 * dz;
+            pp += mr;
+        }
+        acc.add(px, py, pz, pp);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __restrict__ item_leaf,
                                                     const uint32_t* __restrict__ item_first,
                                                     const uint32_t* __restrict__ slot_first,
                                                     int nitems, unsigned* __restrict__ work) {
-    __shared__ Body4<T> stage[4][64];
+    __shared__ Body4<T> stage[4][kStageCap];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Body4<T>* sm = stage[wib];
     const uint64_t mask = (1ull << a.nb) - 1ull;
@@ -160,60 +212,55 @@ __global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __rest
                     tx = (T)a.xs[b0 + tc + t]; ty = (T)a.ys[b0 + tc + t]; tz = (T)a.zs[b0 + tc + t];
                 }
             }
-            float hx = 0.f, hy = 0.f, hz = 0.f, hp = 0.f, lx = 0.f, ly = 0.f, lz = 0.f, lp = 0.f;
-            double dx64 = 0.0, dy64 = 0.0, dz64 = 0.0, dp64 = 0.0;
-            for (uint32_t q = q0; q < q1; ++q) {
-                const int A = (int)(a.p2p_keys[q] & mask);
-                const int a0 = a.t.begin[A], nA = a.t.end[A] - a0;
-                float ox = 0.f, oy = 0.f, oz = 0.f;
-                if (sizeof(T) == 4) {
-                    const float4 ah = a.zhi[A], al = a.zlo[A];
-                    ox = (ah.x - bh.x) + (al.x - bl.x);
-                    oy = (ah.y - bh.y) + (al.y - bl.y);
-                    oz = (ah.z - bh.z) + (al.z - bl.z);
-                }
-                for (int s0 = 0; s0 < nA; s0 += 64) {
-                    const int ns = nA - s0 < 64 ? nA - s0 : 64;
-                    __syncwarp();
-                    for (int l = lane; l < ns; l += 32) {
+            NearAcc<T> acc;
+            uint32_t q = q0;
+            int soff = 0;
+            while (q < q1) {
+                // pack source leaves (or a piece of an oversized one) into the stage
+                __syncwarp();
+                int cnt = 0;
+                bool selfin = false;
+                while (q < q1) {
+                    const int A = (int)(a.p2p_keys[q] & mask);
+                    const int a0 = a.t.begin[A], nA = a.t.end[A] - a0;
+                    const int rem = nA - soff;
+                    int take = rem;
+                    if (cnt + take > kStageCap) {
+                        if (cnt > 0) break;
+                        take = kStageCap;
+                    }
+                    float ox = 0.f, oy = 0.f, oz = 0.f;
+                    if (sizeof(T) == 4) {
+                        const float4 ah = a.zhi[A], al = a.zlo[A];
+                        ox = (ah.x - bh.x) + (al.x - bl.x);
+                        oy = (ah.y - bh.y) + (al.y - bl.y);
+                        oz = (ah.z - bh.z) + (al.z - bl.z);
+                    }
+                    for (int l = lane; l < take; l += 32) {
+                        const int jj = a0 + soff + l;
                         Body4<T> v;
                         if (sizeof(T) == 4) {
-                            const float4 u = a.prel[a0 + s0 + l];
+                            const float4 u = a.prel[jj];
                             v = {(T)(u.x + ox), (T)(u.y + oy), (T)(u.z + oz), (T)u.w};
                         } else {
-                            const int jj = a0 + s0 + l;
                             v = {(T)a.xs[jj], (T)a.ys[jj], (T)a.zs[jj], (T)a.ms[jj]};
                         }
-                        sm[l] = v;
+                        sm[cnt + l] = v;
                     }
-                    __syncwarp();
-                    if (!act) continue;
-                    T px = T(0), py = T(0), pz = T(0), pp = T(0);
-#pragma unroll 4
-                    for (int k = sub; k < ns; k += G) {
-                        const Body4<T> sv = sm[k];
-                        const T dx = sv.x - tx, dy = sv.y - ty, dz = sv.z - tz;
-                        const T r2 = dx * dx + dy * dy + dz * dz;
-                        T rinv;
-                        if (sizeof(T) == 4) rinv = (r2 > T(0)) ? (T)rsqrtf((float)r2) : T(0);
-                        else rinv = (r2 > T(0)) ? T(1) / (T)sqrt((double)r2) : T(0);
-                        const T mr = sv.w * rinv;
-                        const T mr3 = mr * rinv * rinv;
-                        px += mr3 * dx;
-                        py += mr3 * dy;
-                        pz += mr3 * dz;
-                        pp += mr;
-                    }
-                    if (sizeof(T) == 4) {
-                        two_sum(hx, lx, (float)px);
-                        two_sum(hy, ly, (float)py);
-                        two_sum(hz, lz, (float)pz);
-                        two_sum(hp, lp, (float)pp);
-                    } else {
-                        dx64 += (double)px; dy64 += (double)py; dz64 += (double)pz; dp64 += (double)pp;
-                    }
+                    selfin |= (A == B);
+                    cnt += take;
+                    if (take < rem) { soff += take; break; }
+                    soff = 0;
+                    ++q;
                 }
+                __syncwarp();
+                if (!act) continue;
+                if (selfin) p2p_pack<T, true>(sm, cnt, sub, G, tx, ty, tz, acc);
+                else p2p_pack<T, false>(sm, cnt, sub, G, tx, ty, tz, acc);
             }
+            float &hx = acc.hx, &hy = acc.hy, &hz = acc.hz, &hp = acc.hp;
+            float &lx = acc.lx, &ly = acc.ly, &lz = acc.lz, &lp = acc.lp;
+            double &dx64 = acc.dx, &dy64 = acc.dy, &dz64 = acc.dz, &dp64 = acc.dp;
             // combine the G sub-lanes of each target in sub-lane order
             const int leader = t * G;
             for (int s = 1; s < G; ++s) {

@@ -25,7 +25,36 @@ struct WalkCells {
     const double* binom;  // C(p, k), k = 0..p
     int p;
     double eps;
+    // FP32 screen: double-float centres (zhi.w = hat scale s), sizes, and the
+    // scaled degree norms Phat_k = P_k / s^k
+    const float4* zhi;
+    const float4* zlo;
+    const float* r32;
+    const float* Phat;
 };
+
+// Relative margins of the FP32 screen. Its error is below 1e-5 (positive
+// terms only, at most ~3(p+2) roundings of 2^-24 each plus the inputs'
+// rounding), so outside the margin the FP32 decision equals the FP64 one.
+constexpr float kThetaMargin = 1e-5f * 4.0f;
+constexpr float kMacMargin = 1e-4f;
+
+// FP32 estimate of E_{A->B} M_A / r^2: pre/r^2 sum_k C(p,k) Phat_k x^k y^{p-k}
+// with x = s_A / r and y = r_B / r (Horner over k ascending).
+__device__ __forceinline__ float mac_lhs32(const WalkCells& c, int a, float ra, float rb, float sa,
+                                           float r, const float* binom32) {
+    const float sum = ra + rb;
+    const float pre = (sum > 0.0f) ? 8.0f * fmaxf(ra, rb) / sum : 4.0f;
+    const float ir = 1.0f / r;
+    const float x = sa * ir, y = rb * ir;
+    const float* Pa = c.Phat + (size_t)(c.p + 1) * a;
+    float h = 0.0f, xk = 1.0f;
+    for (int k = 0; k <= c.p; ++k) {
+        h = h * y + binom32[k] * Pa[k] * xk;
+        xk *= x;
+    }
+    return pre * h * ir * ir;
+}
 
 // E_{A->B} M_A / r^2 of Sec. 2.3 (reading R8), Horner over k ascending.
 __device__ double mac_lhs(const WalkCells& c, int a, double ra, double rb, double r, double r2) {
@@ -66,6 +95,10 @@ __global__ void __launch_bounds__(256) k_walk_step(WalkCells c, const int2* __re
                                                    int2* __restrict__ leaf_list,
                                                    unsigned long long* cnt_leaf, int64_t cap_leaf,
                                                    unsigned* err) {
+    __shared__ float binom32[kMaxP + 1];
+    if (threadIdx.x <= (unsigned)c.p) binom32[threadIdx.x] = (float)c.binom[threadIdx.x];
+    __syncthreads();
+    const float eps32 = (float)c.eps;
     const int64_t nin_raw = (int64_t)*cnt_in;
     const int64_t nin = nin_raw < cap_out ? nin_raw : cap_out;  // both frontiers hold cap_out pairs
     const int lane = threadIdx.x & 31;
@@ -85,18 +118,53 @@ __global__ void __launch_bounds__(256) k_walk_step(WalkCells c, const int2* __re
                 if (nca == 0) n_leaf = 1;
                 else { split_kind = 1; n_next = (unsigned)(nca * (nca + 1) / 2); }
             } else {
-                const double* za = c.zc + 3 * a;
-                const double* zb = c.zc + 3 * b;
-                const double dx = zb[0] - za[0], dy = zb[1] - za[1], dz = zb[2] - za[2];
-                const double r2 = dx * dx + dy * dy + dz * dz;
-                const double r = sqrt(r2);
-                const double ra = c.r[a], rb = c.r[b];
-                bool accept = ra + rb < r;  // theta = (r_A + r_B)/r < 1 (reading R6)
-                if (MODE == 1 && accept) {
-                    const double lab = mac_lhs(c, a, ra, rb, r, r2);
-                    const double lba = mac_lhs(c, b, rb, ra, r, r2);
-                    accept = lab < c.eps * (double)c.fmin[b] && lba < c.eps * (double)c.fmin[a];
+                // FP32 screen first
+                const float4 ah = c.zhi[a], al = c.zlo[a], bh = c.zhi[b], bl = c.zlo[b];
+                const float fx = (bh.x - ah.x) + (bl.x - al.x), fy = (bh.y - ah.y) + (bl.y - al.y),
+                            fz = (bh.z - ah.z) + (bl.z - al.z);
+                const float fr = sqrtf(fx * fx + fy * fy + fz * fz);
+                const float fra = c.r32[a], frb = c.r32[b];
+                int theta = 2;  // 0: fails, 1: passes, 2: undecided
+                if (fra + frb < fr * (1.0f - kThetaMargin)) theta = 1;
+                else if (fra + frb > fr * (1.0f + kThetaMargin)) theta = 0;
+                bool accept;
+                double r2 = 0.0, r = 0.0;
+                bool have64 = false;
+                if (theta == 2) {
+                    // theta = (r_A + r_B)/r < 1 in FP64 (reading R6)
+                    const double* za = c.zc + 3 * a;
+                    const double* zb = c.zc + 3 * b;
+                    const double dx = zb[0] - za[0], dy = zb[1] - za[1], dz = zb[2] - za[2];
+                    r2 = dx * dx + dy * dy + dz * dz;
+                    r = sqrt(r2);
+                    have64 = true;
+                    accept = c.r[a] + c.r[b] < r;
+                } else {
+                    accept = theta == 1;
                 }
+                if (MODE == 1 && accept) {
+                    const float lab32 = mac_lhs32(c, a, fra, frb, ah.w, fr, binom32);
+                    const float lba32 = mac_lhs32(c, b, frb, fra, bh.w, fr, binom32);
+                    const float rb32 = eps32 * c.fmin[b], ra32 = eps32 * c.fmin[a];
+                    if (lab32 < rb32 * (1.0f - kMacMargin) && lba32 < ra32 * (1.0f - kMacMargin)) {
+                        accept = true;
+                    } else if (lab32 > rb32 * (1.0f + kMacMargin) || lba32 > ra32 * (1.0f + kMacMargin)) {
+                        accept = false;
+                    } else {
+                        if (!have64) {
+                            const double* za = c.zc + 3 * a;
+                            const double* zb = c.zc + 3 * b;
+                            const double dx = zb[0] - za[0], dy = zb[1] - za[1], dz = zb[2] - za[2];
+                            r2 = dx * dx + dy * dy + dz * dz;
+                            r = sqrt(r2);
+                        }
+                        const double ra = c.r[a], rb = c.r[b];
+                        const double lab = mac_lhs(c, a, ra, rb, r, r2);
+                        const double lba = mac_lhs(c, b, rb, ra, r, r2);
+                        accept = lab < c.eps * (double)c.fmin[b] && lba < c.eps * (double)c.fmin[a];
+                    }
+                }
+                const double ra = c.r[a], rb = c.r[b];
                 if (accept) n_acc = 1;
                 else if (nca == 0 && ncb == 0) n_leaf = 1;
                 else {
@@ -255,9 +323,10 @@ inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) /
 }  // namespace
 
 int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* r, const double* P,
-                   const float* fmin, int p, double eps, const double* binom_row, WalkBuffers& wb,
+                   const float* fmin, int p, double eps, const double* binom_row, const float4* zhi,
+                   const float4* zlo, const float* r32, const float* Phat, WalkBuffers& wb,
                    DevScalars* ds, DevScalars* h_ds, cudaStream_t st) {
-    WalkCells c{t.nchild, t.first_child, zc, r, P, fmin, binom_row, p, eps};
+    WalkCells c{t.nchild, t.first_child, zc, r, P, fmin, binom_row, p, eps, zhi, zlo, r32, Phat};
     (k_walk_init<<<1, 256, 0, st>>>(wb.front0, ds->cnt, ds->list_cnt, kMaxWalkIters + 2, mode), note_launch());
     int2* acc_list = wb.out[mode == 0 ? 0 : 2];
     int2* leaf_list = wb.out[mode == 0 ? 1 : 3];

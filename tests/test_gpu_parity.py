@@ -71,7 +71,7 @@ def test_tree_geometry_estimate_and_lists_bit_exact(n, leaf):
         assert np.array_equal(sorted_pairs(f.export_pairs(which)), sorted_pairs(run.pairs(which))), which
 
 
-@pytest.mark.parametrize("n,p,eps", [(4096, 8, 1e-7), (20000, 6, 1e-6), (20000, 10, 1e-8), (3000, 14, 1e-5), (2000, 20, 1e-9)])
+@pytest.mark.parametrize("n,p,eps", [(4096, 8, 1e-7), (20000, 6, 1e-6), (20000, 10, 1e-8), (3000, 14, 1e-5), (3000, 16, 1e-8), (2000, 20, 1e-9), (1500, 30, 1e-10)])
 def test_fp64_forces_match_oracle_fmm(n, p, eps):
     pos, _, m = ics.plummer(n, 7 + n + p)
     _, acc, pot = solve(pos, m, p=p, eps=eps, precision="fp64")
