@@ -144,6 +144,27 @@ int fmm_export_pairs(const fmm_ctx* ctx, int which, int64_t* count, int32_t* pai
  * blocks then sine blocks) to HOST memory; ncos/nsin receive the counts. */
 int fmm_export_swap(int64_t* ncos, int64_t* nsin, double* cos_blocks, double* sin_blocks);
 
+/* Bounding cube, Morton keys and their sort for up to 262144 bodies, with
+ * no device allocation: the paper has no counterpart (it is a service for
+ * callers that cannot call cudaMalloc, e.g. under a device-memory budget owned
+ * by another allocator, or in a loop where an allocation's latency or failure
+ * is not acceptable).
+ * x, y, z: n device FP64 positions. Outputs (device): keys[n] sorted Morton
+ * keys, perm[n] the caller index of each sorted body (ties keep input order),
+ * box[4] (may be NULL) the cube centre and half-size. These are exactly the
+ * keys and permutation fmm_solve builds its octree from.
+ * Scratch: a static device array of about 4.3 MB in the library, held by every
+ * GPU that loads it until the process exits. The first call on a device looks
+ * up the array's address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture. All calls share the array: calls that overlap on
+ * the GPU (other streams, other host threads) race. The call synchronises its
+ * stream before returning.
+ * Errors: FMM_ERR_ARG for n outside [0, 262144] or NULL pointers,
+ * FMM_ERR_NONFINITE for a NaN or infinite position, FMM_ERR_CUDA; the message
+ * is fmm_last_error(NULL). */
+int fmm_morton_sort_noalloc(int64_t n, const double* x, const double* y, const double* z,
+                            uint64_t* keys, int64_t* perm, double* box, void* cuda_stream);
+
 /* Message of the last error on this context (or of the last failed
  * fmm_create when ctx is NULL). Never NULL. */
 const char* fmm_last_error(const fmm_ctx* ctx);

@@ -77,6 +77,7 @@ def lib():
             L.fmm_export_geometry.argtypes = [vp] + [dp] * 6
             L.fmm_export_pairs.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), dp]
             L.fmm_export_swap.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), dp, dp]
+            L.fmm_morton_sort_noalloc.argtypes = [i64, dp, dp, dp, dp, dp, dp, vp]
             L.fmm_last_error.argtypes = [vp]
             L.fmm_last_error.restype = ctypes.c_char_p
             _lib = L
@@ -229,3 +230,23 @@ def export_swap():
     c, s = np.zeros(nc.value), np.zeros(ns.value)
     lib().fmm_export_swap(ctypes.byref(nc), ctypes.byref(ns), c.ctypes.data, s.ctypes.data)
     return c, s
+
+
+NOALLOC_MAX_N = 262144
+
+
+def morton_sort_noalloc(x, y, z, stream=None):
+    """Bounding cube, Morton keys and sort of up to 262144 bodies without any
+    device allocation inside the library (fmm_morton_sort_noalloc): returns
+    device tensors (keys as int64 holding the unsigned keys, perm int64, box
+    float64[4] = cube centre and half-size)."""
+    import torch  # noqa: PLC0415
+    n = x.numel()
+    keys = torch.empty(n, dtype=torch.int64, device=x.device)
+    perm = torch.empty(n, dtype=torch.int64, device=x.device)
+    box = torch.empty(4, dtype=torch.float64, device=x.device)
+    rc = lib().fmm_morton_sort_noalloc(n, _ptr(x), _ptr(y), _ptr(z), _ptr(keys), _ptr(perm), _ptr(box),
+                                       _stream_handle(stream))
+    if rc != 0:
+        raise FmmError(rc, lib().fmm_last_error(None).decode())
+    return keys, perm, box

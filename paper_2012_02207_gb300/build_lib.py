@@ -20,10 +20,10 @@ LIBDIR = os.path.join(HERE, "_lib")
 GEN = os.path.join(LIBDIR, "gen")
 LIB = os.path.join(LIBDIR, "libgbfmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NO_FMA = {"tree.cu", "walk.cu"}
+NO_FMA = {"tree.cu", "walk.cu", "noalloc.cu"}
 M2L32_ORDERS = [4, 6, 8, 10, 12, 14]
 EXTRA_FLAGS = os.environ.get("GBFMM_NVCC_FLAGS", "").split()  # extra nvcc flags for experiments  # orders of the FP32 register M2L kernel
-SOURCES = ["api.cu", "sort.cu", "tree.cu", "walk.cu", "expansions.cu", "m2l.cu", "p2p.cu"]
+SOURCES = ["api.cu", "sort.cu", "tree.cu", "walk.cu", "expansions.cu", "m2l.cu", "p2p.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

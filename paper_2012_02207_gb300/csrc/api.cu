@@ -44,6 +44,11 @@ T* as(Buf& b) { return reinterpret_cast<T*>(b.ptr); }
 
 }  // namespace
 
+namespace gbfmm {
+// message returned by fmm_last_error(NULL) (also used by the no-allocation entry point)
+void set_global_error(const char* msg) { g_create_error = msg; }
+}  // namespace gbfmm
+
 struct fmm_ctx {
     fmm_config cfg{};
     int device = 0;
