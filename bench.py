@@ -31,11 +31,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_BODIES = 1 << 20
+# fastest tuned configurations with RMS <= 1e-6 (paper_2012_02207_gb300/tuned_eps.json)
 P_DEFAULT = 10
-EPS_DEFAULT = 1e-7
+EPS_DEFAULT = 1e-8
+P_FP64 = 12
+EPS_FP64 = 1e-8
 LEAF = 64
 SAMPLE_N = 1 << 16          # bounded CPU sample for the oracle timings
-ERR_SAMPLE = 4096           # bodies whose force error is measured per precision
+ERR_SAMPLE = 65536          # bodies whose force error is measured per precision
 METRIC = "particles/s per FMM force solve at N=1e6: mixed vs FP64 at RMS err<=1e-6"
 N_SM = 152
 FP32_LANES_PER_SM = 128
@@ -191,6 +194,8 @@ def main():
     ap.add_argument("--p", type=int, default=P_DEFAULT)
     ap.add_argument("--eps", type=float, default=EPS_DEFAULT)
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--p64", type=int, default=P_FP64)
+    ap.add_argument("--eps64", type=float, default=EPS_FP64)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -270,7 +275,7 @@ def main():
     err_mixed, med_mixed = rms_err(*outs[:3])
 
     # FP64 mode on the same inputs (slow; a few steps)
-    fp64 = gb.FMM(p=args.p, eps=args.eps, leaf_size=LEAF, precision="fp64")
+    fp64 = gb.FMM(p=args.p64, eps=args.eps64, leaf_size=LEAF, precision="fp64")
     t64, s64 = timed_solves(fp64, args.fp64_steps, 1)
     ms64 = sum(t64) / len(t64)
     err64, med64 = rms_err(*outs[:3])
@@ -321,7 +326,7 @@ def main():
                        "leaf_size": LEAF, "precision": "mixed", "l2": "flushed (512 MB write) before each step",
                        "parallelism": f"replicas{world}"},
             "fp64": {"value": value64, "ms_per_step": ms64, "steps": args.fp64_steps, "rms_err": err64,
-                     "median_err": med64},
+                     "median_err": med64, "p": args.p64, "eps": args.eps64},
             "speedup_vs_fp64": value / value64,
             "rms_err": err_mixed, "median_err": med_mixed, "err_sample": ERR_SAMPLE,
             "phases_ms": {k: statistics.median(s[k] for s in stats) for k in
