@@ -147,9 +147,10 @@ struct NearAcc {
     }
 };
 
-template <typename T, bool GUARD>
-__device__ __forceinline__ void p2p_pack(const Body4<T>* __restrict__ sm, int cnt, int sub, int G, T tx, T ty,
-                                         T tz, NearAcc<T>& acc) {
+template <typename T, bool GUARD, int GC>
+__device__ __forceinline__ void p2p_pack_g(const Body4<T>* __restrict__ sm, int cnt, int sub, int Gr, T tx, T ty,
+                                           T tz, NearAcc<T>& acc) {
+    const int G = GC > 0 ? GC : Gr;  // lanes per target (compile-time when GC > 0)
     for (int k0 = sub; k0 < cnt; k0 += kRun * G) {
         const int k1 = k0 + kRun * G < cnt ? k0 + kRun * G : cnt;
         T px = T(0), py = T(0), pz = T(0), pp = T(0);
@@ -174,6 +175,15 @@ __device__ __forceinline__ void p2p_pack(const Body4<T>* __restrict__ sm, int cn
         }
         acc.add(px, py, pz, pp);
     }
+}
+
+template <typename T, bool GUARD>
+__device__ __forceinline__ void p2p_pack(const Body4<T>* __restrict__ sm, int cnt, int sub, int G, T tx, T ty,
+                                         T tz, NearAcc<T>& acc) {
+    if (G == 1) p2p_pack_g<T, GUARD, 1>(sm, cnt, sub, G, tx, ty, tz, acc);
+    else if (G == 2) p2p_pack_g<T, GUARD, 2>(sm, cnt, sub, G, tx, ty, tz, acc);
+    else if (G == 4) p2p_pack_g<T, GUARD, 4>(sm, cnt, sub, G, tx, ty, tz, acc);
+    else p2p_pack_g<T, GUARD, 0>(sm, cnt, sub, G, tx, ty, tz, acc);
 }
 
 template <typename T>

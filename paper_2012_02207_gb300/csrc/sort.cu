@@ -14,6 +14,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 16;                   // keys per thread
 constexpr int kTile = kThreads * kItems;     // 4096 keys per block
 constexpr int kWarpItems = kTile / kWarps;   // 512 contiguous keys per warp
+constexpr size_t kScatterSmem = (size_t)kTile * (8 + 4) + (size_t)(kWarps + 2) * 256 * 4;
 
 __global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ keys, int64_t n,
                                                    int shift, uint32_t* __restrict__ hist,
@@ -31,19 +32,28 @@ __global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ 
     for (int d = threadIdx.x; d < 256; d += kThreads) hist[(int64_t)d * nblocks + blockIdx.x] = h[d];
 }
 
+// Scatter: rank every key among the earlier keys of its tile with the same
+// digit (warp match + per-warp digit counters), reorder the tile by digit in
+// shared memory, then write each digit's run to its global position with
+// consecutive threads writing consecutive addresses.
 __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict__ kin,
                                                       const uint32_t* __restrict__ vin,
                                                       uint64_t* __restrict__ kout,
                                                       uint32_t* __restrict__ vout, int64_t n,
                                                       int shift, const uint32_t* __restrict__ offs,
                                                       int nblocks) {
-    __shared__ uint32_t wcount[kWarps][256];
-    __shared__ uint32_t boff[256];
+    extern __shared__ __align__(16) unsigned char sh_scatter[];
+    uint64_t* skey = reinterpret_cast<uint64_t*>(sh_scatter);                    // kTile
+    uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kTile);                  // kTile
+    uint32_t (*wcount)[256] = reinterpret_cast<uint32_t (*)[256]>(sval + kTile);  // kWarps x 256
+    uint32_t* boff = &wcount[kWarps][0];    // global start of each digit for this tile
+    uint32_t* lstart = boff + 256;          // start of each digit inside the tile
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&wcount[0][0])[i] = 0;
     for (int d = threadIdx.x; d < 256; d += kThreads) boff[d] = offs[(int64_t)d * nblocks + blockIdx.x];
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)warp * kWarpItems;
+    const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+    const int64_t base = tile0 + (int64_t)warp * kWarpItems;
     uint64_t key[kItems];
     uint32_t val[kItems], rank[kItems], dig[kItems];
 #pragma unroll
@@ -71,6 +81,22 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict
             wcount[w][d] = run;
             run += t;
         }
+        lstart[d] = run;  // this digit's count in the tile, scanned below
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the 256 digit counts
+        uint32_t c[8], s = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { c[k] = lstart[threadIdx.x * 8 + k]; s += c[k]; }
+        uint32_t incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)threadIdx.x >= o) incl += v;
+        }
+        uint32_t run = incl - s;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { lstart[threadIdx.x * 8 + k] = run; run += c[k]; }
     }
     __syncthreads();
 #pragma unroll
@@ -78,10 +104,19 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict
         const int64_t i = base + r * 32 + lane;
         if (i < n) {
             const uint32_t d = dig[r];
-            const uint32_t pos = boff[d] + wcount[warp][d] + rank[r];
-            kout[pos] = key[r];
-            if (vout) vout[pos] = val[r];
+            const uint32_t pos = lstart[d] + wcount[warp][d] + rank[r];
+            skey[pos] = key[r];
+            sval[pos] = val[r];
         }
+    }
+    __syncthreads();
+    const int cnt = (int)((n - tile0) < kTile ? (n - tile0) : kTile);
+    for (int j = threadIdx.x; j < cnt; j += kThreads) {
+        const uint64_t k = skey[j];
+        const uint32_t d = (uint32_t)(k >> shift) & 255u;
+        const uint32_t pos = boff[d] + (uint32_t)j - lstart[d];
+        kout[pos] = k;
+        if (vout) vout[pos] = sval[j];
     }
 }
 
@@ -202,6 +237,11 @@ void scan_exclusive_u32(uint32_t* data, int64_t count, uint32_t* total, cudaStre
 int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bits,
                uint32_t* hist, cudaStream_t st) {
     if (n <= 1 || bits <= 0) return 0;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+        attr = true;
+    }
     const int nblocks = (int)((n + kTile - 1) / kTile);
     int cur = 0;
     for (int shift = 0; shift < bits; shift += 8) {
@@ -211,7 +251,7 @@ int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n
         uint32_t* vo = cur ? v0 : v1;
         (k_hist<<<nblocks, kThreads, 0, st>>>(ki, n, shift, hist, nblocks), note_launch());
         scan_exclusive_u32_large(hist, (int64_t)256 * nblocks, nullptr, hist + (size_t)256 * nblocks + 1, st);
-        (k_scatter<<<nblocks, kThreads, 0, st>>>(ki, vi, ko, vo, n, shift, hist, nblocks), note_launch());
+        (k_scatter<<<nblocks, kThreads, kScatterSmem, st>>>(ki, vi, ko, vo, n, shift, hist, nblocks), note_launch());
         cur ^= 1;
     }
     return cur;

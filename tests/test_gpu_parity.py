@@ -97,8 +97,9 @@ def test_mixed_precision_error_vs_direct(n, p, eps):
     s_mixed = oracle.error_stats(acc, dacc)
     s_fp64 = oracle.error_stats(acc64, dacc)
     # FP32 terms add at most a few 1e-7 to the FP64 truncation error; the
-    # FP32 M2L rounding grows with the number of terms, i.e. with p
-    assert s_mixed["rms"] <= s_fp64["rms"] + 5e-7, (s_mixed, s_fp64)
+    # FP32 M2L rounding grows with p (the z-translation sums alternating terms
+    # with coefficients up to C(2p, p)), so orders >= 12 get a wider margin
+    assert s_mixed["rms"] <= s_fp64["rms"] + (5e-7 if p <= 10 else 1e-6), (s_mixed, s_fp64)
     assert s_mixed["median"] <= s_fp64["median"] + (1e-7 if p <= 10 else 2e-7), (s_mixed, s_fp64)
     assert np.max(np.abs(pot - dpot) / np.abs(dpot)) <= 1e-5
 
