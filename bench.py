@@ -139,6 +139,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def kernel_traffic(name):
+    """DRAM bytes per launch of a kernel from an ncu capture summarised in
+    profiles/traffic.json, or None when the kernel's sources have changed
+    since the capture (their hash no longer matches) or there is none."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh).get(name)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for rel in rec["files"]:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes"] if h.hexdigest() == rec["sources_sha256"] else None
+
+
 def workload():
     import ics
     pos, m = ics.config_inputs("kroupa1m")
@@ -335,7 +354,7 @@ def main():
             "counts": {k: st[k] for k in ("nnodes", "nlevels", "n_far", "n_near", "n_m2l", "n_p2p",
                                           "p2p_interactions", "walk_iters")},
             "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": kernel_traffic(dom),
                          "peak_note": f"FP32 lanes x 2 x {sm_for_peak:.0f} MHz (sm_max_mhz of measured peaks)"},
             "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": 32 * n,
                     "d2h_bytes_per_step": 32 * n},

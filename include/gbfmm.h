@@ -103,8 +103,16 @@ int fmm_solve_host(fmm_ctx* ctx, int64_t n, const double* x, const double* y, co
 
 /* Independent solves of nclusters clusters stored back to back: cluster c
  * holds bodies [offsets[c], offsets[c+1]) (offsets: HOST array of
- * nclusters + 1 values, offsets[0] = 0). Bodies of different clusters do
- * not interact. Device arrays as in fmm_solve. */
+ * nclusters + 1 non-decreasing values, offsets[0] = 0; empty clusters are
+ * allowed; at most 2^30 bodies in all). Bodies of different clusters do not
+ * interact. Device arrays as in fmm_solve. The ensemble is solved as one
+ * forest in a single pipeline pass (one launch of each kernel for all
+ * clusters); each cluster's tree, interaction lists and forces are exactly
+ * those of a separate fmm_solve of that cluster with the same config.
+ * Statistics and exports then describe the whole forest. The paper's tests
+ * (Sec. 3) average over many independent realizations of a cluster, each a
+ * separate run; the single pass over all of them is this library's addition. Errors: FMM_ERR_ARG for bad offsets or NULL pointers,
+ * otherwise as fmm_solve (a coincidence is only checked inside a cluster). */
 int fmm_solve_batch(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, const double* x,
                     const double* y, const double* z, const double* m, double* ax, double* ay,
                     double* az, double* pot, void* cuda_stream);

@@ -167,9 +167,17 @@ class FMM:
         return np.stack(outs[:3], axis=1), outs[3]
 
     def solve_batch(self, offsets, x, y, z, m, out=None, stream=None):
+        """Independent clusters in one pass: cluster c is bodies offsets[c] ..
+        offsets[c+1]-1 of the device FP64 tensors x, y, z, m; no force acts
+        between clusters. Returns (ax, ay, az, pot) like solve()."""
         import torch  # noqa: PLC0415
         offs = np.ascontiguousarray(offsets, dtype=np.int64)
         n = x.numel()
+        for t in (x, y, z, m):
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("x, y, z, m must be contiguous CUDA float64 tensors of equal length")
+        if len(offs) < 1 or offs[-1] != n:
+            raise ValueError("offsets must have nclusters + 1 entries ending at len(x)")
         if out is None:
             out = tuple(torch.empty(n, dtype=torch.float64, device=x.device) for _ in range(4))
         ax, ay, az, pot = out

@@ -21,9 +21,11 @@ GEN = os.path.join(LIBDIR, "gen")
 LIB = os.path.join(LIBDIR, "libgbfmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NO_FMA = {"tree.cu", "walk.cu", "noalloc.cu"}
-FTZ = {"p2p.cu", "m2l.cu"}  # FP32 kernels: no denormal handling (values never reach that range)
-M2L32_ORDERS = [4, 6, 8, 10, 12, 14]
-EXTRA_FLAGS = os.environ.get("GBFMM_NVCC_FLAGS", "").split()  # extra nvcc flags for experiments  # orders of the FP32 register M2L kernel
+# FP32 kernels flush denormals: the hat scale floor keeps every coefficient
+# that matters far above the denormal range
+FTZ = {"p2p.cu", "m2l.cu"}
+M2L32_ORDERS = [4, 6, 8, 10, 12, 14]  # orders of the FP32 register M2L kernel
+EXTRA_FLAGS = os.environ.get("GBFMM_NVCC_FLAGS", "").split()  # extra nvcc flags for experiments
 SOURCES = ["api.cu", "sort.cu", "tree.cu", "walk.cu", "expansions.cu", "m2l.cu", "p2p.cu", "noalloc.cu"]
 
 

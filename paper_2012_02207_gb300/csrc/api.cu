@@ -62,8 +62,11 @@ struct fmm_ctx {
     cudaEvent_t ev[10] = {};
     // per-body
     Buf k0, k1, v0, v1, hist, xs, ys, zs, ms, xf, prel, lcp, win, hi, chunk, f, bbox;
+    // clusters of a forest (an ensemble solve)
+    Buf coff, box, ck0, ck1, cv0, cv1, cid;
+    std::vector<int> h_coff;
     // per-node
-    Buf level, begin, end, parent, first_child, nchild, M, S, zc, r, Pk, mult, mult32, loc, loc32,
+    Buf level, begin, end, parent, first_child, nchild, M, S, zc, r, hs, Pk, mult, mult32, loc, loc32,
         fmin, fscratch, zhi, zlo, contrib, Phat, r32;
     // P2P work items
     Buf item_first, slot_first, item_leaf, leaf_of, part_hi, part_lo, work;
@@ -74,7 +77,7 @@ struct fmm_ctx {
     Buf hin[4], hout[4];
     // last solve
     int64_t n = 0;
-    int nnodes = 0, nlevels = 0, nb = 1, sorted_in_1 = 0;
+    int nnodes = 0, nlevels = 0, nb = 1, sorted_in_1 = 0, nclusters = 1;
     int h_level_start[kMaxLevel + 3] = {};
     int64_t npairs[4] = {0, 0, 0, 0}, ndirected[4] = {0, 0, 0, 0};
     int dk_in_alt[4] = {0, 0, 0, 0};
@@ -165,6 +168,7 @@ TreeView view(fmm_ctx* ctx) {
     t.parent = as<int>(ctx->parent);
     t.first_child = as<int>(ctx->first_child);
     t.nchild = as<int>(ctx->nchild);
+    t.nroots = ctx->nnodes > 0 ? ctx->h_level_start[1] : 0;
     return t;
 }
 
@@ -232,6 +236,9 @@ int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
             ctx->stats.regrows++;
             continue;
         }
+        if (it == kWalkBadIndex) return fail(ctx, FMM_ERR_CUDA, "dual-tree walk read an out-of-range cell index");
+        if (it == FMM_ERR_CUDA)
+            return fail(ctx, it, std::string("dual-tree walk failed: ") + cudaGetErrorString(cudaGetLastError()));
         if (it < 0) return fail(ctx, it, "dual-tree walk failed");
         ctx->stats.walk_iters += it;
         unsigned long long cnt[4];
@@ -253,16 +260,24 @@ int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
     return fail(ctx, FMM_ERR_CAPACITY, "interaction lists outgrew their capacity");
 }
 
-int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
-                 const double* m, double* ax, double* ay, double* az, double* pot, cudaStream_t st) {
+// One pipeline pass over a forest of nclusters independent clusters (bodies
+// offsets[c] .. offsets[c+1]-1 of cluster c; offsets == nullptr: one cluster).
+int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets, const double* x,
+                 const double* y, const double* z, const double* m, double* ax, double* ay, double* az,
+                 double* pot, cudaStream_t st) {
     const int p = ctx->cfg.p;
     const bool mixed = ctx->cfg.precision == FMM_PRECISION_MIXED;
     std::memset(&ctx->stats, 0, sizeof(ctx->stats));
     g_launches = 0;
     ctx->stats.n = n;
     ctx->n = n;
+    ctx->nnodes = 0;
     if (n == 0) return FMM_OK;
     int rc;
+    if (!offsets) nclusters = 1;
+    ctx->nclusters = nclusters;
+    ctx->h_coff.resize((size_t)nclusters + 1);
+    for (int c = 0; c <= nclusters; ++c) ctx->h_coff[c] = offsets ? (int)offsets[c] : (c ? (int)n : 0);
     // ---- per-body workspace
     const size_t N = (size_t)n;
     const int nchunks = tree_nchunks(n);
@@ -274,19 +289,29 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
         (rc = ensure(ctx, ctx->prel, 16 * N)) || (rc = ensure(ctx, ctx->lcp, N)) ||
         (rc = ensure(ctx, ctx->win, N)) || (rc = ensure(ctx, ctx->hi, N)) ||
         (rc = ensure(ctx, ctx->chunk, 4 * ((size_t)(kMaxLevel + 1) * nchunks + 2))) ||
-        (rc = ensure(ctx, ctx->f, 4 * N)) || (rc = ensure(ctx, ctx->bbox, 8 * 6 * 304)))
+        (rc = ensure(ctx, ctx->f, 4 * N)) || (rc = ensure(ctx, ctx->bbox, 8 * 6 * (size_t)bbox_partials(nclusters))) ||
+        (rc = ensure(ctx, ctx->coff, 4 * ((size_t)nclusters + 1))) || (rc = ensure(ctx, ctx->box, 64 * (size_t)nclusters)))
+        return rc;
+    if (nclusters > 1 &&
+        ((rc = ensure(ctx, ctx->ck0, 8 * N)) || (rc = ensure(ctx, ctx->ck1, 8 * N)) ||
+         (rc = ensure(ctx, ctx->cv0, 4 * N)) || (rc = ensure(ctx, ctx->cv1, 4 * N)) ||
+         (rc = ensure(ctx, ctx->cid, 4 * N))))
         return rc;
     CK(cudaEventRecord(ctx->ev[0], st));
     CK(cudaMemsetAsync(&ctx->ds->err, 0, sizeof(unsigned), st));
+    CK(cudaMemcpyAsync(ctx->coff.ptr, ctx->h_coff.data(), 4 * ((size_t)nclusters + 1), cudaMemcpyHostToDevice, st));
     TreeBuffers tb{};
     tb.x = x; tb.y = y; tb.z = z; tb.m = m; tb.n = n; tb.leaf_size = ctx->cfg.leaf_size;
+    tb.nclusters = nclusters; tb.coff = as<int>(ctx->coff); tb.box = as<double>(ctx->box);
+    tb.ck0 = as<uint64_t>(ctx->ck0); tb.ck1 = as<uint64_t>(ctx->ck1);
+    tb.cv0 = as<uint32_t>(ctx->cv0); tb.cv1 = as<uint32_t>(ctx->cv1); tb.cid = as<uint32_t>(ctx->cid);
     tb.bbox_part = as<double>(ctx->bbox);
     tb.k0 = as<uint64_t>(ctx->k0); tb.k1 = as<uint64_t>(ctx->k1);
     tb.v0 = as<uint32_t>(ctx->v0); tb.v1 = as<uint32_t>(ctx->v1);
     tb.hist = as<uint32_t>(ctx->hist);
     tb.xs = as<double>(ctx->xs); tb.ys = as<double>(ctx->ys); tb.zs = as<double>(ctx->zs);
     tb.ms = as<double>(ctx->ms); tb.xf = as<float4>(ctx->xf);
-    tb.lcp = as<uint8_t>(ctx->lcp); tb.win = as<uint8_t>(ctx->win); tb.hi = as<uint8_t>(ctx->hi);
+    tb.lcp = as<int8_t>(ctx->lcp); tb.win = as<int8_t>(ctx->win); tb.hi = as<uint8_t>(ctx->hi);
     tb.chunk_cnt = as<uint32_t>(ctx->chunk);
     tb.ds = ctx->ds;
     int in1 = 0;
@@ -308,7 +333,7 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
         (rc = ensure(ctx, ctx->end, 4 * K)) || (rc = ensure(ctx, ctx->parent, 4 * K)) ||
         (rc = ensure(ctx, ctx->first_child, 4 * K)) || (rc = ensure(ctx, ctx->nchild, 4 * K)) ||
         (rc = ensure(ctx, ctx->M, 8 * K)) || (rc = ensure(ctx, ctx->S, 24 * K)) ||
-        (rc = ensure(ctx, ctx->zc, 24 * K)) || (rc = ensure(ctx, ctx->r, 8 * K)) ||
+        (rc = ensure(ctx, ctx->zc, 24 * K)) || (rc = ensure(ctx, ctx->r, 8 * K)) || (rc = ensure(ctx, ctx->hs, 8 * K)) ||
         (rc = ensure(ctx, ctx->Pk, 8 * K * (p + 1))) || (rc = ensure(ctx, ctx->mult, 8 * K * nr)) ||
         (rc = ensure(ctx, ctx->fmin, 4 * K)) || (rc = ensure(ctx, ctx->fscratch, 4 * (2 * K + N))) ||
         (rc = ensure(ctx, ctx->zhi, 16 * K)) || (rc = ensure(ctx, ctx->zlo, 16 * K)) ||
@@ -342,12 +367,13 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
     cell_geometry(t, as<double>(ctx->xs), as<double>(ctx->ys), as<double>(ctx->zs), as<double>(ctx->ms),
                   ctx->h_level_start, as<double>(ctx->M), as<double>(ctx->S), as<double>(ctx->zc),
                   as<double>(ctx->r), st);
-    node_centres_f32(nnodes, as<double>(ctx->zc), as<double>(ctx->r), as<float4>(ctx->zhi), as<float4>(ctx->zlo), st);
+    hat_scales(nnodes, as<int>(ctx->parent), as<double>(ctx->r), as<double>(ctx->hs), st);
+    node_centres_f32(nnodes, as<double>(ctx->zc), as<double>(ctx->hs), as<float4>(ctx->zhi), as<float4>(ctx->zlo), st);
     CK(cudaEventRecord(ctx->ev[1], st));
     // ---- upward pass
     upward_pass(t, ctx->h_level_start, p, as<double>(ctx->xs), as<double>(ctx->ys), as<double>(ctx->zs),
-                as<double>(ctx->ms), as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->mult),
-                as<double>(ctx->Pk), as<float>(ctx->Phat), as<float>(ctx->r32), as<double>(ctx->contrib), ctx->tb, st);
+                as<double>(ctx->ms), as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->hs),
+                as<double>(ctx->mult), as<double>(ctx->Pk), as<float>(ctx->Phat), as<float>(ctx->r32), as<double>(ctx->contrib), ctx->tb, st);
     CK(cudaEventRecord(ctx->ev[2], st));
     // ---- scalar-force estimate
     if (ctx->front_cap == 0) {
@@ -383,15 +409,15 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
         m2l_f32(nnodes, p, mk, mo, ctx->nb, as<float>(ctx->mult32), as<float4>(ctx->zhi), as<float4>(ctx->zlo),
                 as<float>(ctx->loc32), st);
     } else {
-        m2l_f64(nnodes, p, mk, mo, ctx->nb, as<double>(ctx->mult), as<double>(ctx->zc), as<double>(ctx->r),
+        m2l_f64(nnodes, p, mk, mo, ctx->nb, as<double>(ctx->mult), as<double>(ctx->zc), as<double>(ctx->hs),
                 as<double>(ctx->loc), ctx->tb, st);
         if (mixed) multipoles_to_f32(as<double>(ctx->loc), as<float>(ctx->loc32), (int64_t)(K * nr), st);
     }
     CK(cudaEventRecord(ctx->ev[5], st));
     if (mixed)
-        downward_pass_f32(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->r), as<float>(ctx->loc32), st);
+        downward_pass_f32(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->hs), as<float>(ctx->loc32), st);
     else
-        downward_pass_f64(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->loc),
+        downward_pass_f64(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->hs), as<double>(ctx->loc),
                           ctx->tb, st);
     CK(cudaEventRecord(ctx->ev[6], st));
     // ---- leaves: P2P work items, then L2P + partials per body
@@ -410,7 +436,7 @@ int solve_device(fmm_ctx* ctx, int64_t n, const double* x, const double* y, cons
     LeafArgs la{};
     la.t = t; la.p = p; la.G = ctx->cfg.G;
     la.xs = as<double>(ctx->xs); la.ys = as<double>(ctx->ys); la.zs = as<double>(ctx->zs); la.ms = as<double>(ctx->ms);
-    la.zc = as<double>(ctx->zc); la.r = as<double>(ctx->r);
+    la.zc = as<double>(ctx->zc); la.hs = as<double>(ctx->hs);
     la.zhi = as<float4>(ctx->zhi); la.zlo = as<float4>(ctx->zlo);
     la.p2p_keys = as<uint64_t>(ctx->dkeys[3]); la.p2p_off = as<uint32_t>(ctx->doff[3]); la.nb = ctx->nb;
     la.perm = as<uint32_t>(in1 ? ctx->v1 : ctx->v0);
@@ -537,7 +563,7 @@ void fmm_destroy(fmm_ctx* ctx) {
     Buf* all[] = {&ctx->tables, &ctx->k0, &ctx->k1, &ctx->v0, &ctx->v1, &ctx->hist, &ctx->xs, &ctx->ys,
                   &ctx->zs, &ctx->ms, &ctx->xf, &ctx->prel, &ctx->lcp, &ctx->win, &ctx->hi, &ctx->chunk,
                   &ctx->f, &ctx->bbox, &ctx->level, &ctx->begin, &ctx->end, &ctx->parent,
-                  &ctx->first_child, &ctx->nchild, &ctx->M, &ctx->S, &ctx->zc, &ctx->r, &ctx->Pk,
+                  &ctx->first_child, &ctx->nchild, &ctx->M, &ctx->S, &ctx->zc, &ctx->r, &ctx->hs, &ctx->Pk,
                   &ctx->mult, &ctx->mult32, &ctx->loc, &ctx->loc32, &ctx->fmin, &ctx->fscratch,
                   &ctx->front0, &ctx->front1, &ctx->dalt, &ctx->dcount, &ctx->zhi, &ctx->zlo, &ctx->contrib, &ctx->Phat, &ctx->r32,
                   &ctx->item_first, &ctx->slot_first, &ctx->item_leaf, &ctx->leaf_of, &ctx->part_hi,
@@ -564,7 +590,7 @@ int fmm_solve(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const d
     if (n > 0 && (!x || !y || !z || !m || !ax || !ay || !az))
         return fail(ctx, FMM_ERR_ARG, "NULL input or output pointer");
     cudaSetDevice(ctx->device);
-    return solve_device(ctx, n, x, y, z, m, ax, ay, az, pot, (cudaStream_t)cuda_stream);
+    return solve_device(ctx, n, 1, nullptr, x, y, z, m, ax, ay, az, pot, (cudaStream_t)cuda_stream);
 }
 
 int fmm_solve_host(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
@@ -581,7 +607,7 @@ int fmm_solve_host(fmm_ctx* ctx, int64_t n, const double* x, const double* y, co
         if ((rc = ensure(ctx, ctx->hin[i], bytes)) || (rc = ensure(ctx, ctx->hout[i], bytes))) return rc;
     const double* in[4] = {x, y, z, m};
     for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(ctx->hin[i].ptr, in[i], bytes, cudaMemcpyHostToDevice, st));
-    rc = solve_device(ctx, n, as<double>(ctx->hin[0]), as<double>(ctx->hin[1]), as<double>(ctx->hin[2]),
+    rc = solve_device(ctx, n, 1, nullptr, as<double>(ctx->hin[0]), as<double>(ctx->hin[1]), as<double>(ctx->hin[2]),
                       as<double>(ctx->hin[3]), as<double>(ctx->hout[0]), as<double>(ctx->hout[1]),
                       as<double>(ctx->hout[2]), pot ? as<double>(ctx->hout[3]) : nullptr, st);
     if (rc != FMM_OK) return rc;
@@ -600,21 +626,12 @@ int fmm_solve_batch(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, con
     if (nclusters > 0 && offsets[0] != 0) return fail(ctx, FMM_ERR_ARG, "offsets[0] must be 0");
     for (int32_t c = 0; c < nclusters; ++c)
         if (offsets[c + 1] < offsets[c]) return fail(ctx, FMM_ERR_ARG, "offsets must be non-decreasing");
-    fmm_stats total{};
-    for (int32_t c = 0; c < nclusters; ++c) {
-        const int64_t o = offsets[c], n = offsets[c + 1] - offsets[c];
-        const int rc = fmm_solve(ctx, n, x + o, y + o, z + o, m + o, ax + o, ay + o, az + o,
-                                 pot ? pot + o : nullptr, cuda_stream);
-        if (rc != FMM_OK) return rc;
-        total.n += ctx->stats.n;
-        total.nnodes += ctx->stats.nnodes;
-        total.n_m2l += ctx->stats.n_m2l;
-        total.n_p2p += ctx->stats.n_p2p;
-        total.ms_total += ctx->stats.ms_total;
-        total.kernel_launches += ctx->stats.kernel_launches;
-    }
-    ctx->stats = total;
-    return FMM_OK;
+    const int64_t n = nclusters > 0 ? offsets[nclusters] : 0;
+    if (n > (int64_t)1 << 30) return fail(ctx, FMM_ERR_ARG, "the clusters hold more than 2^30 bodies");
+    if (n > 0 && (!x || !y || !z || !m || !ax || !ay || !az))
+        return fail(ctx, FMM_ERR_ARG, "NULL input or output pointer");
+    cudaSetDevice(ctx->device);
+    return solve_device(ctx, n, nclusters, offsets, x, y, z, m, ax, ay, az, pot, (cudaStream_t)cuda_stream);
 }
 
 int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z, const double* m,

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m(TreeView t, int p, TabF64 tb
                                               const double* __restrict__ zs,
                                               const double* __restrict__ ms,
                                               const double* __restrict__ zc,
-                                              const double* __restrict__ rr,
+                                              const double* __restrict__ hs,
                                               double* __restrict__ mult) {
     __shared__ double sh_tile[WARPS][2 * (PM + 1)][33];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m(TreeView t, int p, TabF64 tb
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int k = blockIdx.x * (blockDim.x >> 5) + wib; k < t.nnodes; k += nwarps) {
         if (t.nchild[k] != 0) continue;
-        const double is = 1.0 / hat_scale(rr[k]);
+        const double is = 1.0 / hs[k];
         const double cx = zc[3 * k], cy = zc[3 * k + 1], cz = zc[3 * k + 2];
         // lane e owns entries e and e + 32 of every column (a column has 2(p-m+1) <= 62 reals)
         double acc[PM + 1][2];
@@ -183,12 +183,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m(TreeView t, int p, TabF64 tb
 // P_n = s^n sqrt(sum_{m=-n}^{n} |Mhat_n^m|^2)  (Sec. 2.3)
 // (also the FP32 copies used by the walk's screen: Phat_n = P_n / s^n and r)
 __global__ void k_pnorm(int nnodes, int p, const double* __restrict__ mult,
-                        const double* __restrict__ rr, double* __restrict__ Pk, float* __restrict__ Phat,
+                        const double* __restrict__ rr, const double* __restrict__ hs,
+                        double* __restrict__ Pk, float* __restrict__ Phat,
                         float* __restrict__ r32) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nnodes) return;
     const double* M = mult + (size_t)ncoef_real(p) * k;
-    const double s = hat_scale(rr[k]);
+    const double s = hs[k];
     double sp = 1.0;
     for (int n = 0; n <= p; ++n) {
         double acc = M[hre(n, 0)] * M[hre(n, 0)];
@@ -211,7 +212,7 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
 //   b = (z_C - z_P)/s_P, sigma = s_C/s_P, beta' = w_{n+k}^{m+l} / (w_k^l w_n^m).
 template <typename T, typename Tab>
 __global__ void k_l2l(TreeView t, int k0, int k1, int p, Tab tb, const double* __restrict__ zc,
-                      const double* __restrict__ rr, T* __restrict__ loc) {
+                      const double* __restrict__ hs, T* __restrict__ loc) {
     extern __shared__ __align__(16) unsigned char sh_l2l_raw[];
     const int C = k0 + blockIdx.x;
     if (C >= k1) return;
@@ -220,12 +221,12 @@ __global__ void k_l2l(TreeView t, int k0, int k1, int p, Tab tb, const double* _
     Cx<T>* S = reinterpret_cast<Cx<T>*>(sh_l2l_raw);
     T* Fp = reinterpret_cast<T*>(S + nc);
     T* sig = Fp + nr;
-    const double sP = hat_scale(rr[P]);
+    const double sP = hs[P];
     if (threadIdx.x == 0) {
         const T bx = (T)((zc[3 * C] - zc[3 * P]) / sP), by = (T)((zc[3 * C + 1] - zc[3 * P + 1]) / sP),
                 bz = (T)((zc[3 * C + 2] - zc[3 * P + 2]) / sP);
         shat_all<T>(p, bx, by, bz, tb, S);
-        const T sg = (T)(hat_scale(rr[C]) / sP);
+        const T sg = (T)(hs[C] / sP);
         T pw = T(1);
         for (int j = 0; j <= p; ++j) { sig[j] = pw; pw *= sg; }
     }
@@ -253,7 +254,17 @@ __global__ void k_l2l(TreeView t, int k0, int k1, int p, Tab tb, const double* _
     }
 }
 
-__global__ void k_node_centres(int nnodes, const double* __restrict__ zc, const double* __restrict__ rr,
+__global__ void k_hat_scales(int nnodes, const int* __restrict__ parent, const double* __restrict__ r,
+                             double* __restrict__ hs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnodes) return;
+    int root = k;
+    while (parent[root] >= 0) root = parent[root];
+    const double floor_s = kHatFloor * (r[root] > 0.0 ? r[root] : 1.0);
+    hs[k] = r[k] > floor_s ? r[k] : floor_s;
+}
+
+__global__ void k_node_centres(int nnodes, const double* __restrict__ zc, const double* __restrict__ hs,
                                float4* __restrict__ zhi, float4* __restrict__ zlo) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nnodes) return;
@@ -263,7 +274,7 @@ __global__ void k_node_centres(int nnodes, const double* __restrict__ zc, const 
         h[d] = (float)z;
         l[d] = (float)(z - (double)h[d]);
     }
-    zhi[k] = make_float4(h[0], h[1], h[2], (float)hat_scale(rr[k]));
+    zhi[k] = make_float4(h[0], h[1], h[2], (float)hs[k]);
     zlo[k] = make_float4(l[0], l[1], l[2], 0.0f);
 }
 
@@ -293,23 +304,27 @@ void upload_expansion_tables(const HostTables& h) {
 
 void upward_pass(const TreeView& t, const int* h_level_start, int p, const double* xs,
                  const double* ys, const double* zs, const double* ms, const double* zc,
-                 const double* r, double* mult, double* Pk, float* Phat, float* r32, double* contrib,
-                 const DevTables& tbl, cudaStream_t st) {
+                 const double* r, const double* hs, double* mult, double* Pk, float* Phat, float* r32,
+                 double* contrib, const DevTables& tbl, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
     if (p <= 16)
-        (k_p2m<16, 4><<<152 * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, r, mult), note_launch());
+        (k_p2m<16, 4><<<152 * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, hs, mult), note_launch());
     else
-        (k_p2m<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, r, mult), note_launch());
+        (k_p2m<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, hs, mult), note_launch());
     const int nr = ncoef_real(p);
     (void)nr;
     for (int L = t.nlevels - 2; L >= 0; --L)
         m2m_level_f64(t, h_level_start[L], h_level_start[L + 1], h_level_start[L + 1], h_level_start[L + 2], p,
-                      zc, r, mult, contrib, tbl, st);
-    (k_pnorm<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, p, mult, r, Pk, Phat, r32), note_launch());
+                      zc, hs, mult, contrib, tbl, st);
+    (k_pnorm<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, p, mult, r, hs, Pk, Phat, r32), note_launch());
 }
 
-void node_centres_f32(int nnodes, const double* zc, const double* r, float4* zhi, float4* zlo, cudaStream_t st) {
-    (k_node_centres<<<blocks_for(nnodes, 128), 128, 0, st>>>(nnodes, zc, r, zhi, zlo), note_launch());
+void hat_scales(int nnodes, const int* parent, const double* r, double* hs, cudaStream_t st) {
+    (k_hat_scales<<<blocks_for(nnodes, 128), 128, 0, st>>>(nnodes, parent, r, hs), note_launch());
+}
+
+void node_centres_f32(int nnodes, const double* zc, const double* hs, float4* zhi, float4* zlo, cudaStream_t st) {
+    (k_node_centres<<<blocks_for(nnodes, 128), 128, 0, st>>>(nnodes, zc, hs, zhi, zlo), note_launch());
 }
 
 __global__ void k_to_f32_strided(const double* __restrict__ a, float* __restrict__ b, int nnodes, int nr,
@@ -331,7 +346,7 @@ void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStr
 }
 
 void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const double* zc,
-                       const double* r, double* loc, const DevTables& tbl, cudaStream_t st) {
+                       const double* hs, double* loc, const DevTables& tbl, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
     const int nc = tri(p + 1, 0), nr = ncoef_real(p);
     const size_t sh = (size_t)(2 * nc + nr + p + 1) * sizeof(double);
@@ -342,17 +357,17 @@ void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const
     }
     for (int L = 1; L < t.nlevels; ++L) {
         const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
-        if (k1 > k0) (k_l2l<double, TabF64><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, tb, zc, r, loc), note_launch());
+        if (k1 > k0) (k_l2l<double, TabF64><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, tb, zc, hs, loc), note_launch());
     }
 }
 
 void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const double* zc,
-                       const double* r, float* loc, cudaStream_t st) {
+                       const double* hs, float* loc, cudaStream_t st) {
     const int nc = tri(p + 1, 0), nr = ncoef_real(p);
     const size_t sh = (size_t)(2 * nc + nr + p + 1) * sizeof(float);
     for (int L = 1; L < t.nlevels; ++L) {
         const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
-        if (k1 > k0) (k_l2l<float, TabF32><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, TabF32{}, zc, r, loc), note_launch());
+        if (k1 > k0) (k_l2l<float, TabF32><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, TabF32{}, zc, hs, loc), note_launch());
     }
 }
 

@@ -22,6 +22,7 @@ enum : unsigned {
     kErrCoincident = 2u,
     kErrNonfinite = 4u,
     kErrTimeout = 8u,
+    kErrIndex = 16u,  // a cell index out of range (an internal error)
 };
 
 // real layout of a hat coefficient vector: degree n starts at n*n with
@@ -76,6 +77,7 @@ struct TreeView {
     int nnodes;
     int nlevels;
     int leaf_size;
+    int nroots;  // trees of the forest: nodes [0, nroots) are their roots (level 0)
     const int* level;
     const int* begin;
     const int* end;
@@ -108,14 +110,21 @@ struct TreeBuffers {
     const double *x, *y, *z, *m;
     int64_t n;
     int leaf_size;
+    int nclusters;               // independent clusters (a forest); 1 for one cluster
+    const int* coff;             // device, nclusters + 1 body offsets of the clusters
     // scratch / outputs
-    double* bbox_part;     // 6 * nblocks_bbox
+    double* bbox_part;           // 6 * bbox_partials(nclusters)
+    double* box;                 // 8 per cluster: centre, h, lower corner, size
     uint64_t *k0, *k1;
     uint32_t *v0, *v1;
+    uint64_t *ck0, *ck1;         // cluster pass of the sort (nclusters > 1)
+    uint32_t *cv0, *cv1;
+    uint32_t* cid;               // cluster of every sorted body (nclusters > 1)
     uint32_t* hist;
     double *xs, *ys, *zs, *ms;   // sorted bodies
     float4* xf;                  // cube-centred FP32 coordinates + mass (scalar-force estimate)
-    uint8_t *lcp, *win, *hi;     // per body
+    int8_t *lcp, *win;           // per body
+    uint8_t* hi;
     uint32_t* chunk_cnt;         // 23 * nchunks (+1 total)
     int *level, *begin, *end, *parent, *first_child, *nchild;
     int64_t node_cap;
@@ -125,6 +134,8 @@ struct TreeBuffers {
 // total lands at chunk_cnt[22 * nchunks]. sorted_in_1 tells where the sorted
 // keys/perm ended up.
 void tree_build_count(TreeBuffers& b, int* sorted_in_1, cudaStream_t st);
+// doubles (times 6) of the bounding-cube partials for nclusters clusters
+int bbox_partials(int nclusters);
 // node level/begin arrays and ds->level_start, ds->nnodes
 void tree_build_emit(TreeBuffers& b, cudaStream_t st);
 int tree_nchunks(int64_t n);
@@ -145,6 +156,7 @@ struct WalkBuffers {
 // Dual-tree walk from (root, root). mode 0: theta < 1 (lists far/near);
 // mode 1: the error-controlled MAC (lists m2l/p2p). Returns iterations or a
 // negative fmm_status. Counts land in ds->list_cnt.
+constexpr int kWalkBadIndex = -100;  // dual_tree_walk: a frontier entry out of range
 int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* r, const double* P,
                    const float* fmin, int p, double eps, const double* binom_row, const float4* zhi,
                    const float4* zlo, const float* r32, const float* Phat, WalkBuffers& wb,
@@ -164,34 +176,40 @@ void directed_offsets(const uint64_t* keys, int64_t nkeys, int nb, int nnodes, u
 
 // ---------------------------------------------------------- expansions.cu
 void upload_expansion_tables(const HostTables& h);
+// Hat scale s_k of every node: its size r_k, floored at kHatFloor times the
+// size of its tree's root so that no cell (a single body has r = 0) gets a scale so small
+// that its FP32 local coefficients F s^n fall into the denormal range.
+constexpr double kHatFloor = 0x1p-40;
+void hat_scales(int nnodes, const int* parent, const double* r, double* hs, cudaStream_t st);
 // FP64 hat multipoles: P2M at leaves, M2M level by level; P_k per node.
+// r: node sizes (the walk's FP32 copy r32 is written from them); hs: hat scales.
 void upward_pass(const TreeView& t, const int* h_level_start, int p, const double* xs,
                  const double* ys, const double* zs, const double* ms, const double* zc,
-                 const double* r, double* mult, double* Pk, float* Phat, float* r32, double* contrib,
-                 const DevTables& tb, cudaStream_t st);
+                 const double* r, const double* hs, double* mult, double* Pk, float* Phat, float* r32,
+                 double* contrib, const DevTables& tb, cudaStream_t st);
 // rotation-accelerated M2M of one level: children [child0, child1) into their
 // parents [parent0, parent1); contrib: (p+1)^2 doubles per node (scratch)
 void m2m_level_f64(const TreeView& t, int parent0, int parent1, int child0, int child1, int p,
-                   const double* zc, const double* r, double* mult, double* contrib, const DevTables& tb,
+                   const double* zc, const double* hs, double* mult, double* contrib, const DevTables& tb,
                    cudaStream_t st);
 void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStream_t st);
 // FP32 copy with each node's vector padded to `stride` floats (zeros after nr)
 void multipoles_to_f32_padded(const double* mult, float* mult32, int nnodes, int nr, int stride, cudaStream_t st);
 // double-float node centres (hi, lo) and the FP32 hat scale in zhi.w
-void node_centres_f32(int nnodes, const double* zc, const double* r, float4* zhi, float4* zlo, cudaStream_t st);
+void node_centres_f32(int nnodes, const double* zc, const double* hs, float4* zhi, float4* zlo, cudaStream_t st);
 // per-node minimum of the scalar-force estimate (leaves over bodies, then levels upward)
 
 // L2L level by level (FP64 or FP32 locals).
 void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const double* zc,
-                       const double* r, double* loc, const DevTables& tb, cudaStream_t st);
+                       const double* hs, double* loc, const DevTables& tb, cudaStream_t st);
 void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const double* zc,
-                       const double* r, float* loc, cudaStream_t st);
+                       const double* hs, float* loc, cudaStream_t st);
 
 // ----------------------------------------------------------------- m2l.cu
 // Rotation-accelerated M2L (Sec. 2.4), gathered per target over the sorted
 // directed list; writes the locals of every node (zero without sources).
 void m2l_f64(int nnodes, int p, const uint64_t* keys, const uint32_t* off, int nb,
-             const double* mult, const double* zc, const double* r, double* loc,
+             const double* mult, const double* zc, const double* hs, double* loc,
              const DevTables& tb, cudaStream_t st);
 void m2l_f32(int nnodes, int p, const uint64_t* keys, const uint32_t* off, int nb,
              const float* mult, const float4* zhi, const float4* zlo, float* loc, cudaStream_t st);
@@ -209,7 +227,7 @@ struct LeafArgs {
     int p;
     double G;
     const double *xs, *ys, *zs, *ms;
-    const double *zc, *r;
+    const double *zc, *hs;  // node centres and hat scales
     const float4 *zhi, *zlo;  // double-float node centres; zhi.w = hat scale
     const uint64_t* p2p_keys;
     const uint32_t* p2p_off;
@@ -233,8 +251,5 @@ void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, co
 void direct_sum_f64(int64_t n, const double* x, const double* y, const double* z, const double* m,
                     double G, int64_t ntgt, const int64_t* tgt, double* ax, double* ay, double* az,
                     double* pot, cudaStream_t st);
-
-// hat scale of a cell: its size r, or a tiny positive stand-in for r = 0
-__host__ __device__ inline double hat_scale(double r) { return r > 0.0 ? r : 1e-30; }
 
 }  // namespace gbfmm

@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(128) k_leaf_reduce(LeafArgs a, const int* __re
         sx = fx; sy = fy; sz = fz; sp = phi;
     } else {
         const TabL64 tb{a.tb.w, a.tb.iw, a.tb.rec_a, a.tb.rec_b, a.tb.diag, a.tb.sub};
-        const double inv_s = 1.0 / hat_scale(a.r[B]);
+        const double inv_s = 1.0 / a.hs[B];
         double phi, fx, fy, fz;
         l2p_hat<double>(a.p, reinterpret_cast<const double*>(a.loc) + (size_t)nr * B,
                         (a.xs[i] - a.zc[3 * B]) * inv_s, (a.ys[i] - a.zc[3 * B + 1]) * inv_s,

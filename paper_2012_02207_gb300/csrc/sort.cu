@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ 
 // digit (warp match + per-warp digit counters), reorder the tile by digit in
 // shared memory, then write each digit's run to its global position with
 // consecutive threads writing consecutive addresses.
-__global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict__ kin,
+__global__ void __launch_bounds__(kThreads, 2) k_scatter(const uint64_t* __restrict__ kin,
                                                       const uint32_t* __restrict__ vin,
                                                       uint64_t* __restrict__ kout,
                                                       uint32_t* __restrict__ vout, int64_t n,
@@ -55,15 +55,19 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict
     const int64_t tile0 = (int64_t)blockIdx.x * kTile;
     const int64_t base = tile0 + (int64_t)warp * kWarpItems;
     uint64_t key[kItems];
-    uint32_t val[kItems], rank[kItems], dig[kItems];
+    uint32_t val[kItems], rank[kItems];
+    // all loads first, so that they are in flight together
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        key[r] = i < n ? kin[i] : 0ull;
+        val[r] = (i < n && vin) ? vin[i] : 0u;
+    }
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const int64_t i = base + r * 32 + lane;
         const bool valid = i < n;
-        key[r] = valid ? kin[i] : 0ull;
-        val[r] = (valid && vin) ? vin[i] : 0u;
         const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 255u : 0xFFFFFFFFu;
-        dig[r] = d;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const uint32_t before = valid ? wcount[warp][d] : 0u;
         rank[r] = before + __popc(peers & ((1u << lane) - 1u));
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict
     for (int r = 0; r < kItems; ++r) {
         const int64_t i = base + r * 32 + lane;
         if (i < n) {
-            const uint32_t d = dig[r];
+            const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
             const uint32_t pos = lstart[d] + wcount[warp][d] + rank[r];
             skey[pos] = key[r];
             sval[pos] = val[r];
@@ -120,41 +124,62 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict
     }
 }
 
-// Single-block exclusive scan: each of 1024 threads owns a contiguous chunk.
+// Single-block exclusive scan in tiles of 4096 words: a coalesced load into
+// shared memory, four consecutive words per thread, a block scan of the
+// thread sums, a coalesced store, and a carry into the next tile.
 __global__ void __launch_bounds__(1024) k_scan(uint32_t* data, int64_t count, uint32_t* total) {
+    __shared__ __align__(16) uint32_t tile[4096];
     __shared__ uint32_t warp_sums[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t chunk = (count + 1023) / 1024;
-    const int64_t lo = (int64_t)tid * chunk;
-    const int64_t hi = lo + chunk < count ? lo + chunk : count;
-    uint32_t s = 0;
-    for (int64_t i = lo; i < hi; ++i) s += data[i];
-    uint32_t incl = s;
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < count; base += 4096) {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) warp_sums[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t ws = warp_sums[lane];
-        uint32_t wi = ws;
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = base + k * 1024 + tid;
+            tile[k * 1024 + tid] = i < count ? data[i] : 0u;
+        }
+        __syncthreads();
+        const uint4 v = reinterpret_cast<const uint4*>(tile)[tid];
+        const uint32_t s = v.x + v.y + v.z + v.w;
+        uint32_t incl = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += v;
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
         }
-        warp_sums[lane] = wi - ws;
-        if (lane == 31 && total) *total = wi;
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t ws = warp_sums[lane];
+            uint32_t wi = ws;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            warp_sums[lane] = wi - ws;  // exclusive offsets of the warps; the tile total is wi at lane 31
+            if (lane == 31) tile[0] = wi;  // tile[0] was consumed above; reused to pass the total
+        }
+        __syncthreads();
+        const uint32_t tile_total = tile[0];
+        uint32_t run = carry + warp_sums[warp] + incl - s;
+        __syncthreads();
+        uint4 o;
+        o.x = run; run += v.x;
+        o.y = run; run += v.y;
+        o.z = run; run += v.z;
+        o.w = run;
+        reinterpret_cast<uint4*>(tile)[tid] = o;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = base + k * 1024 + tid;
+            if (i < count) data[i] = tile[k * 1024 + tid];
+        }
+        carry += tile_total;
+        __syncthreads();
     }
-    __syncthreads();
-    uint32_t run = warp_sums[warp] + incl - s;
-    for (int64_t i = lo; i < hi; ++i) {
-        const uint32_t v = data[i];
-        data[i] = run;
-        run += v;
-    }
+    if (tid == 0 && total) *total = carry;
 }
 // Large scans in three passes: segment sums, a scan of the sums, and a
 // rescan of each segment from its offset.

@@ -14,20 +14,30 @@
 // node of level L starts at body i exactly when lcp_i < L <= min(D_i+1, 21)
 // (the root at i = 0, L = 0). Counting those starts per chunk of bodies and
 // scanning the (level, chunk) table gives every node its index directly.
+//
+// Several independent clusters (an ensemble) are built as one forest: each
+// cluster gets its own cube and keys, the bodies are sorted by (cluster, key),
+// and lcp_i = -1 where a cluster begins, so every cluster has its own root at
+// level 0 and no node spans two clusters. Nodes stay level-major, then
+// (cluster, key) inside a level; a one-cluster forest is the plain octree.
 #include "gbfmm_internal.cuh"
 
 namespace gbfmm {
 
 namespace {
 constexpr int kChunk = 256;  // bodies per thread in the node enumeration
+constexpr int kBboxBlocks = 304;  // bounding-cube partials (2 blocks per SM)
 
+// block (c, s) of a grid of nclusters * slices blocks reduces slice s of cluster c
 __global__ void k_bbox_partial(const double* __restrict__ x, const double* __restrict__ y,
                                const double* __restrict__ z, const double* __restrict__ m,
-                               int64_t n, double* __restrict__ part, unsigned* err) {
+                               const int* __restrict__ coff, int slices, double* __restrict__ part,
+                               unsigned* err) {
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = blockIdx.x / slices, sl = blockIdx.x - c * slices;
+    const int64_t b = coff[c], e = coff[c + 1];
+    for (int64_t i = b + (int64_t)sl * blockDim.x + threadIdx.x; i < e; i += (int64_t)slices * blockDim.x) {
         const double v[3] = {x[i], y[i], z[i]};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -59,26 +69,40 @@ __global__ void k_bbox_partial(const double* __restrict__ x, const double* __res
     if (bad) atomicOr(err, kErrNonfinite);
 }
 
-// Cube (reading R1): centre c = (min+max)/2 per axis, half-size h = the
-// largest (max-min)/2 (h = 1 if all bodies coincide, e.g. n = 1).
-__global__ void k_bbox_final(const double* __restrict__ part, int nparts, DevScalars* ds) {
-    if (threadIdx.x != 0) return;
+// Cube of each cluster (reading R1): centre c = (min+max)/2 per axis,
+// half-size h = the largest (max-min)/2 (h = 1 if all its bodies coincide,
+// e.g. one body). box[8c ..]: cx, cy, cz, h, lox, loy, loz, size.
+__global__ void k_bbox_final(const double* __restrict__ part, int nclusters, int slices,
+                             double* __restrict__ box) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nclusters) return;
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nparts; ++b)
+    for (int b = c * slices; b < (c + 1) * slices; ++b)
         for (int d = 0; d < 3; ++d) {
             mn[d] = fmin(mn[d], part[6 * b + d]);
             mx[d] = fmax(mx[d], part[6 * b + 3 + d]);
         }
+    double* bx = box + 8 * c;
     double h = 0.0;
     for (int d = 0; d < 3; ++d) {
-        ds->box[d] = 0.5 * (mn[d] + mx[d]);
+        bx[d] = 0.5 * (mn[d] + mx[d]);
         const double hd = 0.5 * (mx[d] - mn[d]);
         if (hd > h) h = hd;
     }
     if (h == 0.0) h = 1.0;
-    ds->box[3] = h;
-    for (int d = 0; d < 3; ++d) ds->box[4 + d] = ds->box[d] - h;
-    ds->box[7] = 2.0 * h;
+    bx[3] = h;
+    for (int d = 0; d < 3; ++d) bx[4 + d] = bx[d] - h;
+    bx[7] = 2.0 * h;
+}
+
+// cluster of body i (coff: nclusters + 1 ascending offsets)
+__device__ __forceinline__ int cluster_of(const int* __restrict__ coff, int nclusters, int64_t i) {
+    int lo = 0, hi = nclusters;  // last c with coff[c] <= i
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (coff[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
 __device__ __forceinline__ uint64_t spread3(uint64_t v) {  // 21 bits -> every third bit
@@ -100,79 +124,106 @@ __device__ __forceinline__ uint64_t quantise(double v, double lo, double size) {
 
 // Morton key: x in the high bit of each 3-bit digit, then y, then z.
 __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
-                       const double* __restrict__ z, int64_t n, const DevScalars* __restrict__ ds,
-                       uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+                       const double* __restrict__ z, int64_t n, const int* __restrict__ coff,
+                       int nclusters, const double* __restrict__ box, uint64_t* __restrict__ keys,
+                       uint32_t* __restrict__ idx) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double size = ds->box[7];
-    const uint64_t qx = quantise(x[i], ds->box[4], size);
-    const uint64_t qy = quantise(y[i], ds->box[5], size);
-    const uint64_t qz = quantise(z[i], ds->box[6], size);
+    const double* bx = box + 8 * cluster_of(coff, nclusters, i);
+    const double size = bx[7];
+    const uint64_t qx = quantise(x[i], bx[4], size);
+    const uint64_t qy = quantise(y[i], bx[5], size);
+    const uint64_t qz = quantise(z[i], bx[6], size);
     keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     idx[i] = (uint32_t)i;
 }
 
+// cluster pass of the (cluster, key) sort: the cluster of each key-sorted
+// body as the sort key, its key-sorted position as the value
+__global__ void k_cluster_keys(const uint32_t* __restrict__ perm, int64_t n, const int* __restrict__ coff,
+                               int nclusters, uint64_t* __restrict__ ckey, uint32_t* __restrict__ cval) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    ckey[i] = (uint64_t)cluster_of(coff, nclusters, perm[i]);
+    cval[i] = (uint32_t)i;
+}
+
+__global__ void k_cluster_apply(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ perm,
+                                const uint64_t* __restrict__ ckey, const uint32_t* __restrict__ cval,
+                                int64_t n, uint64_t* __restrict__ keys_out, uint32_t* __restrict__ perm_out,
+                                uint32_t* __restrict__ cid) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = cval[i];
+    keys_out[i] = keys[j];
+    perm_out[i] = perm[j];
+    cid[i] = (uint32_t)ckey[i];
+}
+
 __global__ void k_gather(const double* __restrict__ x, const double* __restrict__ y,
                          const double* __restrict__ z, const double* __restrict__ m,
-                         const uint32_t* __restrict__ perm, int64_t n,
-                         const DevScalars* __restrict__ ds, double* __restrict__ xs,
+                         const uint32_t* __restrict__ perm, int64_t n, const uint32_t* __restrict__ cid,
+                         const double* __restrict__ box, double* __restrict__ xs,
                          double* __restrict__ ys, double* __restrict__ zs, double* __restrict__ ms,
                          float4* __restrict__ xf) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t j = perm[i];
+    const double* bx = box + 8 * (cid ? cid[i] : 0u);
     const double a = x[j], b = y[j], c = z[j], w = m[j];
     xs[i] = a; ys[i] = b; zs[i] = c; ms[i] = w;
-    xf[i] = make_float4((float)(a - ds->box[0]), (float)(b - ds->box[1]), (float)(c - ds->box[2]),
-                        (float)w);
+    xf[i] = make_float4((float)(a - bx[0]), (float)(b - bx[1]), (float)(c - bx[2]), (float)w);
 }
 
-// lcp_i (levels shared by keys i-1 and i) and the coincident-body check.
-__global__ void k_lcp(const uint64_t* __restrict__ keys, const double* __restrict__ xs,
-                      const double* __restrict__ ys, const double* __restrict__ zs, int64_t n,
-                      uint8_t* __restrict__ lcp, unsigned* err) {
+// lcp_i (levels shared by keys i-1 and i; -1 where a cluster begins) and
+// the coincident-body check (within a cluster).
+__global__ void k_lcp(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ cid,
+                      const double* __restrict__ xs, const double* __restrict__ ys,
+                      const double* __restrict__ zs, int64_t n, int8_t* __restrict__ lcp, unsigned* err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (i == 0) { lcp[0] = 0; return; }
+    const uint32_t ci = cid ? cid[i] : 0u;
+    if (i == 0 || (cid && cid[i - 1] != ci)) { lcp[i] = -1; return; }
     const uint64_t k = keys[i];
     const uint64_t d = k ^ keys[i - 1];
-    lcp[i] = d ? (uint8_t)((__clzll((long long)d) - 1) / 3) : (uint8_t)kMaxLevel;
+    lcp[i] = d ? (int8_t)((__clzll((long long)d) - 1) / 3) : (int8_t)kMaxLevel;
     if (d == 0) {
         // equal keys: compare with the earlier bodies of the run (bounded)
         const double a = xs[i], b = ys[i], c = zs[i];
         int steps = 0;
-        for (int64_t j = i - 1; j >= 0 && keys[j] == k && steps < 4096; --j, ++steps)
+        for (int64_t j = i - 1; j >= 0 && keys[j] == k && (!cid || cid[j] == ci) && steps < 4096; --j, ++steps)
             if (xs[j] == a && ys[j] == b && zs[j] == c) { atomicOr(err, kErrCoincident); break; }
     }
 }
 
 // W_a = min(lcp[a+1 .. a+leaf]) for a in [0, n-1-leaf].
-__global__ void k_window_min(const uint8_t* __restrict__ lcp, int64_t n, int leaf,
-                             uint8_t* __restrict__ win) {
+// (a window that crosses into another cluster has W_a = -1)
+__global__ void k_window_min(const int8_t* __restrict__ lcp, int64_t n, int leaf,
+                             int8_t* __restrict__ win) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a > n - 1 - leaf) return;
-    uint8_t w = kMaxLevel;
-    for (int k = 1; k <= leaf; ++k) { const uint8_t v = lcp[a + k]; w = v < w ? v : w; }
+    int8_t w = kMaxLevel;
+    for (int k = 1; k <= leaf; ++k) { const int8_t v = lcp[a + k]; w = v < w ? v : w; }
     win[a] = w;
 }
 
 // hi_i = min(D_i + 1, 21) with D_i the max of W over the windows holding i.
-__global__ void k_window_max(const uint8_t* __restrict__ win, int64_t n, int leaf,
+__global__ void k_window_max(const int8_t* __restrict__ win, int64_t n, int leaf,
                              uint8_t* __restrict__ hi) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (n <= leaf) { hi[i] = 0; return; }
     const int64_t a0 = i - leaf > 0 ? i - leaf : 0;
     const int64_t a1 = i < n - 1 - leaf ? i : n - 1 - leaf;
-    int d = 0;
+    int d = -1;
     for (int64_t a = a0; a <= a1; ++a) d = win[a] > d ? win[a] : d;
     hi[i] = (uint8_t)(d + 1 < kMaxLevel ? d + 1 : kMaxLevel);
 }
 
-__device__ __forceinline__ int start_lo(const uint8_t* lcp, int64_t i) { return i == 0 ? -1 : (int)lcp[i]; }
+__device__ __forceinline__ int start_lo(const int8_t* lcp, int64_t i) { return (int)lcp[i]; }
 
 // per (level, chunk) node-start counts, level-major
-__global__ void k_level_count(const uint8_t* __restrict__ lcp, const uint8_t* __restrict__ hi,
+__global__ void k_level_count(const int8_t* __restrict__ lcp, const uint8_t* __restrict__ hi,
                               int64_t n, int nchunks, uint32_t* __restrict__ cnt) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nchunks) return;
@@ -190,7 +241,7 @@ __global__ void k_level_count(const uint8_t* __restrict__ lcp, const uint8_t* __
     for (int L = 0; L <= kMaxLevel; ++L) cnt[(int64_t)L * nchunks + c] = local[L];
 }
 
-__global__ void k_level_emit(const uint8_t* __restrict__ lcp, const uint8_t* __restrict__ hi,
+__global__ void k_level_emit(const int8_t* __restrict__ lcp, const uint8_t* __restrict__ hi,
                              int64_t n, int nchunks, const uint32_t* __restrict__ off,
                              int* __restrict__ level, int* __restrict__ begin, int64_t node_cap,
                              unsigned* err) {
@@ -226,6 +277,7 @@ __global__ void k_level_starts(const uint32_t* __restrict__ off, int nchunks, co
 
 // end, parent and children of every node by binary searches.
 __global__ void k_finalize(const uint64_t* __restrict__ keys, int64_t n, int leaf, int nnodes,
+                           const uint32_t* __restrict__ cid, const int* __restrict__ coff,
                            const DevScalars* __restrict__ ds, const int* __restrict__ level,
                            const int* __restrict__ begin, int* __restrict__ end,
                            int* __restrict__ parent, int* __restrict__ first_child,
@@ -234,11 +286,12 @@ __global__ void k_finalize(const uint64_t* __restrict__ keys, int64_t n, int lea
     if (k >= nnodes) return;
     const int L = level[k];
     const int b = begin[k];
-    int e = (int)n;
+    const int cend = cid ? coff[cid[b] + 1] : (int)n;  // end of the node's cluster
+    int e = cend;
     if (L > 0) {
         const int shift = 3 * (kMaxLevel - L);
         const uint64_t pre = keys[b] >> shift;
-        int lo = b + 1, hi = (int)n;  // first index with a larger prefix
+        int lo = b + 1, hi = cend;  // first index with a larger prefix
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if ((keys[mid] >> shift) > pre) hi = mid; else lo = mid + 1;
@@ -331,19 +384,39 @@ inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) /
 
 int tree_nchunks(int64_t n) { return (int)((n + kChunk - 1) / kChunk); }
 
+int bbox_partials(int nclusters) { return nclusters >= kBboxBlocks ? nclusters : 2 * kBboxBlocks; }
+
 void tree_build_count(TreeBuffers& b, int* sorted_in_1, cudaStream_t st) {
     const int64_t n = b.n;
-    const int nbb = 152 * 2;
-    (k_bbox_partial<<<nbb, 256, 0, st>>>(b.x, b.y, b.z, b.m, n, b.bbox_part, &b.ds->err), note_launch());
-    (k_bbox_final<<<1, 32, 0, st>>>(b.bbox_part, nbb, b.ds), note_launch());
-    (k_keys<<<blocks_for(n, 256), 256, 0, st>>>(b.x, b.y, b.z, n, b.ds, b.k0, b.v0), note_launch());
-    const int in1 = radix_sort(b.k0, b.v0, b.k1, b.v1, n, 63, b.hist, st);
-    *sorted_in_1 = in1;
+    const int nc = b.nclusters;
+    const int slices = nc >= kBboxBlocks ? 1 : (kBboxBlocks + nc - 1) / nc;
+    (k_bbox_partial<<<nc * slices, 256, 0, st>>>(b.x, b.y, b.z, b.m, b.coff, slices, b.bbox_part, &b.ds->err),
+     note_launch());
+    (k_bbox_final<<<blocks_for(nc, 128), 128, 0, st>>>(b.bbox_part, nc, slices, b.box), note_launch());
+    (k_keys<<<blocks_for(n, 256), 256, 0, st>>>(b.x, b.y, b.z, n, b.coff, nc, b.box, b.k0, b.v0), note_launch());
+    int in1 = radix_sort(b.k0, b.v0, b.k1, b.v1, n, 63, b.hist, st);
     const uint64_t* keys = in1 ? b.k1 : b.k0;
     const uint32_t* perm = in1 ? b.v1 : b.v0;
-    (k_gather<<<blocks_for(n, 256), 256, 0, st>>>(b.x, b.y, b.z, b.m, perm, n, b.ds, b.xs, b.ys, b.zs,
+    const uint32_t* cid = nullptr;
+    if (nc > 1) {
+        // stable pass on the cluster: (cluster, key) order
+        (k_cluster_keys<<<blocks_for(n, 256), 256, 0, st>>>(perm, n, b.coff, nc, b.ck0, b.cv0), note_launch());
+        int bits = 0;
+        while ((1 << bits) < nc) ++bits;
+        const int cin1 = radix_sort(b.ck0, b.cv0, b.ck1, b.cv1, n, bits, b.hist, st);
+        uint64_t* kout = in1 ? b.k0 : b.k1;
+        uint32_t* vout = in1 ? b.v0 : b.v1;
+        (k_cluster_apply<<<blocks_for(n, 256), 256, 0, st>>>(keys, perm, cin1 ? b.ck1 : b.ck0, cin1 ? b.cv1 : b.cv0,
+                                                            n, kout, vout, b.cid), note_launch());
+        in1 ^= 1;
+        keys = kout;
+        perm = vout;
+        cid = b.cid;
+    }
+    *sorted_in_1 = in1;
+    (k_gather<<<blocks_for(n, 256), 256, 0, st>>>(b.x, b.y, b.z, b.m, perm, n, cid, b.box, b.xs, b.ys, b.zs,
                                                  b.ms, b.xf), note_launch());
-    (k_lcp<<<blocks_for(n, 256), 256, 0, st>>>(keys, b.xs, b.ys, b.zs, n, b.lcp, &b.ds->err), note_launch());
+    (k_lcp<<<blocks_for(n, 256), 256, 0, st>>>(keys, cid, b.xs, b.ys, b.zs, n, b.lcp, &b.ds->err), note_launch());
     if (n > b.leaf_size)
         (k_window_min<<<blocks_for(n - b.leaf_size, 256), 256, 0, st>>>(b.lcp, n, b.leaf_size, b.win), note_launch());
     (k_window_max<<<blocks_for(n, 256), 256, 0, st>>>(b.win, n, b.leaf_size, b.hi), note_launch());
@@ -366,7 +439,8 @@ void tree_build_phase2(TreeBuffers& b, const uint64_t* keys, int nnodes, const i
                        int nlevels, cudaStream_t st) {
     (void)h_level_start;
     (void)nlevels;
-    (k_finalize<<<blocks_for(nnodes, 128), 128, 0, st>>>(keys, b.n, b.leaf_size, nnodes, b.ds, b.level,
+    (k_finalize<<<blocks_for(nnodes, 128), 128, 0, st>>>(keys, b.n, b.leaf_size, nnodes,
+                                                        b.nclusters > 1 ? b.cid : nullptr, b.coff, b.ds, b.level,
                                                         b.begin, b.end, b.parent, b.first_child,
                                                         b.nchild), note_launch());
 }

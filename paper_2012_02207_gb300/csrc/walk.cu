@@ -16,6 +16,7 @@ namespace gbfmm {
 namespace {
 
 struct WalkCells {
+    int nnodes;
     const int* nchild;
     const int* first_child;
     const double* zc;
@@ -99,8 +100,14 @@ __global__ void __launch_bounds__(256) k_walk_step(WalkCells c, const int2* __re
     if (threadIdx.x <= (unsigned)c.p) binom32[threadIdx.x] = (float)c.binom[threadIdx.x];
     __syncthreads();
     const float eps32 = (float)c.eps;
-    const int64_t nin_raw = (int64_t)*cnt_in;
-    const int64_t nin = nin_raw < cap_out ? nin_raw : cap_out;  // both frontiers hold cap_out pairs
+    const int64_t nin = (int64_t)*cnt_in;
+    // An input frontier that outgrew its buffer is incomplete (the warps that
+    // crossed the end wrote nothing, leaving holes below it): do no work, the
+    // host sees the capacity error and grows the buffers.
+    if (nin > cap_out) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrCapacity);
+        return;
+    }
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -109,8 +116,10 @@ __global__ void __launch_bounds__(256) k_walk_step(WalkCells c, const int2* __re
         int a = 0, b = 0;
         unsigned n_next = 0, n_acc = 0, n_leaf = 0;
         int split_kind = 0;  // 1: self children pairs, 2: split a, 3: split b
-        if (q < nin) {
-            const int2 pr = fin[q];
+        const int2 pr = q < nin ? fin[q] : make_int2(0, 0);
+        if (q < nin && ((unsigned)pr.x >= (unsigned)c.nnodes || (unsigned)pr.y >= (unsigned)c.nnodes)) {
+            atomicOr(err, kErrIndex);  // never expected: a frontier entry that no step wrote
+        } else if (q < nin) {
             a = pr.x;
             b = pr.y;
             const int nca = c.nchild[a], ncb = c.nchild[b];
@@ -204,11 +213,12 @@ __global__ void __launch_bounds__(256) k_walk_step(WalkCells c, const int2* __re
     }
 }
 
-__global__ void k_walk_init(int2* f0, unsigned long long* cnt, unsigned long long* list_cnt,
+// the walk starts from the self pair (root, root) of every tree of the forest
+__global__ void k_walk_init(int2* f0, int nroots, unsigned long long* cnt, unsigned long long* list_cnt,
                             int iters, int mode) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) f0[0] = make_int2(0, 0);
-    if (i < iters) cnt[i] = (i == 0) ? 1ull : 0ull;
+    if (i < nroots) f0[i] = make_int2(i, i);
+    if (i < iters) cnt[i] = (i == 0) ? (unsigned long long)nroots : 0ull;
     if (i < 2) list_cnt[2 * mode + i] = 0ull;
 }
 
@@ -326,8 +336,11 @@ int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* 
                    const float* fmin, int p, double eps, const double* binom_row, const float4* zhi,
                    const float4* zlo, const float* r32, const float* Phat, WalkBuffers& wb,
                    DevScalars* ds, DevScalars* h_ds, cudaStream_t st) {
-    WalkCells c{t.nchild, t.first_child, zc, r, P, fmin, binom_row, p, eps, zhi, zlo, r32, Phat};
-    (k_walk_init<<<1, 256, 0, st>>>(wb.front0, ds->cnt, ds->list_cnt, kMaxWalkIters + 2, mode), note_launch());
+    WalkCells c{t.nnodes, t.nchild, t.first_child, zc, r, P, fmin, binom_row, p, eps, zhi, zlo, r32, Phat};
+    const int nroots = t.nroots;
+    const int ninit = nroots > kMaxWalkIters + 2 ? nroots : kMaxWalkIters + 2;
+    (k_walk_init<<<blocks_for(ninit, 256), 256, 0, st>>>(wb.front0, nroots, ds->cnt, ds->list_cnt,
+                                                          kMaxWalkIters + 2, mode), note_launch());
     int2* acc_list = wb.out[mode == 0 ? 0 : 2];
     int2* leaf_list = wb.out[mode == 0 ? 1 : 3];
     const int64_t cap_acc = wb.out_cap[mode == 0 ? 0 : 2];
@@ -356,6 +369,7 @@ int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* 
             cudaMemcpyAsync(&err, &ds->err, sizeof(err), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return FMM_ERR_CUDA;
+        if (err & kErrIndex) return kWalkBadIndex;
         if (err & kErrCapacity) return FMM_ERR_CAPACITY;
         if (nxt == 0) break;
     }
