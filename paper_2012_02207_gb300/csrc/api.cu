@@ -189,12 +189,23 @@ int build_directed(fmm_ctx* ctx, int which, cudaStream_t st) {
     if ((rc = ensure(ctx, ctx->dalt, keys_bytes)) != FMM_OK) return rc;
     if ((rc = ensure(ctx, ctx->doff[which], sizeof(uint32_t) * (size_t)(ctx->nnodes + 2))) != FMM_OK) return rc;
     if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(2 * np + 1))) != FMM_OK) return rc;
+    ctx->ndirected[which] = 2 * np;
+    if (2 * ctx->nb <= 32) {
+        // 32-bit keys: half the bytes per radix pass; both ping-pong halves fit in dalt
+        uint32_t* ka = as<uint32_t>(ctx->dalt);
+        uint32_t* kb = ka + (2 * np + 1);
+        pairs_to_directed32(as<int2>(ctx->lists[which]), np, ctx->nb, ka,
+                            as<unsigned long long>(ctx->dcount) + 2 + which, st);
+        const int in1 = radix_sort32(ka, kb, 2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st);
+        directed_offsets_widen(in1 ? kb : ka, 2 * np, ctx->nb, ctx->nnodes, as<uint64_t>(ctx->dkeys[which]),
+                               as<uint32_t>(ctx->doff[which]), st);
+        return FMM_OK;
+    }
     pairs_to_directed(as<int2>(ctx->lists[which]), np, ctx->nb, as<uint64_t>(ctx->dkeys[which]),
                       as<unsigned long long>(ctx->dcount) + 2 + which, st);
     const int in1 = radix_sort(as<uint64_t>(ctx->dkeys[which]), nullptr, as<uint64_t>(ctx->dalt), nullptr,
                                2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st);
     if (in1) std::swap(ctx->dkeys[which], ctx->dalt);
-    ctx->ndirected[which] = 2 * np;
     directed_offsets(as<uint64_t>(ctx->dkeys[which]), 2 * np, ctx->nb, ctx->nnodes,
                      as<uint32_t>(ctx->doff[which]), st);
     return FMM_OK;
@@ -407,10 +418,10 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
         multipoles_to_f32_padded(as<double>(ctx->mult), as<float>(ctx->mult32), nnodes, (int)nr,
                                  (int)((nr + 3) & ~(size_t)3), st);
         m2l_f32(nnodes, p, mk, mo, ctx->nb, as<float>(ctx->mult32), as<float4>(ctx->zhi), as<float4>(ctx->zlo),
-                as<float>(ctx->loc32), st);
+                as<float>(ctx->loc32), &ctx->ds->queue, st);
     } else {
         m2l_f64(nnodes, p, mk, mo, ctx->nb, as<double>(ctx->mult), as<double>(ctx->zc), as<double>(ctx->hs),
-                as<double>(ctx->loc), ctx->tb, st);
+                as<double>(ctx->loc), ctx->tb, &ctx->ds->queue, st);
         if (mixed) multipoles_to_f32(as<double>(ctx->loc), as<float>(ctx->loc32), (int64_t)(K * nr), st);
     }
     CK(cudaEventRecord(ctx->ev[5], st));
@@ -525,6 +536,20 @@ int fmm_create(fmm_ctx** out, const fmm_config* cfg) {
     blob.insert(blob.end(), ctx->ht.diag, ctx->ht.diag + nd);
     blob.insert(blob.end(), ctx->ht.sub, ctx->ht.sub + nd);
     blob.insert(blob.end(), &ctx->ht.binom[cfg->p][0], &ctx->ht.binom[cfg->p][0] + nd);
+    // z-shift coefficients sqrt(C(n+m,k) C(n-m,k)) from exact binomials
+    // (every C(a, k) with a <= 2 kMaxP is below 2^63; long double keeps them exact)
+    const size_t zsh_at = blob.size();
+    blob.resize(blob.size() + kZShiftSize);
+    for (int n = 0; n <= kMaxP; ++n)
+        for (int m = 0; m <= n; ++m)
+            for (int k = 0; k <= n - m; ++k) {
+                long double c1 = 1.0L, c2 = 1.0L;
+                for (int i = 1; i <= k; ++i) {
+                    c1 = c1 * (long double)(n + m - k + i) / (long double)i;
+                    c2 = c2 * (long double)(n - m - k + i) / (long double)i;
+                }
+                blob[zsh_at + zshift_offset(n, m) + k] = (double)sqrtl(c1 * c2);
+            }
     if (ensure(ctx, ctx->tables, blob.size() * sizeof(double)) != FMM_OK ||
         cudaMemcpy(ctx->tables.ptr, blob.data(), blob.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMalloc(&ctx->ds, sizeof(DevScalars)) != cudaSuccess ||
@@ -546,6 +571,7 @@ int fmm_create(fmm_ctx** out, const fmm_config* cfg) {
     ctx->tb.rec_b = base + o; o += nrec;
     ctx->tb.diag = base + o; o += nd;
     ctx->tb.sub = base + o; o += nd;
+    ctx->tb.zshift = base + zsh_at;
     upload_expansion_tables(ctx->ht);
     upload_leaf_tables(ctx->ht);
     for (auto& e : ctx->ev) cudaEventCreate(&e);

@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m(TreeView t, int p, TabF64 tb
         for (int i0 = t.begin[k]; i0 < t.end[k]; i0 += 32) {
             const int i = i0 + lane;
             const bool act = i < t.end[k];
+            const int nact = t.end[k] - i0 < 32 ? t.end[k] - i0 : 32;  // bodies in this chunk
             const double x = act ? (xs[i] - cx) * is : 0.0, y = act ? (ys[i] - cy) * is : 0.0,
                          z = act ? (zs[i] - cz) * is : 0.0, w = act ? ms[i] : 0.0;
             const double r2 = x * x + y * y + z * z;
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m(TreeView t, int p, TabF64 tb
                         const int ent = lane + 32 * h;
                         if (ent < 2 * (p - m + 1)) {
                             double s = acc[m][h];
-                            for (int l = 0; l < 32; ++l) s += tile[ent][l];
+                            for (int l = 0; l < nact; ++l) s += tile[ent][l];  // the rest are zeros
                             acc[m][h] = s;
                         }
                     }

@@ -35,7 +35,7 @@ __host__ __device__ constexpr int ncoef_real(int p) { return (p + 1) * (p + 1); 
 struct DevScalars {
     double box[8];                 // cx, cy, cz, h, lox, loy, loz, size
     unsigned err;                  // kErr* bits
-    int pad;
+    unsigned queue;                // work counter of the M2L kernels (zeroed before each launch)
     unsigned long long cnt[kMaxWalkIters + 2];  // walk frontier sizes per iteration
     unsigned long long list_cnt[4];             // far, near, m2l, p2p
     int nnodes;
@@ -66,7 +66,14 @@ struct DevTables {
     const double* rec_b;
     const double* diag;
     const double* sub;
+    const double* zshift;     // sqrt(C(n+m,k) C(n-m,k)) at zshift_offset(n, m) + k, k <= n-m
 };
+
+// offset of (n, m) in the z-shift coefficient table (n <= kMaxP, 0 <= m <= n)
+__host__ __device__ constexpr int zshift_offset(int n, int m) {
+    return n * (n + 1) * (n + 2) / 6 + m * (n + 1) - m * (m - 1) / 2;
+}
+constexpr int kZShiftSize = zshift_offset(kMaxP + 1, 0);
 
 inline size_t swap_cos_offset(int n) { return (size_t)n * (n + 1) * (2 * n + 1) / 6; }  // sum_{k<n}(k+1)^2
 inline size_t swap_sin_offset(int n) { return (size_t)(n - 1) * n * (2 * n - 1) / 6; }  // sum_{k<n} k^2
@@ -97,6 +104,8 @@ void note_launch();
 size_t radix_hist_words(int64_t n);
 int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bits,
                uint32_t* hist, cudaStream_t st);
+// The same for 32-bit keys without payload.
+int radix_sort32(uint32_t* k0, uint32_t* k1, int64_t n, int bits, uint32_t* hist, cudaStream_t st);
 // single-block exclusive scan of count uint32 values in place; total -> *total (device)
 void scan_exclusive_u32(uint32_t* data, int64_t count, uint32_t* total, cudaStream_t st);
 // the same for large tables (multi-block); scratch: scan_scratch_words(count) words
@@ -170,6 +179,12 @@ void scalar_force(const TreeView& t, const double* zc, const double* M, const fl
 // directed entries of a pair list: (B<-A) and (A<-B), self pairs once.
 void pairs_to_directed(const int2* pairs, int64_t npairs, int nb, uint64_t* keys,
                        unsigned long long* count, cudaStream_t st);
+// 32-bit keys (when 2 nb <= 32); the sorted keys are widened to 64 bits by
+// directed_offsets_widen, which also writes the CSR offsets.
+void pairs_to_directed32(const int2* pairs, int64_t npairs, int nb, uint32_t* keys,
+                         unsigned long long* count, cudaStream_t st);
+void directed_offsets_widen(const uint32_t* k32, int64_t nkeys, int nb, int nnodes, uint64_t* keys,
+                            uint32_t* off, cudaStream_t st);
 // CSR offsets (nnodes + 1) of sorted directed keys.
 void directed_offsets(const uint64_t* keys, int64_t nkeys, int nb, int nnodes, uint32_t* off,
                       cudaStream_t st);
@@ -208,11 +223,13 @@ void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const
 // ----------------------------------------------------------------- m2l.cu
 // Rotation-accelerated M2L (Sec. 2.4), gathered per target over the sorted
 // directed list; writes the locals of every node (zero without sources).
+// queue: a device counter, zeroed here; warps take target cells from it.
 void m2l_f64(int nnodes, int p, const uint64_t* keys, const uint32_t* off, int nb,
              const double* mult, const double* zc, const double* hs, double* loc,
-             const DevTables& tb, cudaStream_t st);
+             const DevTables& tb, unsigned* queue, cudaStream_t st);
 void m2l_f32(int nnodes, int p, const uint64_t* keys, const uint32_t* off, int nb,
-             const float* mult, const float4* zhi, const float4* zlo, float* loc, cudaStream_t st);
+             const float* mult, const float4* zhi, const float4* zlo, float* loc, unsigned* queue,
+             cudaStream_t st);
 bool m2l32_supported(int p);
 
 // ----------------------------------------------------------------- p2p.cu

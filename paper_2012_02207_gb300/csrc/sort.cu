@@ -14,9 +14,17 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 16;                   // keys per thread
 constexpr int kTile = kThreads * kItems;     // 4096 keys per block
 constexpr int kWarpItems = kTile / kWarps;   // 512 contiguous keys per warp
-constexpr size_t kScatterSmem = (size_t)kTile * (8 + 4) + (size_t)(kWarps + 2) * 256 * 4;
+template <typename K, bool VAL>
+constexpr size_t scatter_smem() {
+    return (size_t)kTile * (sizeof(K) + (VAL ? 4 : 0)) + (size_t)(kWarps + 2) * 256 * 4;
+}
+// blocks per SM the scatter's registers are cut for: three for 32-bit keys
+// without payload (80 registers, no spills), two otherwise
+template <typename K, bool VAL>
+constexpr int scatter_min_blocks() { return (sizeof(K) == 4 && !VAL) ? 3 : 2; }
 
-__global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ keys, int64_t n,
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_hist(const K* __restrict__ keys, int64_t n,
                                                    int shift, uint32_t* __restrict__ hist,
                                                    int nblocks) {
     __shared__ uint32_t h[256];
@@ -36,16 +44,17 @@ __global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ 
 // digit (warp match + per-warp digit counters), reorder the tile by digit in
 // shared memory, then write each digit's run to its global position with
 // consecutive threads writing consecutive addresses.
-__global__ void __launch_bounds__(kThreads, 2) k_scatter(const uint64_t* __restrict__ kin,
+template <typename K, bool VAL>
+__global__ void __launch_bounds__(kThreads, scatter_min_blocks<K, VAL>()) k_scatter(const K* __restrict__ kin,
                                                       const uint32_t* __restrict__ vin,
-                                                      uint64_t* __restrict__ kout,
+                                                      K* __restrict__ kout,
                                                       uint32_t* __restrict__ vout, int64_t n,
                                                       int shift, const uint32_t* __restrict__ offs,
                                                       int nblocks) {
     extern __shared__ __align__(16) unsigned char sh_scatter[];
-    uint64_t* skey = reinterpret_cast<uint64_t*>(sh_scatter);                    // kTile
-    uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kTile);                  // kTile
-    uint32_t (*wcount)[256] = reinterpret_cast<uint32_t (*)[256]>(sval + kTile);  // kWarps x 256
+    K* skey = reinterpret_cast<K*>(sh_scatter);                                  // kTile
+    uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kTile);                  // kTile (VAL only)
+    uint32_t (*wcount)[256] = reinterpret_cast<uint32_t (*)[256]>(sval + (VAL ? kTile : 0));  // kWarps x 256
     uint32_t* boff = &wcount[kWarps][0];    // global start of each digit for this tile
     uint32_t* lstart = boff + 256;          // start of each digit inside the tile
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -54,14 +63,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter(const uint64_t* __restr
     __syncthreads();
     const int64_t tile0 = (int64_t)blockIdx.x * kTile;
     const int64_t base = tile0 + (int64_t)warp * kWarpItems;
-    uint64_t key[kItems];
-    uint32_t val[kItems], rank[kItems];
+    K key[kItems];
+    uint32_t val[VAL ? kItems : 1], rank[kItems];
     // all loads first, so that they are in flight together
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const int64_t i = base + r * 32 + lane;
-        key[r] = i < n ? kin[i] : 0ull;
-        val[r] = (i < n && vin) ? vin[i] : 0u;
+        key[r] = i < n ? kin[i] : K(0);
+        if (VAL) val[VAL ? r : 0] = i < n ? vin[i] : 0u;
     }
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
@@ -110,17 +119,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter(const uint64_t* __restr
             const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
             const uint32_t pos = lstart[d] + wcount[warp][d] + rank[r];
             skey[pos] = key[r];
-            sval[pos] = val[r];
+            if (VAL) sval[pos] = val[VAL ? r : 0];
         }
     }
     __syncthreads();
     const int cnt = (int)((n - tile0) < kTile ? (n - tile0) : kTile);
     for (int j = threadIdx.x; j < cnt; j += kThreads) {
-        const uint64_t k = skey[j];
+        const K k = skey[j];
         const uint32_t d = (uint32_t)(k >> shift) & 255u;
         const uint32_t pos = boff[d] + (uint32_t)j - lstart[d];
         kout[pos] = k;
-        if (vout) vout[pos] = sval[j];
+        if (VAL) vout[pos] = sval[j];
     }
 }
 
@@ -259,27 +268,42 @@ void scan_exclusive_u32(uint32_t* data, int64_t count, uint32_t* total, cudaStre
     (k_scan<<<1, 1024, 0, st>>>(data, count, total), note_launch());
 }
 
-int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bits,
-               uint32_t* hist, cudaStream_t st) {
+namespace {
+template <typename K, bool VAL>
+int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int bits, uint32_t* hist,
+                    cudaStream_t st) {
     if (n <= 1 || bits <= 0) return 0;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+        cudaFuncSetAttribute(k_scatter<K, VAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem<K, VAL>());
         attr = true;
     }
     const int nblocks = (int)((n + kTile - 1) / kTile);
     int cur = 0;
     for (int shift = 0; shift < bits; shift += 8) {
-        uint64_t* ki = cur ? k1 : k0;
+        K* ki = cur ? k1 : k0;
         uint32_t* vi = cur ? v1 : v0;
-        uint64_t* ko = cur ? k0 : k1;
+        K* ko = cur ? k0 : k1;
         uint32_t* vo = cur ? v0 : v1;
-        (k_hist<<<nblocks, kThreads, 0, st>>>(ki, n, shift, hist, nblocks), note_launch());
+        (k_hist<K><<<nblocks, kThreads, 0, st>>>(ki, n, shift, hist, nblocks), note_launch());
         scan_exclusive_u32_large(hist, (int64_t)256 * nblocks, nullptr, hist + (size_t)256 * nblocks + 1, st);
-        (k_scatter<<<nblocks, kThreads, kScatterSmem, st>>>(ki, vi, ko, vo, n, shift, hist, nblocks), note_launch());
+        (k_scatter<K, VAL><<<nblocks, kThreads, scatter_smem<K, VAL>(), st>>>(ki, vi, ko, vo, n, shift, hist,
+                                                                              nblocks), note_launch());
         cur ^= 1;
     }
     return cur;
+}
+}  // namespace
+
+int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bits,
+               uint32_t* hist, cudaStream_t st) {
+    return v0 ? radix_sort_impl<uint64_t, true>(k0, v0, k1, v1, n, bits, hist, st)
+              : radix_sort_impl<uint64_t, false>(k0, nullptr, k1, nullptr, n, bits, hist, st);
+}
+
+int radix_sort32(uint32_t* k0, uint32_t* k1, int64_t n, int bits, uint32_t* hist, cudaStream_t st) {
+    return radix_sort_impl<uint32_t, false>(k0, nullptr, k1, nullptr, n, bits, hist, st);
 }
 
 }  // namespace gbfmm

@@ -235,6 +235,32 @@ __global__ void k_directed(const int2* __restrict__ pairs, int64_t np, int nb,
     if (pr.x == pr.y) atomicAdd(count, 1ull);
 }
 
+// 32-bit form of k_directed (when 2 nb <= 32): marker 0xffffffff
+__global__ void k_directed32(const int2* __restrict__ pairs, int64_t np, int nb,
+                             uint32_t* __restrict__ keys, unsigned long long* count) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= np) return;
+    const int2 pr = pairs[q];
+    const uint32_t a = (uint32_t)pr.x, b = (uint32_t)pr.y;
+    keys[2 * q] = (b << nb) | a;
+    keys[2 * q + 1] = (pr.x == pr.y) ? 0xffffffffu : ((a << nb) | b);
+    if (pr.x == pr.y) atomicAdd(count, 1ull);
+}
+
+// sorted 32-bit keys -> the 64-bit keys the consumers read, and the CSR offsets
+__global__ void k_offsets_widen(const uint32_t* __restrict__ k32, int64_t nk, int nb, int nnodes,
+                                uint64_t* __restrict__ keys, uint32_t* __restrict__ off) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > nk) return;
+    const uint32_t k = i < nk ? k32[i] : 0xffffffffu;
+    if (i < nk) keys[i] = k == 0xffffffffu ? ~0ull : (uint64_t)k;
+    int64_t t = (i < nk) ? (int64_t)(k >> nb) : (int64_t)nnodes;
+    int64_t tp = (i > 0) ? (int64_t)(k32[i - 1] >> nb) : -1;
+    t = t < nnodes ? t : nnodes;
+    tp = tp < nnodes ? tp : nnodes;
+    for (int64_t u = tp + 1; u <= t && u <= nnodes; ++u) off[u] = (uint32_t)i;
+}
+
 __global__ void k_offsets(const uint64_t* __restrict__ keys, int64_t nk, int nb, int nnodes,
                           uint32_t* __restrict__ off) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -381,6 +407,16 @@ int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* 
 void pairs_to_directed(const int2* pairs, int64_t npairs, int nb, uint64_t* keys,
                        unsigned long long* count, cudaStream_t st) {
     if (npairs > 0) (k_directed<<<blocks_for(npairs, 256), 256, 0, st>>>(pairs, npairs, nb, keys, count), note_launch());
+}
+
+void pairs_to_directed32(const int2* pairs, int64_t npairs, int nb, uint32_t* keys,
+                         unsigned long long* count, cudaStream_t st) {
+    if (npairs > 0) (k_directed32<<<blocks_for(npairs, 256), 256, 0, st>>>(pairs, npairs, nb, keys, count), note_launch());
+}
+
+void directed_offsets_widen(const uint32_t* k32, int64_t nkeys, int nb, int nnodes, uint64_t* keys,
+                            uint32_t* off, cudaStream_t st) {
+    (k_offsets_widen<<<blocks_for(nkeys + 1, 256), 256, 0, st>>>(k32, nkeys, nb, nnodes, keys, off), note_launch());
 }
 
 void directed_offsets(const uint64_t* keys, int64_t nkeys, int nb, int nnodes, uint32_t* off,

@@ -24,20 +24,24 @@ def energy(v, m, pot):
     return float((0.5 * m * (v * v).sum(1)).sum() + 0.5 * (m * pot).sum())
 
 
-def integrate(fmm, pos, vel, mass, dt, steps, callback=None):
+def integrate(fmm, pos, vel, mass, dt, steps, callback=None, direct=False):
     """KDK leapfrog in place on device tensors pos (n,3), vel (n,3), mass (n,).
+    direct=True takes the forces from the FP64 direct sum instead of the FMM.
 
     Returns the list of energies at steps 0..steps."""
     import torch  # noqa: PLC0415
+
+    def forces(cols):
+        return fmm.direct(*cols, mass) if direct else fmm.solve(*cols, mass)
     cols = [pos[:, d].contiguous() for d in range(3)]
-    ax, ay, az, pot = fmm.solve(*cols, mass)
+    ax, ay, az, pot = forces(cols)
     acc = torch.stack([ax, ay, az], 1)
     energies = [energy(vel, mass, pot)]
     for s in range(steps):
         vel += 0.5 * dt * acc
         pos += dt * vel
         cols = [pos[:, d].contiguous() for d in range(3)]
-        ax, ay, az, pot = fmm.solve(*cols, mass)
+        ax, ay, az, pot = forces(cols)
         acc = torch.stack([ax, ay, az], 1)
         vel += 0.5 * dt * acc
         energies.append(energy(vel, mass, pot))
@@ -63,19 +67,26 @@ def main():
     ap.add_argument("--p", type=int, default=12)
     ap.add_argument("--eps", type=float, default=1e-8)
     ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--bh-mass", type=float, default=0.01, help="central point mass (0: a plain Plummer sphere)")
+    ap.add_argument("--forces", default="fmm", choices=["fmm", "direct"],
+                    help="force solve: the mixed-precision FMM, or the FP64 direct sum (O(N^2), a reference)")
     args = ap.parse_args()
-    pos, vel, m = ics.nucleus(args.n, args.seed)
+    if args.bh_mass > 0:
+        pos, vel, m = ics.nucleus(args.n, args.seed, bh_mass=args.bh_mass)
+    else:
+        pos, vel, m = ics.plummer(args.n, args.seed)
     dev = torch.device("cuda:0")
     P = torch.tensor(pos, device=dev)
     V = torch.tensor(vel, device=dev)
     M = torch.tensor(m, device=dev)
     fmm = FMM(p=args.p, eps=args.eps, precision="mixed")
     t0 = time.perf_counter()
-    es = integrate(fmm, P, V, M, args.dt, args.steps)
+    es = integrate(fmm, P, V, M, args.dt, args.steps, direct=args.forces == "direct")
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     drift = [abs(e - es[0]) / abs(es[0]) for e in es]
-    print(json.dumps({"workload": f"nucleus_plummer_n{args.n}_plus_point_mass", "n_bodies": len(m), "p": args.p,
+    name = f"nucleus_plummer_n{args.n}_plus_point_mass_{args.bh_mass:g}" if args.bh_mass > 0 else f"plummer_n{args.n}"
+    print(json.dumps({"workload": name, "n_bodies": len(m), "forces": args.forces, "p": args.p,
                       "eps": args.eps, "dt": args.dt, "steps": args.steps, "E0": es[0], "E_final": es[-1],
                       "max_rel_energy_error": max(drift), "final_rel_energy_error": drift[-1],
                       "wall_s": wall, "solves_per_s": (args.steps + 1) / wall}))
