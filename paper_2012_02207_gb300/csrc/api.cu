@@ -384,7 +384,8 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     // ---- upward pass
     upward_pass(t, ctx->h_level_start, p, as<double>(ctx->xs), as<double>(ctx->ys), as<double>(ctx->zs),
                 as<double>(ctx->ms), as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->hs),
-                as<double>(ctx->mult), as<double>(ctx->Pk), as<float>(ctx->Phat), as<float>(ctx->r32), as<double>(ctx->contrib), ctx->tb, st);
+                as<double>(ctx->mult), as<double>(ctx->Pk), as<float>(ctx->Phat), as<float>(ctx->r32), as<double>(ctx->contrib), ctx->tb,
+                mixed, st);
     CK(cudaEventRecord(ctx->ev[2], st));
     // ---- scalar-force estimate
     if (ctx->front_cap == 0) {

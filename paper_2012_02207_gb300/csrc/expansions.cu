@@ -12,6 +12,7 @@
 //
 // Real layout of a vector: degree n at offset n^2 as [Re m=0, Re 1, Im 1, ...].
 #include "gbfmm_internal.cuh"
+#include "dword.cuh"
 
 namespace gbfmm {
 
@@ -52,6 +53,12 @@ struct TabF32 {
     __device__ float D(int m) const { return c_diag32[m]; }
     __device__ float Sb(int m) const { return c_sub32[m]; }
 };
+
+// double-word copies of the recurrence constants (mixed-precision P2M)
+__constant__ dw c_dw_a[kMaxP + 1][kMaxP + 1];
+__constant__ dw c_dw_b[kMaxP + 1][kMaxP + 1];
+__constant__ dw c_dw_d[kMaxP + 1];
+__constant__ dw c_dw_s[kMaxP + 1];
 
 // All Shat_n^m(x,y,z), 0 <= m <= n <= p, into out[tri(n,m)] (sequential).
 template <typename T, typename Tab>
@@ -181,6 +188,98 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m(TreeView t, int p, TabF64 tb
     }
 }
 
+// The same P2M in double-word FP32 arithmetic (mixed precision): the
+// positions relative to the leaf centre are formed in FP64, split into
+// double words, and every recurrence step and tile sum runs on the FP32
+// pipes in the same order as k_p2m. The result is stored in FP64; its
+// relative error is of order 1e-13 instead of 1e-16, far below what the
+// FP32 translations downstream add.
+template <int PM, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
+                                                 const double* __restrict__ xs,
+                                                 const double* __restrict__ ys,
+                                                 const double* __restrict__ zs,
+                                                 const double* __restrict__ ms,
+                                                 const double* __restrict__ zc,
+                                                 const double* __restrict__ hs,
+                                                 double* __restrict__ mult) {
+    __shared__ dw sh_tile[WARPS][2 * (PM + 1)][33];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    dw (*tile)[33] = sh_tile[wib];
+    const int nr = ncoef_real(p);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const dw zero = dw_make(0.f, 0.f);
+    for (int k = blockIdx.x * (blockDim.x >> 5) + wib; k < t.nnodes; k += nwarps) {
+        if (t.nchild[k] != 0) continue;
+        const double is = 1.0 / hs[k];
+        const double cx = zc[3 * k], cy = zc[3 * k + 1], cz = zc[3 * k + 2];
+        dw acc[PM + 1][2];
+#pragma unroll
+        for (int m = 0; m <= PM; ++m) { acc[m][0] = zero; acc[m][1] = zero; }
+        for (int i0 = t.begin[k]; i0 < t.end[k]; i0 += 32) {
+            const int i = i0 + lane;
+            const bool act = i < t.end[k];
+            const int nact = t.end[k] - i0 < 32 ? t.end[k] - i0 : 32;
+            const dw x = act ? dw_from((xs[i] - cx) * is) : zero, y = act ? dw_from((ys[i] - cy) * is) : zero,
+                     z = act ? dw_from((zs[i] - cz) * is) : zero, w = act ? dw_from(ms[i]) : zero;
+            const dw r2 = dw_add(dw_add(dw_mul(x, x), dw_mul(y, y)), dw_mul(z, z));
+            dw dre = w, dim = zero;  // w * Shat_m^m
+#pragma unroll
+            for (int m = 0; m <= PM; ++m) {
+                if (m <= p) {
+                    if (m > 0) {
+                        const dw tq = dw_sub(dw_mul(dre, x), dw_mul(dim, y));
+                        dim = dw_mul(dw_add(dw_mul(dre, y), dw_mul(dim, x)), c_dw_d[m]);
+                        dre = dw_mul(tq, c_dw_d[m]);
+                    }
+                    dw s1r = dre, s1i = dim, s2r = zero, s2i = zero;
+                    tile[0][lane] = dre;
+                    tile[1][lane] = dim;
+                    for (int n = m + 1; n <= p; ++n) {
+                        dw vr, vi;
+                        if (n == m + 1) {
+                            const dw sz = dw_mul(c_dw_s[m], z);
+                            vr = dw_mul(sz, s1r);
+                            vi = dw_mul(sz, s1i);
+                        } else {
+                            const dw a = dw_mul(c_dw_a[n][m], z), b = dw_mul(c_dw_b[n][m], r2);
+                            vr = dw_sub(dw_mul(a, s1r), dw_mul(b, s2r));
+                            vi = dw_sub(dw_mul(a, s1i), dw_mul(b, s2i));
+                        }
+                        tile[2 * (n - m)][lane] = vr;
+                        tile[2 * (n - m) + 1][lane] = vi;
+                        s2r = s1r; s2i = s1i; s1r = vr; s1i = vi;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int ent = lane + 32 * h;
+                        if (ent < 2 * (p - m + 1)) {
+                            dw sacc = acc[m][h];
+                            for (int l = 0; l < nact; ++l) sacc = dw_add(sacc, tile[ent][l]);
+                            acc[m][h] = sacc;
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        double* out = mult + (size_t)nr * k;
+#pragma unroll
+        for (int m = 0; m <= PM; ++m) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int ent = lane + 32 * h;
+                if (m <= p && ent < 2 * (p - m + 1)) {
+                    const int n = m + (ent >> 1);
+                    if (ent & 1) { if (m) out[him(n, m)] = dw_to(acc[m][h]); }
+                    else out[hre(n, m)] = dw_to(acc[m][h]);
+                }
+            }
+        }
+    }
+}
+
 // P_n = s^n sqrt(sum_{m=-n}^{n} |Mhat_n^m|^2)  (Sec. 2.3)
 // (also the FP32 copies used by the walk's screen: Phat_n = P_n / s^n and r)
 __global__ void k_pnorm(int nnodes, int p, const double* __restrict__ mult,
@@ -301,14 +400,30 @@ void upload_expansion_tables(const HostTables& h) {
     cudaMemcpyToSymbol(c_rec_b32, b, sizeof(b));
     cudaMemcpyToSymbol(c_diag32, d, sizeof(d));
     cudaMemcpyToSymbol(c_sub32, s, sizeof(s));
+    // double words: hi = the float nearest x, lo = the float nearest x - hi
+    static dw da[kMaxP + 1][kMaxP + 1], db[kMaxP + 1][kMaxP + 1], dd[kMaxP + 1], ds[kMaxP + 1];
+    auto split = [](double x) { const float hi = (float)x; return dw{hi, (float)(x - (double)hi)}; };
+    for (int n = 0; n <= kMaxP; ++n) {
+        for (int m = 0; m <= kMaxP; ++m) { da[n][m] = split(h.rec_a[n][m]); db[n][m] = split(h.rec_b[n][m]); }
+        dd[n] = split(h.diag[n]);
+        ds[n] = split(h.sub[n]);
+    }
+    cudaMemcpyToSymbol(c_dw_a, da, sizeof(da));
+    cudaMemcpyToSymbol(c_dw_b, db, sizeof(db));
+    cudaMemcpyToSymbol(c_dw_d, dd, sizeof(dd));
+    cudaMemcpyToSymbol(c_dw_s, ds, sizeof(ds));
 }
 
 void upward_pass(const TreeView& t, const int* h_level_start, int p, const double* xs,
                  const double* ys, const double* zs, const double* ms, const double* zc,
                  const double* r, const double* hs, double* mult, double* Pk, float* Phat, float* r32,
-                 double* contrib, const DevTables& tbl, cudaStream_t st) {
+                 double* contrib, const DevTables& tbl, bool dword, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
-    if (p <= 16)
+    if (dword && p <= 16)
+        (k_p2m_dw<16, 4><<<152 * 8, 128, 0, st>>>(t, p, xs, ys, zs, ms, zc, hs, mult), note_launch());
+    else if (dword)
+        (k_p2m_dw<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, xs, ys, zs, ms, zc, hs, mult), note_launch());
+    else if (p <= 16)
         (k_p2m<16, 4><<<152 * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, hs, mult), note_launch());
     else
         (k_p2m<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, hs, mult), note_launch());

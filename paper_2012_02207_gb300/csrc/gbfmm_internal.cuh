@@ -196,12 +196,13 @@ void upload_expansion_tables(const HostTables& h);
 // that its FP32 local coefficients F s^n fall into the denormal range.
 constexpr double kHatFloor = 0x1p-40;
 void hat_scales(int nnodes, const int* parent, const double* r, double* hs, cudaStream_t st);
-// FP64 hat multipoles: P2M at leaves, M2M level by level; P_k per node.
+// Hat multipoles in FP64: P2M at leaves, M2M level by level; P_k per node.
+// dword: the P2M arithmetic runs in double-word FP32 (mixed precision).
 // r: node sizes (the walk's FP32 copy r32 is written from them); hs: hat scales.
 void upward_pass(const TreeView& t, const int* h_level_start, int p, const double* xs,
                  const double* ys, const double* zs, const double* ms, const double* zc,
                  const double* r, const double* hs, double* mult, double* Pk, float* Phat, float* r32,
-                 double* contrib, const DevTables& tb, cudaStream_t st);
+                 double* contrib, const DevTables& tb, bool dword, cudaStream_t st);
 // rotation-accelerated M2M of one level: children [child0, child1) into their
 // parents [parent0, parent1); contrib: (p+1)^2 doubles per node (scratch)
 void m2m_level_f64(const TreeView& t, int parent0, int parent1, int child0, int child1, int p,
