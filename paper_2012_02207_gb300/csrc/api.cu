@@ -56,7 +56,7 @@ struct fmm_ctx {
     fmm_stats stats{};
     HostTables ht{};
     DevTables tb{};
-    Buf tables;
+    Buf tables, tables_dw;
     DevScalars* ds = nullptr;
     DevScalars* h_ds = nullptr;  // pinned
     cudaEvent_t ev[10] = {};
@@ -573,6 +573,30 @@ int fmm_create(fmm_ctx** out, const fmm_config* cfg) {
     ctx->tb.diag = base + o; o += nd;
     ctx->tb.sub = base + o; o += nd;
     ctx->tb.zshift = base + zsh_at;
+    // double-word copies: hi = the float nearest x, lo = the float nearest x - hi
+    {
+        std::vector<float2> dwb;
+        auto put = [&dwb](const double* src, size_t cnt) {
+            for (size_t i = 0; i < cnt; ++i) {
+                const float hi = (float)src[i];
+                dwb.push_back(make_float2(hi, (float)(src[i] - (double)hi)));
+            }
+        };
+        put(kSwapCos, ncos);
+        put(kSwapSin, nsin);
+        put(blob.data() + zsh_at, kZShiftSize);
+        if (ensure(ctx, ctx->tables_dw, dwb.size() * sizeof(float2)) != FMM_OK ||
+            cudaMemcpy(ctx->tables_dw.ptr, dwb.data(), dwb.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            g_create_error = "device allocation failed in fmm_create";
+            fmm_destroy(ctx);
+            return FMM_ERR_OOM;
+        }
+        const float2* b2 = reinterpret_cast<const float2*>(ctx->tables_dw.ptr);
+        ctx->tb.swap_cos_dw = b2;
+        ctx->tb.swap_sin_dw = b2 + ncos;
+        ctx->tb.zshift_dw = b2 + ncos + nsin;
+    }
     upload_expansion_tables(ctx->ht);
     upload_leaf_tables(ctx->ht);
     for (auto& e : ctx->ev) cudaEventCreate(&e);
@@ -587,7 +611,7 @@ int fmm_create(fmm_ctx** out, const fmm_config* cfg) {
 
 void fmm_destroy(fmm_ctx* ctx) {
     if (!ctx) return;
-    Buf* all[] = {&ctx->tables, &ctx->k0, &ctx->k1, &ctx->v0, &ctx->v1, &ctx->hist, &ctx->xs, &ctx->ys,
+    Buf* all[] = {&ctx->tables, &ctx->tables_dw, &ctx->k0, &ctx->k1, &ctx->v0, &ctx->v1, &ctx->hist, &ctx->xs, &ctx->ys,
                   &ctx->zs, &ctx->ms, &ctx->xf, &ctx->prel, &ctx->lcp, &ctx->win, &ctx->hi, &ctx->chunk,
                   &ctx->f, &ctx->bbox, &ctx->level, &ctx->begin, &ctx->end, &ctx->parent,
                   &ctx->first_child, &ctx->nchild, &ctx->M, &ctx->S, &ctx->zc, &ctx->r, &ctx->hs, &ctx->Pk,

@@ -430,8 +430,8 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
     const int nr = ncoef_real(p);
     (void)nr;
     for (int L = t.nlevels - 2; L >= 0; --L)
-        m2m_level_f64(t, h_level_start[L], h_level_start[L + 1], h_level_start[L + 1], h_level_start[L + 2], p,
-                      zc, hs, mult, contrib, tbl, st);
+        m2m_level(t, h_level_start[L], h_level_start[L + 1], h_level_start[L + 1], h_level_start[L + 2], p,
+                  zc, hs, mult, contrib, tbl, dword, st);
     (k_pnorm<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, p, mult, r, hs, Pk, Phat, r32), note_launch());
 }
 

@@ -67,6 +67,10 @@ struct DevTables {
     const double* diag;
     const double* sub;
     const double* zshift;     // sqrt(C(n+m,k) C(n-m,k)) at zshift_offset(n, m) + k, k <= n-m
+    // double-word (hi, lo float pairs) copies of the swap and z-shift tables
+    const float2* swap_cos_dw;
+    const float2* swap_sin_dw;
+    const float2* zshift_dw;
 };
 
 // offset of (n, m) in the z-shift coefficient table (n <= kMaxP, 0 <= m <= n)
@@ -197,17 +201,18 @@ void upload_expansion_tables(const HostTables& h);
 constexpr double kHatFloor = 0x1p-40;
 void hat_scales(int nnodes, const int* parent, const double* r, double* hs, cudaStream_t st);
 // Hat multipoles in FP64: P2M at leaves, M2M level by level; P_k per node.
-// dword: the P2M arithmetic runs in double-word FP32 (mixed precision).
+// dword: the P2M and M2M arithmetic runs in double-word FP32 (mixed precision).
 // r: node sizes (the walk's FP32 copy r32 is written from them); hs: hat scales.
 void upward_pass(const TreeView& t, const int* h_level_start, int p, const double* xs,
                  const double* ys, const double* zs, const double* ms, const double* zc,
                  const double* r, const double* hs, double* mult, double* Pk, float* Phat, float* r32,
                  double* contrib, const DevTables& tb, bool dword, cudaStream_t st);
 // rotation-accelerated M2M of one level: children [child0, child1) into their
-// parents [parent0, parent1); contrib: (p+1)^2 doubles per node (scratch)
-void m2m_level_f64(const TreeView& t, int parent0, int parent1, int child0, int child1, int p,
-                   const double* zc, const double* hs, double* mult, double* contrib, const DevTables& tb,
-                   cudaStream_t st);
+// parents [parent0, parent1); contrib: (p+1)^2 doubles per node (scratch);
+// dword: double-word FP32 arithmetic instead of FP64
+void m2m_level(const TreeView& t, int parent0, int parent1, int child0, int child1, int p,
+               const double* zc, const double* hs, double* mult, double* contrib, const DevTables& tb,
+               bool dword, cudaStream_t st);
 void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStream_t st);
 // FP32 copy with each node's vector padded to `stride` floats (zeros after nr)
 void multipoles_to_f32_padded(const double* mult, float* mult32, int nnodes, int nr, int stride, cudaStream_t st);
