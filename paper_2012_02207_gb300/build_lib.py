@@ -26,7 +26,7 @@ NO_FMA = {"tree.cu", "walk.cu", "noalloc.cu"}
 FTZ = {"p2p.cu", "m2l.cu"}
 M2L32_ORDERS = [4, 6, 8, 10, 12, 14]  # orders of the FP32 register M2L kernel
 EXTRA_FLAGS = os.environ.get("GBFMM_NVCC_FLAGS", "").split()  # extra nvcc flags for experiments
-SOURCES = ["api.cu", "sort.cu", "tree.cu", "walk.cu", "expansions.cu", "m2l.cu", "m2m.cu", "p2p.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "sort.cu", "tree.cu", "walk.cu", "expansions.cu", "m2l.cu", "translate.cu", "p2p.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -427,7 +427,8 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     }
     CK(cudaEventRecord(ctx->ev[5], st));
     if (mixed)
-        downward_pass_f32(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->hs), as<float>(ctx->loc32), st);
+        downward_pass_f32(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->hs), as<float>(ctx->loc32),
+                          ctx->tb, st);
     else
         downward_pass_f64(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->hs), as<double>(ctx->loc),
                           ctx->tb, st);

@@ -461,29 +461,39 @@ void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStr
     if (count > 0) (k_to_f32<<<blocks_for(count, 256), 256, 0, st>>>(mult, mult32, count), note_launch());
 }
 
+// L2L level by level: the rotation form (translate.cu) unless GBFMM_L2L_DIRECT
+// selects the direct O(p^4) kernel above.
+#ifndef GBFMM_L2L_DIRECT
+#define GBFMM_L2L_DIRECT 0
+#endif
+
 void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const double* zc,
                        const double* hs, double* loc, const DevTables& tbl, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
     const int nc = tri(p + 1, 0), nr = ncoef_real(p);
     const size_t sh = (size_t)(2 * nc + nr + p + 1) * sizeof(double);
     static bool attr_set = false;
-    if (!attr_set) {
+    if (GBFMM_L2L_DIRECT && !attr_set) {
         cudaFuncSetAttribute(k_l2l<double, TabF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr_set = true;
     }
     for (int L = 1; L < t.nlevels; ++L) {
         const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
-        if (k1 > k0) (k_l2l<double, TabF64><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, tb, zc, hs, loc), note_launch());
+        if (k1 <= k0) continue;
+        if (GBFMM_L2L_DIRECT) (k_l2l<double, TabF64><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, tb, zc, hs, loc), note_launch());
+        else l2l_level(t, k0, k1, p, zc, hs, loc, tbl, false, st);
     }
 }
 
 void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const double* zc,
-                       const double* hs, float* loc, cudaStream_t st) {
+                       const double* hs, float* loc, const DevTables& tbl, cudaStream_t st) {
     const int nc = tri(p + 1, 0), nr = ncoef_real(p);
     const size_t sh = (size_t)(2 * nc + nr + p + 1) * sizeof(float);
     for (int L = 1; L < t.nlevels; ++L) {
         const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
-        if (k1 > k0) (k_l2l<float, TabF32><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, TabF32{}, zc, hs, loc), note_launch());
+        if (k1 <= k0) continue;
+        if (GBFMM_L2L_DIRECT) (k_l2l<float, TabF32><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, TabF32{}, zc, hs, loc), note_launch());
+        else l2l_level(t, k0, k1, p, zc, hs, loc, tbl, true, st);
     }
 }
 

@@ -213,6 +213,10 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
 void m2m_level(const TreeView& t, int parent0, int parent1, int child0, int child1, int p,
                const double* zc, const double* hs, double* mult, double* contrib, const DevTables& tb,
                bool dword, cudaStream_t st);
+// rotation-accelerated L2L of one level: the locals of nodes [k0, k1) gain
+// their parents' shifted locals; loc: FP32 (fp32) or FP64 (p+1)^2 per node
+void l2l_level(const TreeView& t, int k0, int k1, int p, const double* zc, const double* hs, void* loc,
+               const DevTables& tb, bool fp32, cudaStream_t st);
 void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStream_t st);
 // FP32 copy with each node's vector padded to `stride` floats (zeros after nr)
 void multipoles_to_f32_padded(const double* mult, float* mult32, int nnodes, int nr, int stride, cudaStream_t st);
@@ -224,7 +228,7 @@ void node_centres_f32(int nnodes, const double* zc, const double* hs, float4* zh
 void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const double* zc,
                        const double* hs, double* loc, const DevTables& tb, cudaStream_t st);
 void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const double* zc,
-                       const double* hs, float* loc, cudaStream_t st);
+                       const double* hs, float* loc, const DevTables& tb, cudaStream_t st);
 
 // ----------------------------------------------------------------- m2l.cu
 // Rotation-accelerated M2L (Sec. 2.4), gathered per target over the sorted

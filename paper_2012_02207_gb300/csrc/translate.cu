@@ -1,6 +1,7 @@
-// Rotation-accelerated M2M (Sec. 2.1 translation, done with the rotations of
-// Sec. 2.4), one warp per child cell, in FP64 (FP64 mode) or in double-word
-// FP32 (mixed precision; see dword.cuh).
+// Rotation-accelerated M2M and L2L (the translations of Sec. 2.1, done with
+// the rotations of Sec. 2.4), one warp per child cell. M2M runs in FP64 (FP64
+// mode) or double-word FP32 (mixed precision; see dword.cuh); L2L in FP64 or
+// FP32.
 #include "dword.cuh"
 #include "gbfmm_internal.cuh"
 #include "swap_tables.cuh"
@@ -23,6 +24,10 @@ __device__ __forceinline__ double ar_add(double a, double b) { return a + b; }
 __device__ __forceinline__ double ar_sub(double a, double b) { return a - b; }
 __device__ __forceinline__ double ar_mul(double a, double b) { return a * b; }
 __device__ __forceinline__ double ar_neg(double a) { return -a; }
+__device__ __forceinline__ float ar_add(float a, float b) { return a + b; }
+__device__ __forceinline__ float ar_sub(float a, float b) { return a - b; }
+__device__ __forceinline__ float ar_mul(float a, float b) { return a * b; }
+__device__ __forceinline__ float ar_neg(float a) { return -a; }
 __device__ __forceinline__ dw ar_add(dw a, dw b) { return dw_add(a, b); }
 __device__ __forceinline__ dw ar_sub(dw a, dw b) { return dw_sub(a, b); }
 __device__ __forceinline__ dw ar_mul(dw a, dw b) { return dw_mul(a, b); }
@@ -30,16 +35,36 @@ __device__ __forceinline__ dw ar_neg(dw a) { return dw_neg(a); }
 template <typename T> __device__ __forceinline__ T ar_from(double x);
 template <> __device__ __forceinline__ double ar_from<double>(double x) { return x; }
 template <> __device__ __forceinline__ dw ar_from<dw>(double x) { return dw_from(x); }
+template <> __device__ __forceinline__ float ar_from<float>(double x) { return (float)x; }
 __device__ __forceinline__ double ar_to(double x) { return x; }
+__device__ __forceinline__ double ar_to(float x) { return (double)x; }
 __device__ __forceinline__ double ar_to(dw x) { return dw_to(x); }
 
 // tables in the working precision: swap blocks (cos_off/sin_off layout) and
-// the z-shift coefficients (zshift_offset layout)
+// the z-shift coefficients (zshift_offset layout); FP32 and double-word read
+// the (hi, lo) pair tables, FP32 their hi part
 template <typename T>
-struct M2MTables {
-    const T* cosb;
-    const T* sinb;
-    const T* zsh;
+struct RotTables;
+template <>
+struct RotTables<double> {
+    const double *cosb, *sinb, *zsh;
+    __device__ double c(int i) const { return __ldg(cosb + i); }
+    __device__ double s(int i) const { return __ldg(sinb + i); }
+    __device__ double z(int i) const { return __ldg(zsh + i); }
+};
+template <>
+struct RotTables<dw> {
+    const float2 *cosb, *sinb, *zsh;
+    __device__ dw c(int i) const { const float2 v = __ldg(cosb + i); return dw{v.x, v.y}; }
+    __device__ dw s(int i) const { const float2 v = __ldg(sinb + i); return dw{v.x, v.y}; }
+    __device__ dw z(int i) const { const float2 v = __ldg(zsh + i); return dw{v.x, v.y}; }
+};
+template <>
+struct RotTables<float> {
+    const float2 *cosb, *sinb, *zsh;
+    __device__ float c(int i) const { return __ldg(cosb + i).x; }
+    __device__ float s(int i) const { return __ldg(sinb + i).x; }
+    __device__ float z(int i) const { return __ldg(zsh + i).x; }
 };
 
 // coefficient q of the real layout -> (n, m, imaginary part?)
@@ -98,7 +123,7 @@ __device__ void wrotz(WarpVec<T>& w, int p, const T* pw, bool conj, int lane) {
 }
 
 template <typename T>
-__device__ void wswap(WarpVec<T>& w, int p, const M2MTables<T>& tb, int lane) {
+__device__ void wswap(WarpVec<T>& w, int p, const RotTables<T>& tb, int lane) {
     const int nr = ncoef_real(p);
     for (int q = lane; q < nr; q += 32) {
         int n, mm;
@@ -106,11 +131,11 @@ __device__ void wswap(WarpVec<T>& w, int p, const M2MTables<T>& tb, int lane) {
         decode_q(q, n, mm, im);
         T acc = ar_from<T>(0.0);
         if (!im) {
-            const T* A = tb.cosb + cos_off(n) + mm * (n + 1);
-            for (int j = (mm + n) & 1; j <= n; j += 2) acc = ar_add(acc, ar_mul(A[j], w.v[hre(n, j)]));
+            const int a0 = cos_off(n) + mm * (n + 1);
+            for (int j = (mm + n) & 1; j <= n; j += 2) acc = ar_add(acc, ar_mul(tb.c(a0 + j), w.v[hre(n, j)]));
         } else {
-            const T* B = tb.sinb + sin_off(n) + (mm - 1) * n;
-            for (int j = ((mm + n + 1) & 1) ? 1 : 2; j <= n; j += 2) acc = ar_add(acc, ar_mul(B[j - 1], w.v[him(n, j)]));
+            const int b0 = sin_off(n) + (mm - 1) * n;
+            for (int j = ((mm + n + 1) & 1) ? 1 : 2; j <= n; j += 2) acc = ar_add(acc, ar_mul(tb.s(b0 + j - 1), w.v[him(n, j)]));
         }
         w.t[q] = acc;
     }
@@ -126,7 +151,7 @@ __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int k0, int k1, int
                                                   const double* __restrict__ zc,
                                                   const double* __restrict__ hs,
                                                   const double* __restrict__ mult,
-                                                  double* __restrict__ contrib, M2MTables<T> tb) {
+                                                  double* __restrict__ contrib, RotTables<T> tb) {
     extern __shared__ __align__(16) unsigned char sh_m2m_raw[];
     T* sh_m2m = reinterpret_cast<T*>(sh_m2m_raw);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -175,10 +200,10 @@ __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int k0, int k1, int
         int n, mm;
         bool im;
         decode_q(q, n, mm, im);
-        const T* cz = tb.zsh + zshift_offset(n, mm);
+        const int cz = zshift_offset(n, mm);
         T acc = ar_from<T>(0.0);
         for (int k = 0; k <= n - mm; ++k)
-            acc = ar_add(acc, ar_mul(ar_mul(cz[k], upow[k]),
+            acc = ar_add(acc, ar_mul(ar_mul(tb.z(cz + k), upow[k]),
                                      ar_mul(spow[n - k], wv.v[im ? him(n - k, mm) : hre(n - k, mm)])));
         wv.t[q] = acc;
     }
@@ -190,6 +215,77 @@ __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int k0, int k1, int
     wrotz(wv, p, pwa, true, lane);   // Rz(phi - pi/2)
     double* dst = contrib + (size_t)nr * C;
     for (int q = lane; q < nr; q += 32) dst[q] = ar_to(wv.v[q]);
+}
+
+// Rotation-accelerated L2L: with b = z_C - z_P rotated onto +z,
+//     Fhat_n^m(C) += sigma^n sum_{k=0}^{p-n} sqrt(C(n+k+m,k) C(n+k-m,k)) u^k Fhat_{n+k}^m(P),
+// u = rho/s_P, sigma = s_C/s_P (the hat form of F_n^m(C) = sum_k rho^k/k! F_{n+k}^m(P)
+// on the axis), between the same rotations as M2M. The local coefficients
+// (T = float or double) are added to the child's, which the M2L wrote.
+template <typename T>
+__global__ void __launch_bounds__(128) k_l2l_rot(TreeView t, int k0, int k1, int p,
+                                                  const double* __restrict__ zc,
+                                                  const double* __restrict__ hs,
+                                                  T* __restrict__ loc, RotTables<T> tb) {
+    extern __shared__ __align__(16) unsigned char sh_l2l_raw[];
+    T* sh = reinterpret_cast<T*>(sh_l2l_raw);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nr = ncoef_real(p);
+    T* base = sh + (size_t)wib * m2m_warp_values(p);
+    WarpVec<T> wv{base, base + nr};
+    T* pwa = base + 2 * nr;
+    T* pwb = pwa + 2 * (p + 1);
+    T* upow = pwb + 2 * (p + 1);
+    T* spow = upow + (p + 1);
+    const int C = k0 + blockIdx.x * (blockDim.x >> 5) + wib;
+    if (C >= k1) return;
+    const int P = t.parent[C];
+    const T* src = loc + (size_t)nr * P;
+    for (int q = lane; q < nr; q += 32) wv.v[q] = src[q];
+    const double bx = zc[3 * C] - zc[3 * P], by = zc[3 * C + 1] - zc[3 * P + 1], bz = zc[3 * C + 2] - zc[3 * P + 2];
+    const double rxy2 = bx * bx + by * by;
+    const double rho = sqrt(rxy2 + bz * bz);
+    const double rxy = sqrt(rxy2);
+    double cp = 1.0, sp = 0.0, ct = 1.0, st = 0.0;
+    if (rxy > 0.0) { cp = bx / rxy; sp = by / rxy; }
+    if (rho > 0.0) { ct = bz / rho; st = rxy / rho; }
+    const double sP = hs[P];
+    const double u = rho / sP, sg = hs[C] / sP;
+    wpowers<T>(pwa, p, ar_from<T>(sp), ar_from<T>(cp), lane);
+    wpowers<T>(pwb, p, ar_from<T>(ct), ar_from<T>(-st), lane);
+    if (lane <= p) {
+        T a = ar_from<T>(1.0), b = ar_from<T>(1.0), ba = ar_from<T>(u), bb = ar_from<T>(sg);
+        for (int e = lane; e > 0; e >>= 1) {
+            if (e & 1) { a = ar_mul(a, ba); b = ar_mul(b, bb); }
+            ba = ar_mul(ba, ba);
+            bb = ar_mul(bb, bb);
+        }
+        upow[lane] = a;
+        spow[lane] = b;
+    }
+    __syncwarp();
+    wrotz(wv, p, pwa, false, lane);  // Rz(pi/2 - phi)
+    wswap(wv, p, tb, lane);
+    wrotz(wv, p, pwb, false, lane);  // Rz(-theta)
+    wswap(wv, p, tb, lane);
+    for (int q = lane; q < nr; q += 32) {
+        int n, mm;
+        bool im;
+        decode_q(q, n, mm, im);
+        T acc = ar_from<T>(0.0);
+        for (int k = 0; k <= p - n; ++k)
+            acc = ar_add(acc, ar_mul(ar_mul(tb.z(zshift_offset(n + k, mm) + k), upow[k]),
+                                     wv.v[im ? him(n + k, mm) : hre(n + k, mm)]));
+        wv.t[q] = ar_mul(spow[n], acc);
+    }
+    __syncwarp();
+    { T* tq = wv.v; wv.v = wv.t; wv.t = tq; }
+    wswap(wv, p, tb, lane);
+    wrotz(wv, p, pwb, true, lane);   // Rz(theta)
+    wswap(wv, p, tb, lane);
+    wrotz(wv, p, pwa, true, lane);   // Rz(phi - pi/2)
+    T* dst = loc + (size_t)nr * C;
+    for (int q = lane; q < nr; q += 32) dst[q] = ar_add(dst[q], wv.v[q]);
 }
 
 __global__ void k_m2m_sum(TreeView t, int k0, int k1, int nr, const double* __restrict__ contrib,
@@ -205,7 +301,7 @@ __global__ void k_m2m_sum(TreeView t, int k0, int k1, int nr, const double* __re
 
 template <typename T>
 void launch_m2m(const TreeView& t, int child0, int child1, int p, const double* zc, const double* hs,
-                const double* mult, double* contrib, const M2MTables<T>& tb, cudaStream_t st) {
+                const double* mult, double* contrib, const RotTables<T>& tb, cudaStream_t st) {
     const size_t sh = (size_t)4 * m2m_warp_values(p) * sizeof(T);
     static bool attr = false;
     if (!attr) {
@@ -216,7 +312,31 @@ void launch_m2m(const TreeView& t, int child0, int child1, int p, const double* 
     (k_m2m_rot<T><<<nblk, 128, sh, st>>>(t, child0, child1, p, zc, hs, mult, contrib, tb), note_launch());
 }
 
+template <typename T>
+void launch_l2l(const TreeView& t, int k0, int k1, int p, const double* zc, const double* hs, T* loc,
+                const RotTables<T>& tb, cudaStream_t st) {
+    const size_t sh = (size_t)4 * m2m_warp_values(p) * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_l2l_rot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        attr = true;
+    }
+    const int nblk = (k1 - k0 + 3) / 4;
+    (k_l2l_rot<T><<<nblk, 128, sh, st>>>(t, k0, k1, p, zc, hs, loc, tb), note_launch());
+}
+
 }  // namespace
+
+void l2l_level(const TreeView& t, int k0, int k1, int p, const double* zc, const double* hs, void* loc,
+               const DevTables& tb, bool fp32, cudaStream_t st) {
+    if (k1 <= k0) return;
+    if (fp32)
+        launch_l2l<float>(t, k0, k1, p, zc, hs, static_cast<float*>(loc),
+                          RotTables<float>{tb.swap_cos_dw, tb.swap_sin_dw, tb.zshift_dw}, st);
+    else
+        launch_l2l<double>(t, k0, k1, p, zc, hs, static_cast<double*>(loc),
+                           RotTables<double>{tb.swap_cos, tb.swap_sin, tb.zshift}, st);
+}
 
 void m2m_level(const TreeView& t, int parent0, int parent1, int child0, int child1, int p,
                const double* zc, const double* hs, double* mult, double* contrib, const DevTables& tb,
@@ -225,12 +345,10 @@ void m2m_level(const TreeView& t, int parent0, int parent1, int child0, int chil
     const int nr = ncoef_real(p);
     if (dword)
         launch_m2m<dw>(t, child0, child1, p, zc, hs, mult, contrib,
-                       M2MTables<dw>{reinterpret_cast<const dw*>(tb.swap_cos_dw),
-                                     reinterpret_cast<const dw*>(tb.swap_sin_dw),
-                                     reinterpret_cast<const dw*>(tb.zshift_dw)}, st);
+                       RotTables<dw>{tb.swap_cos_dw, tb.swap_sin_dw, tb.zshift_dw}, st);
     else
         launch_m2m<double>(t, child0, child1, p, zc, hs, mult, contrib,
-                           M2MTables<double>{tb.swap_cos, tb.swap_sin, tb.zshift}, st);
+                           RotTables<double>{tb.swap_cos, tb.swap_sin, tb.zshift}, st);
     const int64_t work = (int64_t)(parent1 - parent0) * nr;
     (k_m2m_sum<<<(int)((work + 127) / 128), 128, 0, st>>>(t, parent0, parent1, nr, contrib, mult), note_launch());
 }
