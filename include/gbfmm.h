@@ -119,7 +119,9 @@ int fmm_solve_batch(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, con
 
 /* Plain FP64 O(N * ntargets) direct sum at the given target indices (a
  * device int64 array, or NULL for all n bodies): the exact quantity the FMM
- * approximates (Sec. 3.1.1), used to measure force errors. */
+ * approximates (Sec. 3.1.1), used to measure force errors. 1/r comes from an
+ * FP32 seed refined by two Newton steps, to FP64 rounding; a body exactly on
+ * top of the target contributes nothing. */
 int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
                const double* m, int64_t ntargets, const int64_t* targets, double* ax, double* ay,
                double* az, double* pot, void* cuda_stream);

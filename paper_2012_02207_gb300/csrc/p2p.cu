@@ -147,32 +147,56 @@ struct NearAcc {
     }
 };
 
+// 1/sqrt(x) in FP64 without the long FP64 divide and square root: an FP32
+// seed refined by two Newton steps y <- y (3 - x y^2) / 2 (each squares the
+// relative error: about 2^-22 -> 2^-44 -> the FP64 rounding level). Outside
+// the FP32 range of the seed (and for x = 0) it falls back to 1 / sqrt(x).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    if (!(x > 1e-30 && x < 1e30)) return x > 0.0 ? 1.0 / sqrt(x) : 0.0;
+    double y = (double)rsqrtf((float)x);
+    const double hx = 0.5 * x;
+    y = y * fma(-hx * y, y, 1.5);
+    y = y * fma(-hx * y, y, 1.5);
+    return y;
+}
+
 template <typename T, bool GUARD, int GC>
 __device__ __forceinline__ void p2p_pack_g(const Body4<T>* __restrict__ sm, int cnt, int sub, int Gr, T tx, T ty,
                                            T tz, NearAcc<T>& acc) {
     const int G = GC > 0 ? GC : Gr;  // lanes per target (compile-time when GC > 0)
-    for (int k0 = sub; k0 < cnt; k0 += kRun * G) {
+    auto term = [&](int k, T& px, T& py, T& pz, T& pp) {
+        const Body4<T> sv = sm[k];
+        const T dx = sv.x - tx, dy = sv.y - ty, dz = sv.z - tz;
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        T rinv;
+        if (sizeof(T) == 4) {
+            rinv = (T)rsqrtf((float)r2);
+            if (GUARD && !(r2 > T(0))) rinv = T(0);  // the body itself
+        } else {
+            rinv = (T)rsqrt_nr((double)r2);
+        }
+        const T mr = sv.w * rinv;
+        const T mr3 = mr * rinv * rinv;
+        px += mr3 * dx;
+        py += mr3 * dy;
+        pz += mr3 * dz;
+        pp += mr;
+    };
+    int k0 = sub;
+    if (GC > 0) {
+        // full runs of kRun terms, unrolled (constant shared-memory offsets, no loop control)
+        for (; k0 + kRun * GC <= cnt; k0 += kRun * GC) {
+            T px = T(0), py = T(0), pz = T(0), pp = T(0);
+#pragma unroll
+            for (int u = 0; u < kRun; ++u) term(k0 + u * GC, px, py, pz, pp);
+            acc.add(px, py, pz, pp);
+        }
+    }
+    for (; k0 < cnt; k0 += kRun * G) {
         const int k1 = k0 + kRun * G < cnt ? k0 + kRun * G : cnt;
         T px = T(0), py = T(0), pz = T(0), pp = T(0);
 #pragma unroll 4
-        for (int k = k0; k < k1; k += G) {
-            const Body4<T> sv = sm[k];
-            const T dx = sv.x - tx, dy = sv.y - ty, dz = sv.z - tz;
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            T rinv;
-            if (sizeof(T) == 4) {
-                rinv = (T)rsqrtf((float)r2);
-                if (GUARD && !(r2 > T(0))) rinv = T(0);  // the body itself
-            } else {
-                rinv = (r2 > T(0)) ? T(1) / (T)sqrt((double)r2) : T(0);
-            }
-            const T mr = sv.w * rinv;
-            const T mr3 = mr * rinv * rinv;
-            px += mr3 * dx;
-            py += mr3 * dy;
-            pz += mr3 * dz;
-            pp += mr;
-        }
+        for (int k = k0; k < k1; k += G) term(k, px, py, pz, pp);
         acc.add(px, py, pz, pp);
     }
 }
@@ -386,7 +410,8 @@ __global__ void k_leaf_relative(TreeView t, const double* __restrict__ xs, const
         prel[i] = make_float4((float)(xs[i] - cx), (float)(ys[i] - cy), (float)(zs[i] - cz), (float)ms[i]);
 }
 
-// Direct FP64 sum, one thread per target, source tiles staged in shared memory.
+// Direct FP64 sum, one thread per target, source tiles staged in shared memory
+// (1/r by the Newton-refined rsqrt above, to FP64 rounding).
 __global__ void __launch_bounds__(256) k_direct(int64_t n, const double* __restrict__ x,
                                                 const double* __restrict__ y,
                                                 const double* __restrict__ z,
@@ -409,9 +434,9 @@ __global__ void __launch_bounds__(256) k_direct(int64_t n, const double* __restr
             const double4 s = tile[k];
             const double dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
             const double r2 = dx * dx + dy * dy + dz * dz;
-            const double r = sqrt(r2);
-            const double mr = s.w / r;
-            const double mr3 = mr / r2;
+            const double rinv = rsqrt_nr(r2);
+            const double mr = s.w * rinv;
+            const double mr3 = mr * rinv * rinv;
             sx += mr3 * dx;
             sy += mr3 * dy;
             sz += mr3 * dz;
