@@ -409,8 +409,6 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     // ---- error-controlled walk
     if ((rc = run_walk(ctx, 1, st))) return rc;
     if ((rc = build_directed(ctx, 2, st)) || (rc = build_directed(ctx, 3, st))) return rc;
-    count_p2p_interactions(as<uint64_t>(ctx->dkeys[3]), ctx->ndirected[3], ctx->nb, nnodes, as<int>(ctx->begin),
-                           as<int>(ctx->end), as<unsigned long long>(ctx->dcount) + 1, st);
     CK(cudaEventRecord(ctx->ev[4], st));
     // ---- far field
     const uint64_t* mk = as<uint64_t>(ctx->dkeys[2]);
@@ -456,6 +454,7 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     la.ax = ax; la.ay = ay; la.az = az; la.pot = pot;
     la.part_hi = as<double2>(ctx->part_hi); la.part_lo = as<double2>(ctx->part_lo);
     la.tb = ctx->tb;
+    la.interactions = as<unsigned long long>(ctx->dcount) + 1;
     if (mixed) {
         leaf_relative_f32(t, la.xs, la.ys, la.zs, la.ms, la.zc, as<float4>(ctx->prel), st);
         la.prel = as<float4>(ctx->prel);

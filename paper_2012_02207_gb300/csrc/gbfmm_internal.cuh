@@ -262,6 +262,7 @@ struct LeafArgs {
     const uint32_t* perm;
     double *ax, *ay, *az, *pot;
     const void* loc;   // FP64 or FP32 locals
+    unsigned long long* interactions;  // directed body-body interactions (added by the P2P kernel)
     const float4* prel;  // leaf-relative FP32 bodies (mixed)
     double2 *part_hi, *part_lo;  // P2P partials: (ax, ay), (az, pot)
     DevTables tb;
@@ -271,8 +272,6 @@ void leaf_items_plan(const TreeView& t, const uint32_t* p2p_off, uint32_t* item_
 void leaf_items_fill(const TreeView& t, const uint32_t* item_first, int* item_leaf, int* leaf_of, cudaStream_t st);
 void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_t* item_first,
                const uint32_t* slot_first, int nitems, unsigned* work, const int* leaf_of, cudaStream_t st);
-void count_p2p_interactions(const uint64_t* keys, int64_t nk, int nb, int nnodes, const int* begin,
-                            const int* end, unsigned long long* out, cudaStream_t st);
 void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, const double* zs,
                        const double* ms, const double* zc, float4* prel, cudaStream_t st);
 void direct_sum_f64(int64_t n, const double* x, const double* y, const double* z, const double* m,

@@ -232,6 +232,8 @@ __global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __rest
         const int b0 = a.t.begin[B], nB = a.t.end[B] - b0;
         const uint32_t slot0 = slot_first[B] + (uint32_t)j * (uint32_t)nB;
         const float4 bh = a.zhi[B], bl = a.zlo[B];
+        unsigned long long nsrc = 0;  // source bodies of this item (for the interaction count)
+        bool self_item = false;
         for (int tc = 0; tc < nB; tc += 32) {
             const int nt = nB - tc < 32 ? nB - tc : 32;
             const int G = 32 / nt;            // lanes per target
@@ -282,6 +284,7 @@ __global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __rest
                         sm[cnt + l] = v;
                     }
                     selfin |= (A == B);
+                    if (tc == 0) { nsrc += (unsigned long long)take; self_item |= (A == B); }
                     cnt += take;
                     if (take < rem) { soff += take; break; }
                     soff = 0;
@@ -327,6 +330,9 @@ __global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __rest
                 }
             }
         }
+        // directed body-body interactions of the item (a body never acts on itself)
+        if (lane == 0)
+            atomicAdd(a.interactions, (unsigned long long)nB * nsrc - (self_item ? (unsigned long long)nB : 0ull));
     }
 }
 
@@ -452,30 +458,8 @@ __global__ void __launch_bounds__(256) k_direct(int64_t n, const double* __restr
     }
 }
 
-// directed body-body interactions of the P2P list (self pairs without i = j)
-__global__ void k_count_p2p(const uint64_t* __restrict__ keys, int64_t nk, int nb, int nnodes,
-                            const int* __restrict__ begin, const int* __restrict__ end,
-                            unsigned long long* out) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long c = 0;
-    if (q < nk && (keys[q] >> nb) < (uint64_t)nnodes) {
-        const int t = (int)(keys[q] >> nb), s = (int)(keys[q] & ((1ull << nb) - 1ull));
-        const unsigned long long nt = (unsigned long long)(end[t] - begin[t]);
-        const unsigned long long ns = (unsigned long long)(end[s] - begin[s]);
-        c = nt * ns - (t == s ? nt : 0ull);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
-}
-
 inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 }  // namespace
-
-void count_p2p_interactions(const uint64_t* keys, int64_t nk, int nb, int nnodes, const int* begin,
-                            const int* end, unsigned long long* out, cudaStream_t st) {
-    if (nk > 0) (k_count_p2p<<<blocks_for(nk, 256), 256, 0, st>>>(keys, nk, nb, nnodes, begin, end, out), note_launch());
-}
 
 void upload_leaf_tables(const HostTables& h) {
     float w[kMaxPF32 + 2][kMaxPF32 + 2], iw[kMaxPF32 + 2][kMaxPF32 + 2];

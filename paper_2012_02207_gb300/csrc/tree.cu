@@ -74,14 +74,21 @@ __global__ void k_bbox_partial(const double* __restrict__ x, const double* __res
 // e.g. one body). box[8c ..]: cx, cy, cz, h, lox, loy, loz, size.
 __global__ void k_bbox_final(const double* __restrict__ part, int nclusters, int slices,
                              double* __restrict__ box) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per cluster; min and max are exact, so the order does not matter
+    const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (c >= nclusters) return;
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = c * slices; b < (c + 1) * slices; ++b)
+    for (int b = c * slices + lane; b < (c + 1) * slices; b += 32)
         for (int d = 0; d < 3; ++d) {
             mn[d] = fmin(mn[d], part[6 * b + d]);
             mx[d] = fmax(mx[d], part[6 * b + 3 + d]);
         }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+        }
+    if (lane != 0) return;
     double* bx = box + 8 * c;
     double h = 0.0;
     for (int d = 0; d < 3; ++d) {
@@ -392,7 +399,7 @@ void tree_build_count(TreeBuffers& b, int* sorted_in_1, cudaStream_t st) {
     const int slices = nc >= kBboxBlocks ? 1 : (kBboxBlocks + nc - 1) / nc;
     (k_bbox_partial<<<nc * slices, 256, 0, st>>>(b.x, b.y, b.z, b.m, b.coff, slices, b.bbox_part, &b.ds->err),
      note_launch());
-    (k_bbox_final<<<blocks_for(nc, 128), 128, 0, st>>>(b.bbox_part, nc, slices, b.box), note_launch());
+    (k_bbox_final<<<blocks_for((int64_t)nc * 32, 128), 128, 0, st>>>(b.bbox_part, nc, slices, b.box), note_launch());
     (k_keys<<<blocks_for(n, 256), 256, 0, st>>>(b.x, b.y, b.z, n, b.coff, nc, b.box, b.k0, b.v0), note_launch());
     int in1 = radix_sort(b.k0, b.v0, b.k1, b.v1, n, 63, b.hist, st);
     const uint64_t* keys = in1 ? b.k1 : b.k0;

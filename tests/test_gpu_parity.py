@@ -72,6 +72,12 @@ def test_tree_geometry_estimate_and_lists_bit_exact(n, leaf, precision):
     assert np.all(np.abs(gg["P"] - og["P"]) <= (1e-12 if precision == "fp64" else 1e-11) * scale)
     for which in ("far", "near", "m2l", "p2p"):
         assert np.array_equal(sorted_pairs(f.export_pairs(which)), sorted_pairs(run.pairs(which))), which
+    # directed body-body interactions of the oracle's P2P list (a body never acts on itself)
+    size = ot["end"] - ot["begin"]
+    pp = sorted_pairs(run.pairs("p2p"))
+    na, nb_ = size[pp[:, 0]].astype(np.int64), size[pp[:, 1]].astype(np.int64)
+    expect = int(np.where(pp[:, 0] == pp[:, 1], na * (na - 1), 2 * na * nb_).sum())
+    assert f.stats()["p2p_interactions"] == expect
 
 
 @pytest.mark.parametrize("n,p,eps", [(4096, 8, 1e-7), (20000, 6, 1e-6), (20000, 10, 1e-8), (3000, 14, 1e-5), (3000, 16, 1e-8), (2000, 20, 1e-9), (1500, 30, 1e-10)])
