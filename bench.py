@@ -176,6 +176,19 @@ def cpu_sample(p, eps):
     return SAMPLE_N / dt, dt, oracle.num_threads()
 
 
+def replica_throughput(ms_local, n, world, dist=None, device=None):
+    """Whole-job throughput of N independent replicas (one per rank): every
+    rank solved n bodies; the job takes as long as the slowest rank.
+    Returns (particles/s over all ranks, the max ms over ranks)."""
+    ms = ms_local
+    if dist is not None:
+        import torch  # noqa: PLC0415
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return n * world / (ms * 1e-3), ms
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -274,12 +287,7 @@ def main():
         times, stats = timed_solves(mixed, args.steps, args.warmup)
         wall = time.perf_counter() - wall0
     clocks = clk.summary()
-    ms = sum(times) / len(times)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * world / (ms * 1e-3)
+    value, ms = replica_throughput(sum(times) / len(times), n, world, dist, dev)
 
     # accuracy of this exact run over ALL bodies against the FP64 direct sum on
     # the GPU (O(N^2), about half a minute at N = 2^20; untimed). The RMS is
