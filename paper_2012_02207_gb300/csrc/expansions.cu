@@ -204,8 +204,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
                                                  const double* __restrict__ hs,
                                                  double* __restrict__ mult) {
     __shared__ dw sh_tile[WARPS][2 * (PM + 1)][33];
+    // lane-private sums: entry e of column m at sh_acc[warp][m][e] (e = lane, lane + 32)
+    __shared__ dw sh_acc[WARPS][PM + 1][64];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     dw (*tile)[33] = sh_tile[wib];
+    dw (*acc)[64] = sh_acc[wib];
     const int nr = ncoef_real(p);
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     const dw zero = dw_make(0.f, 0.f);
@@ -213,9 +216,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
         if (t.nchild[k] != 0) continue;
         const double is = 1.0 / hs[k];
         const double cx = zc[3 * k], cy = zc[3 * k + 1], cz = zc[3 * k + 2];
-        dw acc[PM + 1][2];
-#pragma unroll
-        for (int m = 0; m <= PM; ++m) { acc[m][0] = zero; acc[m][1] = zero; }
+        for (int m = 0; m <= p; ++m) { acc[m][lane] = zero; acc[m][lane + 32] = zero; }
         for (int i0 = t.begin[k]; i0 < t.end[k]; i0 += 32) {
             const int i = i0 + lane;
             const bool act = i < t.end[k];
@@ -224,59 +225,49 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
                      z = act ? dw_from((zs[i] - cz) * is) : zero, w = act ? dw_from(ms[i]) : zero;
             const dw r2 = dw_add(dw_add(dw_mul(x, x), dw_mul(y, y)), dw_mul(z, z));
             dw dre = w, dim = zero;  // w * Shat_m^m
-#pragma unroll
-            for (int m = 0; m <= PM; ++m) {
-                if (m <= p) {
-                    if (m > 0) {
-                        const dw tq = dw_sub(dw_mul(dre, x), dw_mul(dim, y));
-                        dim = dw_mul(dw_add(dw_mul(dre, y), dw_mul(dim, x)), c_dw_d[m]);
-                        dre = dw_mul(tq, c_dw_d[m]);
-                    }
-                    dw s1r = dre, s1i = dim, s2r = zero, s2i = zero;
-                    tile[0][lane] = dre;
-                    tile[1][lane] = dim;
-                    for (int n = m + 1; n <= p; ++n) {
-                        dw vr, vi;
-                        if (n == m + 1) {
-                            const dw sz = dw_mul(c_dw_s[m], z);
-                            vr = dw_mul(sz, s1r);
-                            vi = dw_mul(sz, s1i);
-                        } else {
-                            const dw a = dw_mul(c_dw_a[n][m], z), b = dw_mul(c_dw_b[n][m], r2);
-                            vr = dw_sub(dw_mul(a, s1r), dw_mul(b, s2r));
-                            vi = dw_sub(dw_mul(a, s1i), dw_mul(b, s2i));
-                        }
-                        tile[2 * (n - m)][lane] = vr;
-                        tile[2 * (n - m) + 1][lane] = vi;
-                        s2r = s1r; s2i = s1i; s1r = vr; s1i = vi;
-                    }
-                    __syncwarp();
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int ent = lane + 32 * h;
-                        if (ent < 2 * (p - m + 1)) {
-                            dw sacc = acc[m][h];
-                            for (int l = 0; l < nact; ++l) sacc = dw_add(sacc, tile[ent][l]);
-                            acc[m][h] = sacc;
-                        }
-                    }
-                    __syncwarp();
+            // one code path for every column m (a rolled loop keeps the code small)
+#pragma unroll 1
+            for (int m = 0; m <= p; ++m) {
+                if (m > 0) {
+                    const dw tq = dw_sub(dw_mul(dre, x), dw_mul(dim, y));
+                    dim = dw_mul(dw_add(dw_mul(dre, y), dw_mul(dim, x)), c_dw_d[m]);
+                    dre = dw_mul(tq, c_dw_d[m]);
                 }
+                dw s1r = dre, s1i = dim, s2r = zero, s2i = zero;
+                tile[0][lane] = dre;
+                tile[1][lane] = dim;
+                for (int n = m + 1; n <= p; ++n) {
+                    dw vr, vi;
+                    if (n == m + 1) {
+                        const dw sz = dw_mul(c_dw_s[m], z);
+                        vr = dw_mul(sz, s1r);
+                        vi = dw_mul(sz, s1i);
+                    } else {
+                        const dw a = dw_mul(c_dw_a[n][m], z), b = dw_mul(c_dw_b[n][m], r2);
+                        vr = dw_sub(dw_mul(a, s1r), dw_mul(b, s2r));
+                        vi = dw_sub(dw_mul(a, s1i), dw_mul(b, s2i));
+                    }
+                    tile[2 * (n - m)][lane] = vr;
+                    tile[2 * (n - m) + 1][lane] = vi;
+                    s2r = s1r; s2i = s1i; s1r = vr; s1i = vi;
+                }
+                __syncwarp();
+                for (int ent = lane; ent < 2 * (p - m + 1); ent += 32) {
+                    dw sacc = acc[m][ent];
+                    for (int l = 0; l < nact; ++l) sacc = dw_add(sacc, tile[ent][l]);
+                    acc[m][ent] = sacc;
+                }
+                __syncwarp();
             }
         }
         double* out = mult + (size_t)nr * k;
-#pragma unroll
-        for (int m = 0; m <= PM; ++m) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int ent = lane + 32 * h;
-                if (m <= p && ent < 2 * (p - m + 1)) {
-                    const int n = m + (ent >> 1);
-                    if (ent & 1) { if (m) out[him(n, m)] = dw_to(acc[m][h]); }
-                    else out[hre(n, m)] = dw_to(acc[m][h]);
-                }
+        for (int m = 0; m <= p; ++m)
+            for (int ent = lane; ent < 2 * (p - m + 1); ent += 32) {
+                const int n = m + (ent >> 1);
+                if (ent & 1) { if (m) out[him(n, m)] = dw_to(acc[m][ent]); }
+                else out[hre(n, m)] = dw_to(acc[m][ent]);
             }
-        }
+        __syncwarp();
     }
 }
 
