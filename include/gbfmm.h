@@ -77,6 +77,8 @@ typedef struct {
     double ms_tree, ms_upward, ms_estimate, ms_walk, ms_m2l, ms_downward, ms_leaf, ms_total;
     int32_t walk_iters, regrows;
     int64_t kernel_launches;  /* kernels the library launched in the last solve */
+    int32_t graph_replays;    /* 1 if the last fmm_solve_graph call replayed its captured graph */
+    int32_t reserved;
 } fmm_stats;
 
 typedef struct fmm_ctx fmm_ctx;
@@ -114,6 +116,31 @@ int fmm_solve_host(fmm_ctx* ctx, int64_t n, const double* x, const double* y, co
  * separate run; the single pass over all of them is this library's addition. Errors: FMM_ERR_ARG for bad offsets or NULL pointers,
  * otherwise as fmm_solve (a coincidence is only checked inside a cluster). */
 int fmm_solve_batch(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, const double* x,
+                    const double* y, const double* z, const double* m, double* ax, double* ay,
+                    double* az, double* pot, void* cuda_stream);
+
+/* The solve of fmm_solve (offsets == NULL) or fmm_solve_batch (nclusters
+ * clusters, HOST offsets as there) replayed from a captured CUDA graph. The
+ * first call for a set of arguments is an ordinary solve (its result is
+ * returned), which also plans capacities from the sizes it met (nodes, nodes
+ * per level and levels, walk steps, list lengths, P2P work items, each with
+ * headroom) and captures the whole solve, with no read-back, into one CUDA
+ * graph on an internal stream. Later calls with the same n, offsets and
+ * pointers replay the graph: one launch, then one read of a status block.
+ * If the bodies moved enough that a planned capacity is exceeded (or the
+ * tree got deeper), that call falls back to an ordinary solve and the next
+ * call plans and captures again; the result is always that of fmm_solve.
+ * Any reallocation of the context's workspace (another solve of a larger
+ * problem on the same context) also forces a new capture.
+ * cuda_stream is synchronised before the solve; the call returns with the
+ * outputs complete. The paper has no counterpart (it is a CPU code); this is
+ * the GPU way to remove per-phase launch and read-back costs from repeated
+ * solves of the same bodies (time steps) or ensembles. Statistics after a
+ * replay carry the counts from the status block and graph_replays = 1;
+ * the per-phase times come from event nodes inside the graph and ms_total
+ * is the whole replay. Exports after a
+ * replay are not supported. Errors as fmm_solve and fmm_solve_batch. */
+int fmm_solve_graph(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, int64_t n, const double* x,
                     const double* y, const double* z, const double* m, double* ax, double* ay,
                     double* az, double* pot, void* cuda_stream);
 

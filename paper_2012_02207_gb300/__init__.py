@@ -45,7 +45,8 @@ class Stats(ctypes.Structure):
                 ("ms_tree", ctypes.c_double), ("ms_upward", ctypes.c_double), ("ms_estimate", ctypes.c_double),
                 ("ms_walk", ctypes.c_double), ("ms_m2l", ctypes.c_double), ("ms_downward", ctypes.c_double),
                 ("ms_leaf", ctypes.c_double), ("ms_total", ctypes.c_double), ("walk_iters", ctypes.c_int32),
-                ("regrows", ctypes.c_int32), ("kernel_launches", ctypes.c_int64)]
+                ("regrows", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,6 +72,7 @@ def lib():
             L.fmm_solve.argtypes = [vp, i64] + [dp] * 8 + [vp]
             L.fmm_solve_host.argtypes = [vp, i64] + [dp] * 8 + [vp]
             L.fmm_solve_batch.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)] + [dp] * 8 + [vp]
+            L.fmm_solve_graph.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), i64] + [dp] * 8 + [vp]
             L.fmm_direct.argtypes = [vp, i64, dp, dp, dp, dp, i64, dp, dp, dp, dp, dp, vp]
             L.fmm_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
             L.fmm_export_tree.argtypes = [vp] + [dp] * 8
@@ -184,6 +186,28 @@ class FMM:
         self._check(lib().fmm_solve_batch(self._h, len(offs) - 1, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                           _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(ax), _ptr(ay), _ptr(az),
                                           _ptr(pot), _stream_handle(stream)))
+        return ax, ay, az, pot
+
+    def solve_graph(self, x, y, z, m, out=None, offsets=None, stream=None):
+        """solve() (or solve_batch() with offsets) replayed from a captured CUDA
+        graph: the first call with given tensors solves, plans and captures;
+        later calls with the same tensors replay the graph (see fmm_solve_graph).
+        The output tensors must be passed in (out) to be reused between calls."""
+        import torch  # noqa: PLC0415
+        n = x.numel()
+        for t in (x, y, z, m):
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("x, y, z, m must be contiguous CUDA float64 tensors of equal length")
+        if out is None:
+            out = tuple(torch.empty(n, dtype=torch.float64, device=x.device) for _ in range(4))
+        ax, ay, az, pot = out
+        if offsets is None:
+            optr, ncl = None, 1
+        else:
+            offs = np.ascontiguousarray(offsets, dtype=np.int64)
+            optr, ncl = offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(offs) - 1
+        self._check(lib().fmm_solve_graph(self._h, ncl, optr, n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(ax),
+                                          _ptr(ay), _ptr(az), _ptr(pot), _stream_handle(stream)))
         return ax, ay, az, pot
 
     def direct(self, x, y, z, m, targets=None, stream=None):

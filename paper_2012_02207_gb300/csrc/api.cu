@@ -49,6 +49,26 @@ namespace gbfmm {
 void set_global_error(const char* msg) { g_create_error = msg; }
 }  // namespace gbfmm
 
+// A captured solve (fmm_solve_graph): the capacities it was captured for,
+// taken from an ordinary solve of the same problem with headroom, and the
+// arguments its launches are bound to.
+struct GraphPlan {
+    bool valid = false;
+    int64_t n = 0;
+    std::vector<int64_t> offs;
+    const void* ptrs[8] = {};
+    cudaStream_t st = nullptr;
+    int64_t gen = -1;                     // buffer generation it was captured with
+    int node_cap = 0, nlevels = 0, nroots = 0, nb = 1;
+    int lvl_cap[kMaxLevel + 2] = {};
+    int walk_iters[2] = {0, 0};
+    int64_t pair_cap[4] = {0, 0, 0, 0};
+    uint32_t items_cap = 0, slots_cap = 0;
+    int* h_coff = nullptr;                // pinned copy of the cluster offsets (a memcpy node)
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+};
+
 struct fmm_ctx {
     fmm_config cfg{};
     int device = 0;
@@ -71,7 +91,9 @@ struct fmm_ctx {
     // P2P work items
     Buf item_first, slot_first, item_leaf, leaf_of, part_hi, part_lo, work;
     // walk and lists
-    Buf front0, front1, lists[4], dkeys[4], dalt, doff[4], dcount;
+    // per list: sorted directed keys, the sort's second buffer (its own, so a
+    // buffer never moves to a list of another size), CSR offsets
+    Buf front0, front1, lists[4], dkeys[4], dalt[4], doff[4], dcount;
     int64_t front_cap = 0, list_cap[4] = {0, 0, 0, 0};
     // host staging for fmm_solve_host
     Buf hin[4], hout[4];
@@ -81,7 +103,22 @@ struct fmm_ctx {
     int h_level_start[kMaxLevel + 3] = {};
     int64_t npairs[4] = {0, 0, 0, 0}, ndirected[4] = {0, 0, 0, 0};
     int dk_in_alt[4] = {0, 0, 0, 0};
+    // workspace generation: bumped by every reallocation (a captured graph
+    // holds the old addresses and must be captured again)
+    int64_t gen = 0;
+    GraphPlan plan;
+    const GraphPlan* gmode = nullptr;     // set while the solve runs in graph form
+    cudaStream_t gstream = nullptr;       // stream of the captured solve (capture needs a non-default one)
+    int walk_steps[2] = {0, 0};           // steps of the last ordinary solve's walks
+    uint32_t items_total[2] = {0, 0};     // and its P2P work items and partial slots
+    cudaEvent_t gev[2] = {nullptr, nullptr};
 };
+
+void drop_plan(GraphPlan& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.h_coff) cudaFreeHost(g.h_coff);
+    g = GraphPlan{};
+}
 
 namespace {
 
@@ -99,6 +136,7 @@ int fail(fmm_ctx* c, int code, const std::string& msg) {
 
 int ensure(fmm_ctx* ctx, Buf& b, size_t bytes) {
     if (b.bytes >= bytes) return FMM_OK;
+    ctx->gen++;
     if (b.ptr) cudaFree(b.ptr);
     b.ptr = nullptr;
     b.bytes = 0;
@@ -169,6 +207,15 @@ TreeView view(fmm_ctx* ctx) {
     t.first_child = as<int>(ctx->first_child);
     t.nchild = as<int>(ctx->nchild);
     t.nroots = ctx->nnodes > 0 ? ctx->h_level_start[1] : 0;
+    for (int L = 0; L <= kMaxLevel; ++L)
+        t.lvl_cnt[L] = ctx->nnodes > 0 ? ctx->h_level_start[L + 1] - ctx->h_level_start[L] : 0;
+    t.lvl_cnt[kMaxLevel + 1] = 0;
+    if (const GraphPlan* g = ctx->gmode) {  // grids sized by the planned capacities
+        t.nroots = g->nroots;
+        for (int L = 0; L <= kMaxLevel + 1; ++L) t.lvl_cnt[L] = g->lvl_cap[L];
+    }
+    t.dnn = &ctx->ds->nnodes;
+    t.dls = ctx->ds->level_start;
     return t;
 }
 
@@ -180,33 +227,36 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 // directed, sorted, CSR-indexed form of pair list `which`: every unordered
 // pair (A, B) gives the keys B<<nb|A and A<<nb|B; a self pair gives one key
-// and an all-ones marker that sorts last and is ignored.
+// and an all-ones marker that sorts last and is ignored. The key count lives on
+// the device (dcount[8 + which]): a captured solve sizes the grids for its
+// planned capacity but sorts only the keys present.
 int build_directed(fmm_ctx* ctx, int which, cudaStream_t st) {
     const int64_t np = ctx->npairs[which];
     const size_t keys_bytes = sizeof(uint64_t) * (size_t)(2 * np + 1);
     int rc;
     if ((rc = ensure(ctx, ctx->dkeys[which], keys_bytes)) != FMM_OK) return rc;
-    if ((rc = ensure(ctx, ctx->dalt, keys_bytes)) != FMM_OK) return rc;
+    if ((rc = ensure(ctx, ctx->dalt[which], keys_bytes)) != FMM_OK) return rc;
     if ((rc = ensure(ctx, ctx->doff[which], sizeof(uint32_t) * (size_t)(ctx->nnodes + 2))) != FMM_OK) return rc;
     if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(2 * np + 1))) != FMM_OK) return rc;
     ctx->ndirected[which] = 2 * np;
+    unsigned long long* nkeys = as<unsigned long long>(ctx->dcount) + 8 + which;
     if (2 * ctx->nb <= 32) {
         // 32-bit keys: half the bytes per radix pass; both ping-pong halves fit in dalt
-        uint32_t* ka = as<uint32_t>(ctx->dalt);
+        uint32_t* ka = as<uint32_t>(ctx->dalt[which]);
         uint32_t* kb = ka + (2 * np + 1);
-        pairs_to_directed32(as<int2>(ctx->lists[which]), np, ctx->nb, ka,
-                            as<unsigned long long>(ctx->dcount) + 2 + which, st);
-        const int in1 = radix_sort32(ka, kb, 2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st);
-        directed_offsets_widen(in1 ? kb : ka, 2 * np, ctx->nb, ctx->nnodes, as<uint64_t>(ctx->dkeys[which]),
-                               as<uint32_t>(ctx->doff[which]), st);
+        pairs_to_directed32(as<int2>(ctx->lists[which]), ctx->ds->list_cnt + which, np, ctx->nb, ka,
+                            as<unsigned long long>(ctx->dcount) + 2 + which, nkeys, st);
+        const int in1 = radix_sort32(ka, kb, 2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st, nkeys);
+        directed_offsets_widen(in1 ? kb : ka, 2 * np, nkeys, ctx->nb, &ctx->ds->nnodes,
+                               as<uint64_t>(ctx->dkeys[which]), as<uint32_t>(ctx->doff[which]), st);
         return FMM_OK;
     }
-    pairs_to_directed(as<int2>(ctx->lists[which]), np, ctx->nb, as<uint64_t>(ctx->dkeys[which]),
-                      as<unsigned long long>(ctx->dcount) + 2 + which, st);
-    const int in1 = radix_sort(as<uint64_t>(ctx->dkeys[which]), nullptr, as<uint64_t>(ctx->dalt), nullptr,
-                               2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st);
-    if (in1) std::swap(ctx->dkeys[which], ctx->dalt);
-    directed_offsets(as<uint64_t>(ctx->dkeys[which]), 2 * np, ctx->nb, ctx->nnodes,
+    pairs_to_directed(as<int2>(ctx->lists[which]), ctx->ds->list_cnt + which, np, ctx->nb,
+                      as<uint64_t>(ctx->dkeys[which]), as<unsigned long long>(ctx->dcount) + 2 + which, nkeys, st);
+    const int in1 = radix_sort(as<uint64_t>(ctx->dkeys[which]), nullptr, as<uint64_t>(ctx->dalt[which]), nullptr,
+                               2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st, nkeys);
+    if (in1) std::swap(ctx->dkeys[which], ctx->dalt[which]);
+    directed_offsets(as<uint64_t>(ctx->dkeys[which]), 2 * np, nkeys, ctx->nb, &ctx->ds->nnodes,
                      as<uint32_t>(ctx->doff[which]), st);
     return FMM_OK;
 }
@@ -214,6 +264,34 @@ int build_directed(fmm_ctx* ctx, int which, cudaStream_t st) {
 int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
     TreeView t = view(ctx);
     const int p = ctx->cfg.p;
+    const double* binom_row0 = ctx->tb.sub + (kMaxP + 1);
+    if (const GraphPlan* g = ctx->gmode) {
+        // graph form: planned capacities and steps, no read-back; overflows and
+        // an unfinished walk raise kErrCapacity for the check after the replay
+        int rc;
+        if ((rc = ensure(ctx, ctx->front0, sizeof(int2) * (size_t)ctx->front_cap)) != FMM_OK) return rc;
+        if ((rc = ensure(ctx, ctx->front1, sizeof(int2) * (size_t)ctx->front_cap)) != FMM_OK) return rc;
+        WalkBuffers wb;
+        wb.front0 = as<int2>(ctx->front0);
+        wb.front1 = as<int2>(ctx->front1);
+        wb.front_cap = ctx->front_cap;
+        for (int l = 0; l < 4; ++l) {
+            wb.out[l] = as<int2>(ctx->lists[l]);
+            wb.out_cap[l] = g->pair_cap[l];
+        }
+        for (int l = 2 * mode; l < 2 * mode + 2; ++l) {
+            if ((rc = ensure(ctx, ctx->lists[l], sizeof(int2) * (size_t)g->pair_cap[l])) != FMM_OK) return rc;
+            wb.out[l] = as<int2>(ctx->lists[l]);
+            ctx->npairs[l] = g->pair_cap[l];
+        }
+        dual_tree_walk(mode, t, as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->Pk),
+                       as<float>(ctx->fmin), p, ctx->cfg.eps, binom_row0, as<float4>(ctx->zhi),
+                       as<float4>(ctx->zlo), as<float>(ctx->r32), as<float>(ctx->Phat), wb,
+                       ctx->ds, ctx->h_ds, g->walk_iters[mode], st);
+        walk_check_finished(ctx->ds, g->walk_iters[mode], st);
+        CK(cudaGetLastError());
+        return FMM_OK;
+    }
     for (int attempt = 0; attempt < 12; ++attempt) {
         int rc;
         if ((rc = ensure(ctx, ctx->front0, sizeof(int2) * (size_t)ctx->front_cap)) != FMM_OK) return rc;
@@ -234,7 +312,7 @@ int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
         const int it = dual_tree_walk(mode, t, as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->Pk),
                                       as<float>(ctx->fmin), p, ctx->cfg.eps, binom_row, as<float4>(ctx->zhi),
                                       as<float4>(ctx->zlo), as<float>(ctx->r32), as<float>(ctx->Phat), wb,
-                                      ctx->ds, ctx->h_ds, st);
+                                      ctx->ds, ctx->h_ds, 0, st);
         if (it == FMM_ERR_CAPACITY) {
             // the counters kept counting past the capacity: grow to what was asked for
             CK(cudaMemcpyAsync(ctx->h_ds, ctx->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
@@ -252,6 +330,7 @@ int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
             return fail(ctx, it, std::string("dual-tree walk failed: ") + cudaGetErrorString(cudaGetLastError()));
         if (it < 0) return fail(ctx, it, "dual-tree walk failed");
         ctx->stats.walk_iters += it;
+        ctx->walk_steps[mode] = it;
         unsigned long long cnt[4];
         CK(cudaMemcpyAsync(cnt, ctx->ds->list_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -278,6 +357,13 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
                  double* pot, cudaStream_t st) {
     const int p = ctx->cfg.p;
     const bool mixed = ctx->cfg.precision == FMM_PRECISION_MIXED;
+    const GraphPlan* gp = ctx->gmode;  // non-null: the graph form (planned sizes, no read-back)
+    // phase events; while capturing they become event-record nodes (the external
+    // flag is only accepted then), so a replay times its phases too
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (gp) CK(cudaStreamIsCapturing(st, &cap));
+    const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    auto rec = [&](int i) { return cudaEventRecordWithFlags(ctx->ev[i], st, ev_flags); };
     std::memset(&ctx->stats, 0, sizeof(ctx->stats));
     g_launches = 0;
     ctx->stats.n = n;
@@ -308,9 +394,10 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
          (rc = ensure(ctx, ctx->cv0, 4 * N)) || (rc = ensure(ctx, ctx->cv1, 4 * N)) ||
          (rc = ensure(ctx, ctx->cid, 4 * N))))
         return rc;
-    CK(cudaEventRecord(ctx->ev[0], st));
+    CK(rec(0));
     CK(cudaMemsetAsync(&ctx->ds->err, 0, sizeof(unsigned), st));
-    CK(cudaMemcpyAsync(ctx->coff.ptr, ctx->h_coff.data(), 4 * ((size_t)nclusters + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->coff.ptr, gp ? gp->h_coff : ctx->h_coff.data(), 4 * ((size_t)nclusters + 1),
+                       cudaMemcpyHostToDevice, st));
     TreeBuffers tb{};
     tb.x = x; tb.y = y; tb.z = z; tb.m = m; tb.n = n; tb.leaf_size = ctx->cfg.leaf_size;
     tb.nclusters = nclusters; tb.coff = as<int>(ctx->coff); tb.box = as<double>(ctx->box);
@@ -330,13 +417,17 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     ctx->sorted_in_1 = in1;
     uint32_t total = 0;
     unsigned err = 0;
-    CK(cudaMemcpyAsync(&total, as<uint32_t>(ctx->chunk) + (size_t)(kMaxLevel + 1) * nchunks, 4,
-                       cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&err, &ctx->ds->err, 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (err & kErrNonfinite) return fail(ctx, FMM_ERR_NONFINITE, "non-finite position or mass, or a mass <= 0");
-    if (err & kErrCoincident) return fail(ctx, FMM_ERR_COINCIDENT, "two bodies share the same position");
-    const int nnodes = (int)total;
+    if (gp) {
+        total = (uint32_t)gp->node_cap;
+    } else {
+        CK(cudaMemcpyAsync(&total, as<uint32_t>(ctx->chunk) + (size_t)(kMaxLevel + 1) * nchunks, 4,
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&err, &ctx->ds->err, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (err & kErrNonfinite) return fail(ctx, FMM_ERR_NONFINITE, "non-finite position or mass, or a mass <= 0");
+        if (err & kErrCoincident) return fail(ctx, FMM_ERR_COINCIDENT, "two bodies share the same position");
+    }
+    const int nnodes = (int)total;  // the node arrays' size (the planned capacity in graph form)
     ctx->nnodes = nnodes;
     const size_t K = (size_t)nnodes;
     const size_t nr = (size_t)ncoef_real(p);
@@ -364,29 +455,34 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     tb.parent = as<int>(ctx->parent); tb.first_child = as<int>(ctx->first_child);
     tb.nchild = as<int>(ctx->nchild); tb.node_cap = nnodes;
     tree_build_emit(tb, st);
-    CK(cudaMemcpyAsync(ctx->h_ds, ctx->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    std::memcpy(ctx->h_level_start, ctx->h_ds->level_start, sizeof(ctx->h_level_start));
     int nl = 1;
-    for (int L = 1; L <= kMaxLevel; ++L)
-        if (ctx->h_level_start[L] < nnodes) nl = L + 1;
+    if (gp) {
+        nl = gp->nlevels;
+        ctx->nb = gp->nb;
+    } else {
+        CK(cudaMemcpyAsync(ctx->h_ds, ctx->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::memcpy(ctx->h_level_start, ctx->h_ds->level_start, sizeof(ctx->h_level_start));
+        for (int L = 1; L <= kMaxLevel; ++L)
+            if (ctx->h_level_start[L] < nnodes) nl = L + 1;
+        ctx->nb = bit_length(nnodes);
+    }
     ctx->nlevels = nl;
-    ctx->nb = bit_length(nnodes);
     TreeView t = view(ctx);
     const uint64_t* keys = as<uint64_t>(in1 ? ctx->k1 : ctx->k0);
     tree_build_phase2(tb, keys, nnodes, ctx->h_level_start, nl, st);
     cell_geometry(t, as<double>(ctx->xs), as<double>(ctx->ys), as<double>(ctx->zs), as<double>(ctx->ms),
                   ctx->h_level_start, as<double>(ctx->M), as<double>(ctx->S), as<double>(ctx->zc),
                   as<double>(ctx->r), st);
-    hat_scales(nnodes, as<int>(ctx->parent), as<double>(ctx->r), as<double>(ctx->hs), st);
-    node_centres_f32(nnodes, as<double>(ctx->zc), as<double>(ctx->hs), as<float4>(ctx->zhi), as<float4>(ctx->zlo), st);
-    CK(cudaEventRecord(ctx->ev[1], st));
+    hat_scales(t, as<int>(ctx->parent), as<double>(ctx->r), as<double>(ctx->hs), st);
+    node_centres_f32(t, as<double>(ctx->zc), as<double>(ctx->hs), as<float4>(ctx->zhi), as<float4>(ctx->zlo), st);
+    CK(rec(1));
     // ---- upward pass
     upward_pass(t, ctx->h_level_start, p, as<double>(ctx->xs), as<double>(ctx->ys), as<double>(ctx->zs),
                 as<double>(ctx->ms), as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->hs),
                 as<double>(ctx->mult), as<double>(ctx->Pk), as<float>(ctx->Phat), as<float>(ctx->r32), as<double>(ctx->contrib), ctx->tb,
                 mixed, st);
-    CK(cudaEventRecord(ctx->ev[2], st));
+    CK(rec(2));
     // ---- scalar-force estimate
     if (ctx->front_cap == 0) {
         const int64_t base = 64 * (int64_t)nnodes + 4096;
@@ -398,52 +494,60 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
             for (int l = 0; l < 4; ++l) ctx->list_cap[l] = 16;
         }
     }
-    if ((rc = ensure(ctx, ctx->dcount, 64))) return rc;
-    CK(cudaMemsetAsync(ctx->dcount.ptr, 0, 64, st));
+    if ((rc = ensure(ctx, ctx->dcount, 128))) return rc;  // [1] P2P interactions, [2..5] self pairs, [8..11] keys
+    CK(cudaMemsetAsync(ctx->dcount.ptr, 0, 128, st));
     if ((rc = run_walk(ctx, 0, st))) return rc;
     if ((rc = build_directed(ctx, 0, st)) || (rc = build_directed(ctx, 1, st))) return rc;
     scalar_force(t, as<double>(ctx->zc), as<double>(ctx->M), as<float4>(ctx->xf), as<uint64_t>(ctx->dkeys[0]),
                  as<uint32_t>(ctx->doff[0]), as<uint64_t>(ctx->dkeys[1]), as<uint32_t>(ctx->doff[1]), ctx->nb,
                  ctx->h_level_start, as<float>(ctx->fscratch), as<float>(ctx->f), as<float>(ctx->fmin), st);
-    CK(cudaEventRecord(ctx->ev[3], st));
+    CK(rec(3));
     // ---- error-controlled walk
     if ((rc = run_walk(ctx, 1, st))) return rc;
     if ((rc = build_directed(ctx, 2, st)) || (rc = build_directed(ctx, 3, st))) return rc;
-    CK(cudaEventRecord(ctx->ev[4], st));
+    CK(rec(4));
     // ---- far field
     const uint64_t* mk = as<uint64_t>(ctx->dkeys[2]);
     const uint32_t* mo = as<uint32_t>(ctx->doff[2]);
     if (mixed && m2l32_supported(p)) {
-        multipoles_to_f32_padded(as<double>(ctx->mult), as<float>(ctx->mult32), nnodes, (int)nr,
+        multipoles_to_f32_padded(as<double>(ctx->mult), as<float>(ctx->mult32), t, (int)nr,
                                  (int)((nr + 3) & ~(size_t)3), st);
-        m2l_f32(nnodes, p, mk, mo, ctx->nb, as<float>(ctx->mult32), as<float4>(ctx->zhi), as<float4>(ctx->zlo),
+        m2l_f32(t.dnn, p, mk, mo, ctx->nb, as<float>(ctx->mult32), as<float4>(ctx->zhi), as<float4>(ctx->zlo),
                 as<float>(ctx->loc32), &ctx->ds->queue, st);
     } else {
-        m2l_f64(nnodes, p, mk, mo, ctx->nb, as<double>(ctx->mult), as<double>(ctx->zc), as<double>(ctx->hs),
+        m2l_f64(t.dnn, p, mk, mo, ctx->nb, as<double>(ctx->mult), as<double>(ctx->zc), as<double>(ctx->hs),
                 as<double>(ctx->loc), ctx->tb, &ctx->ds->queue, st);
-        if (mixed) multipoles_to_f32(as<double>(ctx->loc), as<float>(ctx->loc32), (int64_t)(K * nr), st);
+        if (mixed) multipoles_to_f32(as<double>(ctx->loc), as<float>(ctx->loc32), t, (int)nr, st);
     }
-    CK(cudaEventRecord(ctx->ev[5], st));
+    CK(rec(5));
     if (mixed)
         downward_pass_f32(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->hs), as<float>(ctx->loc32),
                           ctx->tb, st);
     else
         downward_pass_f64(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->hs), as<double>(ctx->loc),
                           ctx->tb, st);
-    CK(cudaEventRecord(ctx->ev[6], st));
+    CK(rec(6));
     // ---- leaves: P2P work items, then L2P + partials per body
     uint32_t* item_first = as<uint32_t>(ctx->item_first);
     uint32_t* slot_first = as<uint32_t>(ctx->slot_first);
     uint32_t* totals = as<uint32_t>(ctx->work) + 4;
     leaf_items_plan(t, as<uint32_t>(ctx->doff[3]), item_first, slot_first, totals, st);
     uint32_t htot[2] = {0, 0};
-    CK(cudaMemcpyAsync(htot, totals, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    if (gp) {
+        htot[0] = gp->items_cap;
+        htot[1] = gp->slots_cap;
+        leaf_items_check(totals, gp->items_cap, gp->slots_cap, &ctx->ds->err, st);
+    } else {
+        CK(cudaMemcpyAsync(htot, totals, 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        ctx->items_total[0] = htot[0];
+        ctx->items_total[1] = htot[1];
+    }
     if ((rc = ensure(ctx, ctx->item_leaf, 4 * (size_t)(htot[0] + 1))) ||
         (rc = ensure(ctx, ctx->part_hi, 16 * (size_t)(htot[1] + 1))) ||
         (rc = ensure(ctx, ctx->part_lo, 16 * (size_t)(htot[1] + 1))))
         return rc;
-    leaf_items_fill(t, item_first, as<int>(ctx->item_leaf), as<int>(ctx->leaf_of), st);
+    leaf_items_fill(t, item_first, as<int>(ctx->item_leaf), htot[0], as<int>(ctx->leaf_of), st);
     LeafArgs la{};
     la.t = t; la.p = p; la.G = ctx->cfg.G;
     la.xs = as<double>(ctx->xs); la.ys = as<double>(ctx->ys); la.zs = as<double>(ctx->zs); la.ms = as<double>(ctx->ms);
@@ -455,6 +559,7 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     la.part_hi = as<double2>(ctx->part_hi); la.part_lo = as<double2>(ctx->part_lo);
     la.tb = ctx->tb;
     la.interactions = as<unsigned long long>(ctx->dcount) + 1;
+    la.slots_cap = htot[1];
     if (mixed) {
         leaf_relative_f32(t, la.xs, la.ys, la.zs, la.ms, la.zc, as<float4>(ctx->prel), st);
         la.prel = as<float4>(ctx->prel);
@@ -462,10 +567,11 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     } else {
         la.loc = ctx->loc.ptr;
     }
-    leaf_eval(la, mixed, as<int>(ctx->item_leaf), item_first, slot_first, (int)htot[0],
+    leaf_eval(la, mixed, as<int>(ctx->item_leaf), item_first, slot_first, totals,
               as<unsigned>(ctx->work), as<int>(ctx->leaf_of), st);
-    CK(cudaEventRecord(ctx->ev[7], st));
+    CK(rec(7));
     CK(cudaGetLastError());
+    if (gp) return FMM_OK;  // the caller checks the status block after the replay
     CK(cudaStreamSynchronize(st));
     CK(cudaMemcpy(&err, &ctx->ds->err, 4, cudaMemcpyDeviceToHost));
     if (err & kErrCapacity) return fail(ctx, FMM_ERR_CAPACITY, "an internal list overflowed");
@@ -616,13 +722,19 @@ void fmm_destroy(fmm_ctx* ctx) {
                   &ctx->f, &ctx->bbox, &ctx->level, &ctx->begin, &ctx->end, &ctx->parent,
                   &ctx->first_child, &ctx->nchild, &ctx->M, &ctx->S, &ctx->zc, &ctx->r, &ctx->hs, &ctx->Pk,
                   &ctx->mult, &ctx->mult32, &ctx->loc, &ctx->loc32, &ctx->fmin, &ctx->fscratch,
-                  &ctx->front0, &ctx->front1, &ctx->dalt, &ctx->dcount, &ctx->zhi, &ctx->zlo, &ctx->contrib, &ctx->Phat, &ctx->r32,
+                  &ctx->front0, &ctx->front1, &ctx->dcount, &ctx->zhi, &ctx->zlo, &ctx->contrib, &ctx->Phat, &ctx->r32,
                   &ctx->item_first, &ctx->slot_first, &ctx->item_leaf, &ctx->leaf_of, &ctx->part_hi,
-                  &ctx->part_lo, &ctx->work};
+                  &ctx->part_lo, &ctx->work, &ctx->coff, &ctx->box, &ctx->ck0, &ctx->ck1, &ctx->cv0,
+                  &ctx->cv1, &ctx->cid};
     for (Buf* b : all) release(*b);
+    drop_plan(ctx->plan);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+    if (ctx->gev[0]) cudaEventDestroy(ctx->gev[0]);
+    if (ctx->gev[1]) cudaEventDestroy(ctx->gev[1]);
     for (int l = 0; l < 4; ++l) {
         release(ctx->lists[l]);
         release(ctx->dkeys[l]);
+        release(ctx->dalt[l]);
         release(ctx->doff[l]);
         release(ctx->hin[l]);
         release(ctx->hout[l]);
@@ -667,6 +779,147 @@ int fmm_solve_host(fmm_ctx* ctx, int64_t n, const double* x, const double* y, co
         if (outp[i]) CK(cudaMemcpyAsync(outp[i], ctx->hout[i].ptr, bytes, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return FMM_OK;
+}
+
+int fmm_solve_graph(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, int64_t n, const double* x,
+                    const double* y, const double* z, const double* m, double* ax, double* ay, double* az,
+                    double* pot, void* cuda_stream) {
+    if (!ctx) return FMM_ERR_ARG;
+    if (n < 0 || n > (int64_t)1 << 30) return fail(ctx, FMM_ERR_ARG, "n must be in [0, 2^30]");
+    if (offsets) {
+        if (nclusters < 1 || offsets[0] != 0 || offsets[nclusters] != n)
+            return fail(ctx, FMM_ERR_ARG, "offsets must run from 0 to n");
+        for (int32_t c = 0; c < nclusters; ++c)
+            if (offsets[c + 1] < offsets[c]) return fail(ctx, FMM_ERR_ARG, "offsets must be non-decreasing");
+    } else {
+        nclusters = 1;
+    }
+    if (n == 0) return solve_device(ctx, 0, nclusters, offsets, x, y, z, m, ax, ay, az, pot, nullptr);
+    if (!x || !y || !z || !m || !ax || !ay || !az) return fail(ctx, FMM_ERR_ARG, "NULL input or output pointer");
+    cudaSetDevice(ctx->device);
+    if (!ctx->gstream) {
+        CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+        CK(cudaEventCreate(&ctx->gev[0]));
+        CK(cudaEventCreate(&ctx->gev[1]));
+    }
+    cudaStream_t gs = ctx->gstream;
+    CK(cudaStreamSynchronize((cudaStream_t)cuda_stream));  // the inputs are ready
+    GraphPlan& g = ctx->plan;
+    const void* ptrs[8] = {x, y, z, m, ax, ay, az, pot};
+    std::vector<int64_t> offs(offsets ? offsets : nullptr, offsets ? offsets + nclusters + 1 : nullptr);
+    const bool same = g.valid && g.n == n && g.offs == offs && g.gen == ctx->gen &&
+                      std::equal(ptrs, ptrs + 8, g.ptrs);
+    if (same) {
+        // replay, then read one status block: any overflow or a tree deeper than
+        // planned sends this call to the ordinary solve and the next to a new plan
+        CK(cudaEventRecord(ctx->gev[0], gs));
+        CK(cudaGraphLaunch(g.exec, gs));
+        CK(cudaEventRecord(ctx->gev[1], gs));
+        CK(cudaMemcpyAsync(ctx->h_ds, ctx->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, gs));
+        unsigned long long cnt[6] = {};
+        CK(cudaMemcpyAsync(cnt, ctx->dcount.ptr, sizeof(cnt), cudaMemcpyDeviceToHost, gs));
+        CK(cudaStreamSynchronize(gs));
+        const DevScalars& d = *ctx->h_ds;
+        bool ok = d.err == 0;
+        int nl = 1;
+        for (int L = 0; L <= kMaxLevel && ok; ++L) {
+            const int cntL = d.level_start[L + 1] - d.level_start[L];
+            if (cntL > g.lvl_cap[L]) ok = false;
+            if (cntL > 0) nl = L + 1;
+        }
+        if (nl > g.nlevels) ok = false;
+        if (ok) {
+            ctx->nnodes = d.nnodes;
+            ctx->nlevels = nl;
+            std::memcpy(ctx->h_level_start, d.level_start, sizeof(ctx->h_level_start));
+            std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+            fmm_stats& st = ctx->stats;
+            st.n = n;
+            st.nnodes = d.nnodes;
+            st.nlevels = nl;
+            st.n_far = (int64_t)d.list_cnt[0];
+            st.n_near = (int64_t)d.list_cnt[1];
+            st.n_m2l = (int64_t)d.list_cnt[2];
+            st.n_p2p = (int64_t)d.list_cnt[3];
+            st.p2p_interactions = (int64_t)cnt[1];
+            st.walk_iters = g.walk_iters[0] + g.walk_iters[1];
+            st.kernel_launches = g.launches;
+            st.ms_tree = elapsed(ctx->ev[0], ctx->ev[1]);
+            st.ms_upward = elapsed(ctx->ev[1], ctx->ev[2]);
+            st.ms_estimate = elapsed(ctx->ev[2], ctx->ev[3]);
+            st.ms_walk = elapsed(ctx->ev[3], ctx->ev[4]);
+            st.ms_m2l = elapsed(ctx->ev[4], ctx->ev[5]);
+            st.ms_downward = elapsed(ctx->ev[5], ctx->ev[6]);
+            st.ms_leaf = elapsed(ctx->ev[6], ctx->ev[7]);
+            st.ms_total = elapsed(ctx->gev[0], ctx->gev[1]);
+            st.graph_replays = 1;
+            return FMM_OK;
+        }
+        g.valid = false;
+    }
+    // an ordinary solve gives this call's result and the sizes to plan from
+    int rc = solve_device(ctx, n, nclusters, offsets, x, y, z, m, ax, ay, az, pot, gs);
+    if (rc != FMM_OK) return rc;
+    const fmm_stats eager = ctx->stats;
+    drop_plan(g);
+    g.n = n;
+    g.offs = offs;
+    std::copy(ptrs, ptrs + 8, g.ptrs);
+    const auto grow = [](int64_t v, double f, int64_t pad) { return (int64_t)(v * f) + pad; };
+    // node headroom, but not past the index width of the ordinary solve when that
+    // still leaves 6%: one more bit can turn the 32-bit directed keys into 64-bit
+    // ones (a 2^16-node tree) or add a radix pass
+    int64_t node_cap = grow(ctx->nnodes, 1.25, 64);
+    const int64_t same_width = ((int64_t)1 << bit_length(ctx->nnodes)) - 1;
+    if (node_cap > same_width && same_width >= ctx->nnodes + ctx->nnodes / 16 + 16) node_cap = same_width;
+    g.node_cap = (int)std::min<int64_t>(node_cap, INT32_MAX / 2);
+    g.nb = bit_length(g.node_cap);
+    g.nlevels = std::min(ctx->nlevels + 1, kMaxLevel + 1);
+    g.nroots = nclusters;
+    for (int L = 0; L <= kMaxLevel + 1; ++L) {
+        const int cntL = L <= kMaxLevel ? ctx->h_level_start[L + 1] - ctx->h_level_start[L] : 0;
+        g.lvl_cap[L] = L < g.nlevels ? (int)std::min<int64_t>(grow(cntL, 1.5, 64), g.node_cap) : 0;
+    }
+    for (int l = 0; l < 4; ++l) g.pair_cap[l] = grow(ctx->npairs[l], 1.3, 4096);
+    // walk steps: the ordinary solve's count of each walk plus a margin
+    g.walk_iters[0] = std::min(ctx->walk_steps[0] + 4, kMaxWalkIters);
+    g.walk_iters[1] = std::min(ctx->walk_steps[1] + 4, kMaxWalkIters);
+    g.items_cap = (uint32_t)grow(ctx->items_total[0], 1.3, 1024);
+    g.slots_cap = (uint32_t)grow(ctx->items_total[1], 1.3, 65536);
+    CK(cudaMallocHost(&g.h_coff, 4 * ((size_t)nclusters + 1)));
+    std::memcpy(g.h_coff, ctx->h_coff.data(), 4 * ((size_t)nclusters + 1));
+    // the graph form once without capture: allocates every buffer at its planned
+    // size (nothing may allocate while capturing) and checks that it runs clean
+    ctx->gmode = &g;
+    rc = solve_device(ctx, n, nclusters, offsets, x, y, z, m, ax, ay, az, pot, gs);
+    ctx->gmode = nullptr;
+    unsigned err = 1;
+    if (rc == FMM_OK) {
+        CK(cudaMemcpyAsync(&err, &ctx->ds->err, 4, cudaMemcpyDeviceToHost, gs));
+        CK(cudaStreamSynchronize(gs));
+    }
+    if (rc == FMM_OK && err == 0) {
+        cudaGraph_t graph = nullptr;
+        const int64_t gen0 = ctx->gen;
+        if (cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            ctx->gmode = &g;
+            rc = solve_device(ctx, n, nclusters, offsets, x, y, z, m, ax, ay, az, pot, gs);
+            ctx->gmode = nullptr;
+            g.launches = g_launches;
+            const cudaError_t ec = cudaStreamEndCapture(gs, &graph);
+            if (rc == FMM_OK && ec == cudaSuccess && graph && ctx->gen == gen0 &&
+                cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess) {
+                g.valid = true;
+                g.gen = ctx->gen;
+            }
+            if (graph) cudaGraphDestroy(graph);
+        }
+        cudaGetLastError();
+    }
+    // this call's result is the ordinary solve's (the graph form wrote the same)
+    ctx->stats = eager;
+    ctx->stats.graph_replays = 0;
+    return rc == FMM_OK || g.valid ? FMM_OK : rc;
 }
 
 int fmm_solve_batch(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, const double* x,

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m(TreeView t, int p, TabF64 tb
     double (*tile)[33] = sh_tile[wib];
     const int nr = ncoef_real(p);
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int k = blockIdx.x * (blockDim.x >> 5) + wib; k < t.nnodes; k += nwarps) {
+    for (int k = blockIdx.x * (blockDim.x >> 5) + wib, nnodes = *t.dnn; k < nnodes; k += nwarps) {
         if (t.nchild[k] != 0) continue;
         const double is = 1.0 / hs[k];
         const double cx = zc[3 * k], cy = zc[3 * k + 1], cz = zc[3 * k + 2];
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
     const int nr = ncoef_real(p);
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     const dw zero = dw_make(0.f, 0.f);
-    for (int k = blockIdx.x * (blockDim.x >> 5) + wib; k < t.nnodes; k += nwarps) {
+    for (int k = blockIdx.x * (blockDim.x >> 5) + wib, nnodes = *t.dnn; k < nnodes; k += nwarps) {
         if (t.nchild[k] != 0) continue;
         const double is = 1.0 / hs[k];
         const double cx = zc[3 * k], cy = zc[3 * k + 1], cz = zc[3 * k + 2];
@@ -273,12 +273,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
 
 // P_n = s^n sqrt(sum_{m=-n}^{n} |Mhat_n^m|^2)  (Sec. 2.3)
 // (also the FP32 copies used by the walk's screen: Phat_n = P_n / s^n and r)
-__global__ void k_pnorm(int nnodes, int p, const double* __restrict__ mult,
+__global__ void k_pnorm(const int* __restrict__ dnn, int p, const double* __restrict__ mult,
                         const double* __restrict__ rr, const double* __restrict__ hs,
                         double* __restrict__ Pk, float* __restrict__ Phat,
                         float* __restrict__ r32) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nnodes) return;
+    if (k >= *dnn) return;
     const double* M = mult + (size_t)ncoef_real(p) * k;
     const double s = hs[k];
     double sp = 1.0;
@@ -293,20 +293,20 @@ __global__ void k_pnorm(int nnodes, int p, const double* __restrict__ mult,
     r32[k] = (float)rr[k];
 }
 
-__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, const int* __restrict__ dnn, int nr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (float)a[i];
+    if (i < (int64_t)*dnn * nr) b[i] = (float)a[i];
 }
 
 // ---- L2L: one block per child, one thread per output (n, m >= 0)
 //   Fhat_n^m(C) += sum_{k<=p-n} sum_l conj(Shat_k^l(b)) beta' sigma^n Fhat_{n+k}^{m+l}(P),
 //   b = (z_C - z_P)/s_P, sigma = s_C/s_P, beta' = w_{n+k}^{m+l} / (w_k^l w_n^m).
 template <typename T, typename Tab>
-__global__ void k_l2l(TreeView t, int k0, int k1, int p, Tab tb, const double* __restrict__ zc,
+__global__ void k_l2l(TreeView t, int L, int p, Tab tb, const double* __restrict__ zc,
                       const double* __restrict__ hs, T* __restrict__ loc) {
     extern __shared__ __align__(16) unsigned char sh_l2l_raw[];
-    const int C = k0 + blockIdx.x;
-    if (C >= k1) return;
+    const int C = t.dls[L] + blockIdx.x;
+    if (C >= t.dls[L + 1]) return;
     const int P = t.parent[C];
     const int nc = tri(p + 1, 0), nr = ncoef_real(p);
     Cx<T>* S = reinterpret_cast<Cx<T>*>(sh_l2l_raw);
@@ -345,20 +345,20 @@ __global__ void k_l2l(TreeView t, int k0, int k1, int p, Tab tb, const double* _
     }
 }
 
-__global__ void k_hat_scales(int nnodes, const int* __restrict__ parent, const double* __restrict__ r,
-                             double* __restrict__ hs) {
+__global__ void k_hat_scales(const int* __restrict__ dnn, const int* __restrict__ parent,
+                             const double* __restrict__ r, double* __restrict__ hs) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nnodes) return;
+    if (k >= *dnn) return;
     int root = k;
     while (parent[root] >= 0) root = parent[root];
     const double floor_s = kHatFloor * (r[root] > 0.0 ? r[root] : 1.0);
     hs[k] = r[k] > floor_s ? r[k] : floor_s;
 }
 
-__global__ void k_node_centres(int nnodes, const double* __restrict__ zc, const double* __restrict__ hs,
+__global__ void k_node_centres(const int* __restrict__ dnn, const double* __restrict__ zc, const double* __restrict__ hs,
                                float4* __restrict__ zhi, float4* __restrict__ zlo) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nnodes) return;
+    if (k >= *dnn) return;
     float h[3], l[3];
     for (int d = 0; d < 3; ++d) {
         const double z = zc[3 * k + d];
@@ -420,36 +420,38 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
         (k_p2m<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, hs, mult), note_launch());
     const int nr = ncoef_real(p);
     (void)nr;
-    for (int L = t.nlevels - 2; L >= 0; --L)
-        m2m_level(t, h_level_start[L], h_level_start[L + 1], h_level_start[L + 1], h_level_start[L + 2], p,
-                  zc, hs, mult, contrib, tbl, dword, st);
-    (k_pnorm<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, p, mult, r, hs, Pk, Phat, r32), note_launch());
+    (void)h_level_start;
+    for (int L = t.nlevels - 2; L >= 0; --L) m2m_level(t, L, p, zc, hs, mult, contrib, tbl, dword, st);
+    (k_pnorm<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.dnn, p, mult, r, hs, Pk, Phat, r32), note_launch());
 }
 
-void hat_scales(int nnodes, const int* parent, const double* r, double* hs, cudaStream_t st) {
-    (k_hat_scales<<<blocks_for(nnodes, 128), 128, 0, st>>>(nnodes, parent, r, hs), note_launch());
+void hat_scales(const TreeView& t, const int* parent, const double* r, double* hs, cudaStream_t st) {
+    (k_hat_scales<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.dnn, parent, r, hs), note_launch());
 }
 
-void node_centres_f32(int nnodes, const double* zc, const double* hs, float4* zhi, float4* zlo, cudaStream_t st) {
-    (k_node_centres<<<blocks_for(nnodes, 128), 128, 0, st>>>(nnodes, zc, hs, zhi, zlo), note_launch());
+void node_centres_f32(const TreeView& t, const double* zc, const double* hs, float4* zhi, float4* zlo,
+                      cudaStream_t st) {
+    (k_node_centres<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.dnn, zc, hs, zhi, zlo), note_launch());
 }
 
-__global__ void k_to_f32_strided(const double* __restrict__ a, float* __restrict__ b, int nnodes, int nr,
-                                 int stride) {
+__global__ void k_to_f32_strided(const double* __restrict__ a, float* __restrict__ b, const int* __restrict__ dnn,
+                                 int nr, int stride) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)nnodes * stride) return;
+    if (q >= (int64_t)*dnn * stride) return;
     const int64_t k = q / stride;
     const int j = (int)(q - k * stride);
     b[q] = j < nr ? (float)a[k * nr + j] : 0.0f;
 }
 
-void multipoles_to_f32_padded(const double* mult, float* mult32, int nnodes, int nr, int stride, cudaStream_t st) {
-    const int64_t n = (int64_t)nnodes * stride;
-    if (n > 0) (k_to_f32_strided<<<(int)((n + 255) / 256), 256, 0, st>>>(mult, mult32, nnodes, nr, stride), note_launch());
+void multipoles_to_f32_padded(const double* mult, float* mult32, const TreeView& t, int nr, int stride,
+                              cudaStream_t st) {
+    const int64_t n = (int64_t)t.nnodes * stride;
+    if (n > 0) (k_to_f32_strided<<<(int)((n + 255) / 256), 256, 0, st>>>(mult, mult32, t.dnn, nr, stride), note_launch());
 }
 
-void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStream_t st) {
-    if (count > 0) (k_to_f32<<<blocks_for(count, 256), 256, 0, st>>>(mult, mult32, count), note_launch());
+void multipoles_to_f32(const double* mult, float* mult32, const TreeView& t, int nr, cudaStream_t st) {
+    const int64_t count = (int64_t)t.nnodes * nr;
+    if (count > 0) (k_to_f32<<<blocks_for(count, 256), 256, 0, st>>>(mult, mult32, t.dnn, nr), note_launch());
 }
 
 // L2L level by level: the rotation form (translate.cu) unless GBFMM_L2L_DIRECT
@@ -468,11 +470,11 @@ void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const
         cudaFuncSetAttribute(k_l2l<double, TabF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr_set = true;
     }
+    (void)h_level_start;
     for (int L = 1; L < t.nlevels; ++L) {
-        const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
-        if (k1 <= k0) continue;
-        if (GBFMM_L2L_DIRECT) (k_l2l<double, TabF64><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, tb, zc, hs, loc), note_launch());
-        else l2l_level(t, k0, k1, p, zc, hs, loc, tbl, false, st);
+        if (t.lvl_cnt[L] <= 0) continue;
+        if (GBFMM_L2L_DIRECT) (k_l2l<double, TabF64><<<t.lvl_cnt[L], 64, sh, st>>>(t, L, p, tb, zc, hs, loc), note_launch());
+        else l2l_level(t, L, p, zc, hs, loc, tbl, false, st);
     }
 }
 
@@ -480,11 +482,11 @@ void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const
                        const double* hs, float* loc, const DevTables& tbl, cudaStream_t st) {
     const int nc = tri(p + 1, 0), nr = ncoef_real(p);
     const size_t sh = (size_t)(2 * nc + nr + p + 1) * sizeof(float);
+    (void)h_level_start;
     for (int L = 1; L < t.nlevels; ++L) {
-        const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
-        if (k1 <= k0) continue;
-        if (GBFMM_L2L_DIRECT) (k_l2l<float, TabF32><<<k1 - k0, 64, sh, st>>>(t, k0, k1, p, TabF32{}, zc, hs, loc), note_launch());
-        else l2l_level(t, k0, k1, p, zc, hs, loc, tbl, true, st);
+        if (t.lvl_cnt[L] <= 0) continue;
+        if (GBFMM_L2L_DIRECT) (k_l2l<float, TabF32><<<t.lvl_cnt[L], 64, sh, st>>>(t, L, p, TabF32{}, zc, hs, loc), note_launch());
+        else l2l_level(t, L, p, zc, hs, loc, tbl, true, st);
     }
 }
 

@@ -83,12 +83,20 @@ inline size_t swap_cos_offset(int n) { return (size_t)n * (n + 1) * (2 * n + 1) 
 inline size_t swap_sin_offset(int n) { return (size_t)(n - 1) * n * (2 * n - 1) / 6; }  // sum_{k<n} k^2
 
 // Tree arrays (device), nodes numbered level by level, key order inside a level.
+// Kernels take the node count and the level ranges from device memory (dnn,
+// dls: written by the tree build), so one launch sequence serves any tree up
+// to the sizes the host used for the grids: the exact sizes of this tree in
+// an ordinary solve, planned capacities when the solve is replayed from a
+// captured CUDA graph.
 struct TreeView {
     int n;
-    int nnodes;
-    int nlevels;
+    int nnodes;   // grid size of per-node launches (>= *dnn)
+    int nlevels;  // levels launched by per-level loops (>= the tree's)
     int leaf_size;
-    int nroots;  // trees of the forest: nodes [0, nroots) are their roots (level 0)
+    int nroots;   // grid size for the roots (>= the number of trees)
+    int lvl_cnt[kMaxLevel + 2];  // grid size of per-level launches, level L
+    const int* dnn;  // device: number of nodes
+    const int* dls;  // device: level_start[0 .. kMaxLevel + 1]
     const int* level;
     const int* begin;
     const int* end;
@@ -105,11 +113,14 @@ void note_launch();
 // Stable LSD radix sort of 64-bit keys (optionally with 32-bit values) on the
 // low `bits` bits. Ping-pongs between buffers; returns 1 if the sorted data
 // ends in (k1, v1), 0 if in (k0, v0). hist needs radix_hist_words(n) words.
+// dn (device, may be NULL): the grid covers n keys but only the first
+// min(n, *dn) are sorted (a count known on the device only, in a captured solve).
 size_t radix_hist_words(int64_t n);
 int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bits,
-               uint32_t* hist, cudaStream_t st);
+               uint32_t* hist, cudaStream_t st, const unsigned long long* dn = nullptr);
 // The same for 32-bit keys without payload.
-int radix_sort32(uint32_t* k0, uint32_t* k1, int64_t n, int bits, uint32_t* hist, cudaStream_t st);
+int radix_sort32(uint32_t* k0, uint32_t* k1, int64_t n, int bits, uint32_t* hist, cudaStream_t st,
+                 const unsigned long long* dn = nullptr);
 // single-block exclusive scan of count uint32 values in place; total -> *total (device)
 void scan_exclusive_u32(uint32_t* data, int64_t count, uint32_t* total, cudaStream_t st);
 // the same for large tables (multi-block); scratch: scan_scratch_words(count) words
@@ -173,25 +184,31 @@ constexpr int kWalkBadIndex = -100;  // dual_tree_walk: a frontier entry out of 
 int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* r, const double* P,
                    const float* fmin, int p, double eps, const double* binom_row, const float4* zhi,
                    const float4* zlo, const float* r32, const float* Phat, WalkBuffers& wb,
-                   DevScalars* ds, DevScalars* h_ds, cudaStream_t st);
+                   DevScalars* ds, DevScalars* h_ds, int fixed_iters, cudaStream_t st);
+// a walk run for a planned nit steps must have an empty frontier after them
+// (else kErrCapacity)
+void walk_check_finished(DevScalars* ds, int nit, cudaStream_t st);
 // Scalar-force estimate f (Sec. 2.3) from the theta-walk lists given as
 // per-target CSR (sorted directed keys target<<nb | source).
 void scalar_force(const TreeView& t, const double* zc, const double* M, const float4* xf,
                   const uint64_t* far_keys, const uint32_t* far_off, const uint64_t* near_keys,
                   const uint32_t* near_off, int nb, const int* h_level_start, float* farf, float* f,
                   float* fmin, cudaStream_t st);
-// directed entries of a pair list: (B<-A) and (A<-B), self pairs once.
-void pairs_to_directed(const int2* pairs, int64_t npairs, int nb, uint64_t* keys,
-                       unsigned long long* count, cudaStream_t st);
+// directed entries of a pair list: (B<-A) and (A<-B), a self pair once and a
+// marker that sorts last; np: the device count of pairs, npcap >= *np the
+// pairs the grid covers; *nkeys (device) <- 2 min(*np, npcap), the keys written.
+void pairs_to_directed(const int2* pairs, const unsigned long long* np, int64_t npcap, int nb, uint64_t* keys,
+                       unsigned long long* count, unsigned long long* nkeys, cudaStream_t st);
 // 32-bit keys (when 2 nb <= 32); the sorted keys are widened to 64 bits by
 // directed_offsets_widen, which also writes the CSR offsets.
-void pairs_to_directed32(const int2* pairs, int64_t npairs, int nb, uint32_t* keys,
-                         unsigned long long* count, cudaStream_t st);
-void directed_offsets_widen(const uint32_t* k32, int64_t nkeys, int nb, int nnodes, uint64_t* keys,
-                            uint32_t* off, cudaStream_t st);
-// CSR offsets (nnodes + 1) of sorted directed keys.
-void directed_offsets(const uint64_t* keys, int64_t nkeys, int nb, int nnodes, uint32_t* off,
-                      cudaStream_t st);
+void pairs_to_directed32(const int2* pairs, const unsigned long long* np, int64_t npcap, int nb, uint32_t* keys,
+                         unsigned long long* count, unsigned long long* nkeys, cudaStream_t st);
+// dnk (device): the keys present, of the nkeys the grid covers
+void directed_offsets_widen(const uint32_t* k32, int64_t nkeys, const unsigned long long* dnk, int nb,
+                            const int* dnn, uint64_t* keys, uint32_t* off, cudaStream_t st);
+// CSR offsets (nnodes + 1, nnodes = *dnn) of sorted directed keys.
+void directed_offsets(const uint64_t* keys, int64_t nkeys, const unsigned long long* dnk, int nb, const int* dnn,
+                      uint32_t* off, cudaStream_t st);
 
 // ---------------------------------------------------------- expansions.cu
 void upload_expansion_tables(const HostTables& h);
@@ -199,7 +216,7 @@ void upload_expansion_tables(const HostTables& h);
 // size of its tree's root so that no cell (a single body has r = 0) gets a scale so small
 // that its FP32 local coefficients F s^n fall into the denormal range.
 constexpr double kHatFloor = 0x1p-40;
-void hat_scales(int nnodes, const int* parent, const double* r, double* hs, cudaStream_t st);
+void hat_scales(const TreeView& t, const int* parent, const double* r, double* hs, cudaStream_t st);
 // Hat multipoles in FP64: P2M at leaves, M2M level by level; P_k per node.
 // dword: the P2M and M2M arithmetic runs in double-word FP32 (mixed precision).
 // r: node sizes (the walk's FP32 copy r32 is written from them); hs: hat scales.
@@ -207,21 +224,22 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
                  const double* ys, const double* zs, const double* ms, const double* zc,
                  const double* r, const double* hs, double* mult, double* Pk, float* Phat, float* r32,
                  double* contrib, const DevTables& tb, bool dword, cudaStream_t st);
-// rotation-accelerated M2M of one level: children [child0, child1) into their
-// parents [parent0, parent1); contrib: (p+1)^2 doubles per node (scratch);
-// dword: double-word FP32 arithmetic instead of FP64
-void m2m_level(const TreeView& t, int parent0, int parent1, int child0, int child1, int p,
-               const double* zc, const double* hs, double* mult, double* contrib, const DevTables& tb,
-               bool dword, cudaStream_t st);
-// rotation-accelerated L2L of one level: the locals of nodes [k0, k1) gain
-// their parents' shifted locals; loc: FP32 (fp32) or FP64 (p+1)^2 per node
-void l2l_level(const TreeView& t, int k0, int k1, int p, const double* zc, const double* hs, void* loc,
+// rotation-accelerated M2M of one level: the children (level L + 1) into their
+// parents (level L); contrib: (p+1)^2 doubles per node (scratch); dword:
+// double-word FP32 arithmetic instead of FP64
+void m2m_level(const TreeView& t, int L, int p, const double* zc, const double* hs, double* mult,
+               double* contrib, const DevTables& tb, bool dword, cudaStream_t st);
+// rotation-accelerated L2L of one level: the locals of the nodes of level L
+// gain their parents' shifted locals; loc: FP32 (fp32) or FP64 (p+1)^2 per node
+void l2l_level(const TreeView& t, int L, int p, const double* zc, const double* hs, void* loc,
                const DevTables& tb, bool fp32, cudaStream_t st);
-void multipoles_to_f32(const double* mult, float* mult32, int64_t count, cudaStream_t st);
+void multipoles_to_f32(const double* mult, float* mult32, const TreeView& t, int nr, cudaStream_t st);
 // FP32 copy with each node's vector padded to `stride` floats (zeros after nr)
-void multipoles_to_f32_padded(const double* mult, float* mult32, int nnodes, int nr, int stride, cudaStream_t st);
+void multipoles_to_f32_padded(const double* mult, float* mult32, const TreeView& t, int nr, int stride,
+                              cudaStream_t st);
 // double-float node centres (hi, lo) and the FP32 hat scale in zhi.w
-void node_centres_f32(int nnodes, const double* zc, const double* hs, float4* zhi, float4* zlo, cudaStream_t st);
+void node_centres_f32(const TreeView& t, const double* zc, const double* hs, float4* zhi, float4* zlo,
+                      cudaStream_t st);
 // per-node minimum of the scalar-force estimate (leaves over bodies, then levels upward)
 
 // L2L level by level (FP64 or FP32 locals).
@@ -233,11 +251,11 @@ void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const
 // ----------------------------------------------------------------- m2l.cu
 // Rotation-accelerated M2L (Sec. 2.4), gathered per target over the sorted
 // directed list; writes the locals of every node (zero without sources).
-// queue: a device counter, zeroed here; warps take target cells from it.
-void m2l_f64(int nnodes, int p, const uint64_t* keys, const uint32_t* off, int nb,
+// queue: a device counter, zeroed here; warps take target cells (below *dnn) from it.
+void m2l_f64(const int* dnn, int p, const uint64_t* keys, const uint32_t* off, int nb,
              const double* mult, const double* zc, const double* hs, double* loc,
              const DevTables& tb, unsigned* queue, cudaStream_t st);
-void m2l_f32(int nnodes, int p, const uint64_t* keys, const uint32_t* off, int nb,
+void m2l_f32(const int* dnn, int p, const uint64_t* keys, const uint32_t* off, int nb,
              const float* mult, const float4* zhi, const float4* zlo, float* loc, unsigned* queue,
              cudaStream_t st);
 bool m2l32_supported(int p);
@@ -263,15 +281,21 @@ struct LeafArgs {
     double *ax, *ay, *az, *pot;
     const void* loc;   // FP64 or FP32 locals
     unsigned long long* interactions;  // directed body-body interactions (added by the P2P kernel)
+    uint32_t slots_cap;                // partial slots the buffers hold
     const float4* prel;  // leaf-relative FP32 bodies (mixed)
     double2 *part_hi, *part_lo;  // P2P partials: (ax, ay), (az, pot)
     DevTables tb;
 };
 void leaf_items_plan(const TreeView& t, const uint32_t* p2p_off, uint32_t* item_first, uint32_t* slot_first,
                      uint32_t* totals, cudaStream_t st);
-void leaf_items_fill(const TreeView& t, const uint32_t* item_first, int* item_leaf, int* leaf_of, cudaStream_t st);
+// raise kErrCapacity (and run no item) when the item or slot totals exceed the buffers
+void leaf_items_check(uint32_t* totals, uint32_t items_cap, uint32_t slots_cap, unsigned* err, cudaStream_t st);
+void leaf_items_fill(const TreeView& t, const uint32_t* item_first, int* item_leaf, uint32_t items_cap,
+                     int* leaf_of, cudaStream_t st);
+// nitems: device count of work items
 void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_t* item_first,
-               const uint32_t* slot_first, int nitems, unsigned* work, const int* leaf_of, cudaStream_t st);
+               const uint32_t* slot_first, const uint32_t* nitems, unsigned* work, const int* leaf_of,
+               cudaStream_t st);
 void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, const double* zs,
                        const double* ms, const double* zc, float4* prel, cudaStream_t st);
 void direct_sum_f64(int64_t n, const double* x, const double* y, const double* z, const double* m,

@@ -214,11 +214,12 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __restrict__ item_leaf,
                                                     const uint32_t* __restrict__ item_first,
                                                     const uint32_t* __restrict__ slot_first,
-                                                    int nitems, unsigned* __restrict__ work) {
+                                                    const uint32_t* __restrict__ nitems_p, unsigned* __restrict__ work) {
     __shared__ Body4<T> stage[4][kStageCap];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Body4<T>* sm = stage[wib];
     const uint64_t mask = (1ull << a.nb) - 1ull;
+    const int nitems = (int)*nitems_p;
     for (;;) {
         unsigned it = 0;
         if (lane == 0) it = atomicAdd(work, 1u);
@@ -370,6 +371,7 @@ __global__ void __launch_bounds__(128) k_leaf_reduce(LeafArgs a, const int* __re
     const uint32_t s0 = slot_first[B] + (uint32_t)(i - b0);
     for (uint32_t it = i0; it < i1; ++it) {
         const uint32_t slot = s0 + (it - i0) * (uint32_t)nB;
+        if (slot >= a.slots_cap) break;  // only after a capacity error (the result is discarded)
         const double2 u = a.part_hi[slot], w = a.part_lo[slot];
         sx += u.x; sy += u.y; sz += w.x; sp -= w.y;
     }
@@ -384,25 +386,36 @@ __global__ void __launch_bounds__(128) k_leaf_reduce(LeafArgs a, const int* __re
 __global__ void k_items_count(TreeView t, const uint32_t* __restrict__ off, uint32_t* __restrict__ nitems,
                               uint32_t* __restrict__ nslots) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= t.nnodes) return;
+    if (b >= t.nnodes) return;  // the grid's nodes; those past *dnn get no items
     uint32_t ni = 0;
-    if (t.nchild[b] == 0) {
+    if (b < *t.dnn && t.nchild[b] == 0) {
         const uint32_t deg = off[b + 1] - off[b];
         ni = (deg + kLeavesPerItem - 1) / kLeavesPerItem;
     }
     nitems[b] = ni;
-    nslots[b] = ni * (uint32_t)(t.end[b] - t.begin[b]);
+    nslots[b] = ni ? ni * (uint32_t)(t.end[b] - t.begin[b]) : 0u;
 }
 
-__global__ void k_items_fill(int nnodes, const uint32_t* __restrict__ item_first, int* __restrict__ item_leaf) {
+__global__ void k_items_fill(const int* __restrict__ dnn, const uint32_t* __restrict__ item_first,
+                             int* __restrict__ item_leaf, uint32_t items_cap) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nnodes) return;
-    for (uint32_t it = item_first[b]; it < item_first[b + 1]; ++it) item_leaf[it] = b;
+    if (b >= *dnn) return;
+    for (uint32_t it = item_first[b]; it < item_first[b + 1] && it < items_cap; ++it) item_leaf[it] = b;
+}
+
+// work items or partial slots past the buffers (a replayed solve whose lists
+// grew): raise the capacity error and run no item
+__global__ void k_check_items(uint32_t* totals, uint32_t items_cap, uint32_t slots_cap, unsigned* err) {
+    if (threadIdx.x != 0) return;
+    if (totals[0] > items_cap || totals[1] > slots_cap) {
+        atomicOr(err, kErrCapacity);
+        totals[0] = 0;
+    }
 }
 
 __global__ void k_leaf_of_bodies(TreeView t, int* __restrict__ leaf_of) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= t.nnodes || t.nchild[k] != 0) return;
+    if (k >= *t.dnn || t.nchild[k] != 0) return;
     for (int i = t.begin[k]; i < t.end[k]; ++i) leaf_of[i] = k;
 }
 
@@ -410,7 +423,7 @@ __global__ void k_leaf_relative(TreeView t, const double* __restrict__ xs, const
                                 const double* __restrict__ zs, const double* __restrict__ ms,
                                 const double* __restrict__ zc, float4* __restrict__ prel) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= t.nnodes || t.nchild[k] != 0) return;
+    if (k >= *t.dnn || t.nchild[k] != 0) return;
     const double cx = zc[3 * k], cy = zc[3 * k + 1], cz = zc[3 * k + 2];
     for (int i = t.begin[k]; i < t.end[k]; ++i)
         prel[i] = make_float4((float)(xs[i] - cx), (float)(ys[i] - cy), (float)(zs[i] - cz), (float)ms[i]);
@@ -489,13 +502,19 @@ void leaf_items_plan(const TreeView& t, const uint32_t* p2p_off, uint32_t* item_
     cudaMemcpyAsync(totals + 1, slot_first + t.nnodes, 4, cudaMemcpyDeviceToDevice, st);
 }
 
-void leaf_items_fill(const TreeView& t, const uint32_t* item_first, int* item_leaf, int* leaf_of, cudaStream_t st) {
-    (k_items_fill<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, item_first, item_leaf), note_launch());
+void leaf_items_check(uint32_t* totals, uint32_t items_cap, uint32_t slots_cap, unsigned* err, cudaStream_t st) {
+    (k_check_items<<<1, 32, 0, st>>>(totals, items_cap, slots_cap, err), note_launch());
+}
+
+void leaf_items_fill(const TreeView& t, const uint32_t* item_first, int* item_leaf, uint32_t items_cap,
+                     int* leaf_of, cudaStream_t st) {
+    (k_items_fill<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.dnn, item_first, item_leaf, items_cap), note_launch());
     (k_leaf_of_bodies<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, leaf_of), note_launch());
 }
 
 void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_t* item_first,
-               const uint32_t* slot_first, int nitems, unsigned* work, const int* leaf_of, cudaStream_t st) {
+               const uint32_t* slot_first, const uint32_t* nitems, unsigned* work, const int* leaf_of,
+               cudaStream_t st) {
     cudaMemsetAsync(work, 0, sizeof(unsigned), st);
     if (fp32) {
         (k_p2p_items<float><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());

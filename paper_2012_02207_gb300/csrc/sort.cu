@@ -25,9 +25,10 @@ constexpr int scatter_min_blocks() { return (sizeof(K) == 4 && !VAL) ? 3 : 2; }
 
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_hist(const K* __restrict__ keys, int64_t n,
-                                                   int shift, uint32_t* __restrict__ hist,
-                                                   int nblocks) {
+                                                   const unsigned long long* __restrict__ dn, int shift,
+                                                   uint32_t* __restrict__ hist, int nblocks) {
     __shared__ uint32_t h[256];
+    if (dn && (int64_t)*dn < n) n = (int64_t)*dn;  // tiles past the count give empty histograms
     for (int i = threadIdx.x; i < 256; i += kThreads) h[i] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kTile;
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(kThreads, scatter_min_blocks<K, VAL>()) k_scat
                                                       const uint32_t* __restrict__ vin,
                                                       K* __restrict__ kout,
                                                       uint32_t* __restrict__ vout, int64_t n,
+                                                      const unsigned long long* __restrict__ dn,
                                                       int shift, const uint32_t* __restrict__ offs,
                                                       int nblocks) {
     extern __shared__ __align__(16) unsigned char sh_scatter[];
@@ -62,6 +64,8 @@ __global__ void __launch_bounds__(kThreads, scatter_min_blocks<K, VAL>()) k_scat
     for (int d = threadIdx.x; d < 256; d += kThreads) boff[d] = offs[(int64_t)d * nblocks + blockIdx.x];
     __syncthreads();
     const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+    if (dn && (int64_t)*dn < n) n = (int64_t)*dn;
+    if (tile0 >= n) return;  // the whole block: nothing of this tile is present
     const int64_t base = tile0 + (int64_t)warp * kWarpItems;
     K key[kItems];
     uint32_t val[VAL ? kItems : 1], rank[kItems];
@@ -271,7 +275,7 @@ void scan_exclusive_u32(uint32_t* data, int64_t count, uint32_t* total, cudaStre
 namespace {
 template <typename K, bool VAL>
 int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int bits, uint32_t* hist,
-                    cudaStream_t st) {
+                    cudaStream_t st, const unsigned long long* dn) {
     if (n <= 1 || bits <= 0) return 0;
     static bool attr = false;
     if (!attr) {
@@ -286,10 +290,10 @@ int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int bit
         uint32_t* vi = cur ? v1 : v0;
         K* ko = cur ? k0 : k1;
         uint32_t* vo = cur ? v0 : v1;
-        (k_hist<K><<<nblocks, kThreads, 0, st>>>(ki, n, shift, hist, nblocks), note_launch());
+        (k_hist<K><<<nblocks, kThreads, 0, st>>>(ki, n, dn, shift, hist, nblocks), note_launch());
         scan_exclusive_u32_large(hist, (int64_t)256 * nblocks, nullptr, hist + (size_t)256 * nblocks + 1, st);
-        (k_scatter<K, VAL><<<nblocks, kThreads, scatter_smem<K, VAL>(), st>>>(ki, vi, ko, vo, n, shift, hist,
-                                                                              nblocks), note_launch());
+        (k_scatter<K, VAL><<<nblocks, kThreads, scatter_smem<K, VAL>(), st>>>(ki, vi, ko, vo, n, dn, shift,
+                                                                              hist, nblocks), note_launch());
         cur ^= 1;
     }
     return cur;
@@ -297,13 +301,14 @@ int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int bit
 }  // namespace
 
 int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bits,
-               uint32_t* hist, cudaStream_t st) {
-    return v0 ? radix_sort_impl<uint64_t, true>(k0, v0, k1, v1, n, bits, hist, st)
-              : radix_sort_impl<uint64_t, false>(k0, nullptr, k1, nullptr, n, bits, hist, st);
+               uint32_t* hist, cudaStream_t st, const unsigned long long* dn) {
+    return v0 ? radix_sort_impl<uint64_t, true>(k0, v0, k1, v1, n, bits, hist, st, dn)
+              : radix_sort_impl<uint64_t, false>(k0, nullptr, k1, nullptr, n, bits, hist, st, dn);
 }
 
-int radix_sort32(uint32_t* k0, uint32_t* k1, int64_t n, int bits, uint32_t* hist, cudaStream_t st) {
-    return radix_sort_impl<uint32_t, false>(k0, nullptr, k1, nullptr, n, bits, hist, st);
+int radix_sort32(uint32_t* k0, uint32_t* k1, int64_t n, int bits, uint32_t* hist, cudaStream_t st,
+                 const unsigned long long* dn) {
+    return radix_sort_impl<uint32_t, false>(k0, nullptr, k1, nullptr, n, bits, hist, st, dn);
 }
 
 }  // namespace gbfmm

@@ -147,7 +147,7 @@ __device__ void wswap(WarpVec<T>& w, int p, const RotTables<T>& tb, int lane) {
 __host__ __device__ inline int m2m_warp_values(int p) { return 2 * ncoef_real(p) + 6 * (p + 1); }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int k0, int k1, int p,
+__global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int Lc, int p,
                                                   const double* __restrict__ zc,
                                                   const double* __restrict__ hs,
                                                   const double* __restrict__ mult,
@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int k0, int k1, int
     T* pwb = pwa + 2 * (p + 1);    // (cos theta - i sin theta)^m: Rz(-theta), conjugate for Rz(theta)
     T* upow = pwb + 2 * (p + 1);   // u^k
     T* spow = upow + (p + 1);      // (s_C/s_P)^k
-    const int C = k0 + blockIdx.x * (blockDim.x >> 5) + wib;
-    if (C >= k1) return;
+    const int C = t.dls[Lc] + blockIdx.x * (blockDim.x >> 5) + wib;
+    if (C >= t.dls[Lc + 1]) return;
     const int P = t.parent[C];
     const double* src = mult + (size_t)nr * C;
     for (int q = lane; q < nr; q += 32) wv.v[q] = ar_from<T>(src[q]);
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int k0, int k1, int
 // on the axis), between the same rotations as M2M. The local coefficients
 // (T = float or double) are added to the child's, which the M2L wrote.
 template <typename T>
-__global__ void __launch_bounds__(128) k_l2l_rot(TreeView t, int k0, int k1, int p,
+__global__ void __launch_bounds__(128) k_l2l_rot(TreeView t, int L, int p,
                                                   const double* __restrict__ zc,
                                                   const double* __restrict__ hs,
                                                   T* __restrict__ loc, RotTables<T> tb) {
@@ -237,8 +237,8 @@ __global__ void __launch_bounds__(128) k_l2l_rot(TreeView t, int k0, int k1, int
     T* pwb = pwa + 2 * (p + 1);
     T* upow = pwb + 2 * (p + 1);
     T* spow = upow + (p + 1);
-    const int C = k0 + blockIdx.x * (blockDim.x >> 5) + wib;
-    if (C >= k1) return;
+    const int C = t.dls[L] + blockIdx.x * (blockDim.x >> 5) + wib;
+    if (C >= t.dls[L + 1]) return;
     const int P = t.parent[C];
     const T* src = loc + (size_t)nr * P;
     for (int q = lane; q < nr; q += 32) wv.v[q] = src[q];
@@ -288,11 +288,11 @@ __global__ void __launch_bounds__(128) k_l2l_rot(TreeView t, int k0, int k1, int
     for (int q = lane; q < nr; q += 32) dst[q] = ar_add(dst[q], wv.v[q]);
 }
 
-__global__ void k_m2m_sum(TreeView t, int k0, int k1, int nr, const double* __restrict__ contrib,
+__global__ void k_m2m_sum(TreeView t, int L, int nr, const double* __restrict__ contrib,
                           double* __restrict__ mult) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int P = k0 + (int)(q / nr), j = (int)(q % nr);
-    if (P >= k1 || t.nchild[P] == 0) return;
+    const int P = t.dls[L] + (int)(q / nr), j = (int)(q % nr);
+    if (P >= t.dls[L + 1] || t.nchild[P] == 0) return;
     const int c0 = t.first_child[P];
     double s = 0.0;
     for (int c = c0; c < c0 + t.nchild[P]; ++c) s += contrib[(size_t)nr * c + j];
@@ -300,7 +300,7 @@ __global__ void k_m2m_sum(TreeView t, int k0, int k1, int nr, const double* __re
 }
 
 template <typename T>
-void launch_m2m(const TreeView& t, int child0, int child1, int p, const double* zc, const double* hs,
+void launch_m2m(const TreeView& t, int Lc, int p, const double* zc, const double* hs,
                 const double* mult, double* contrib, const RotTables<T>& tb, cudaStream_t st) {
     const size_t sh = (size_t)4 * m2m_warp_values(p) * sizeof(T);
     static bool attr = false;
@@ -308,12 +308,12 @@ void launch_m2m(const TreeView& t, int child0, int child1, int p, const double* 
         cudaFuncSetAttribute(k_m2m_rot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr = true;
     }
-    const int nblk = (child1 - child0 + 3) / 4;
-    (k_m2m_rot<T><<<nblk, 128, sh, st>>>(t, child0, child1, p, zc, hs, mult, contrib, tb), note_launch());
+    const int nblk = (t.lvl_cnt[Lc] + 3) / 4;
+    (k_m2m_rot<T><<<nblk, 128, sh, st>>>(t, Lc, p, zc, hs, mult, contrib, tb), note_launch());
 }
 
 template <typename T>
-void launch_l2l(const TreeView& t, int k0, int k1, int p, const double* zc, const double* hs, T* loc,
+void launch_l2l(const TreeView& t, int L, int p, const double* zc, const double* hs, T* loc,
                 const RotTables<T>& tb, cudaStream_t st) {
     const size_t sh = (size_t)4 * m2m_warp_values(p) * sizeof(T);
     static bool attr = false;
@@ -321,36 +321,35 @@ void launch_l2l(const TreeView& t, int k0, int k1, int p, const double* zc, cons
         cudaFuncSetAttribute(k_l2l_rot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr = true;
     }
-    const int nblk = (k1 - k0 + 3) / 4;
-    (k_l2l_rot<T><<<nblk, 128, sh, st>>>(t, k0, k1, p, zc, hs, loc, tb), note_launch());
+    const int nblk = (t.lvl_cnt[L] + 3) / 4;
+    (k_l2l_rot<T><<<nblk, 128, sh, st>>>(t, L, p, zc, hs, loc, tb), note_launch());
 }
 
 }  // namespace
 
-void l2l_level(const TreeView& t, int k0, int k1, int p, const double* zc, const double* hs, void* loc,
+void l2l_level(const TreeView& t, int L, int p, const double* zc, const double* hs, void* loc,
                const DevTables& tb, bool fp32, cudaStream_t st) {
-    if (k1 <= k0) return;
+    if (t.lvl_cnt[L] <= 0) return;
     if (fp32)
-        launch_l2l<float>(t, k0, k1, p, zc, hs, static_cast<float*>(loc),
+        launch_l2l<float>(t, L, p, zc, hs, static_cast<float*>(loc),
                           RotTables<float>{tb.swap_cos_dw, tb.swap_sin_dw, tb.zshift_dw}, st);
     else
-        launch_l2l<double>(t, k0, k1, p, zc, hs, static_cast<double*>(loc),
+        launch_l2l<double>(t, L, p, zc, hs, static_cast<double*>(loc),
                            RotTables<double>{tb.swap_cos, tb.swap_sin, tb.zshift}, st);
 }
 
-void m2m_level(const TreeView& t, int parent0, int parent1, int child0, int child1, int p,
-               const double* zc, const double* hs, double* mult, double* contrib, const DevTables& tb,
-               bool dword, cudaStream_t st) {
-    if (child1 <= child0) return;
+void m2m_level(const TreeView& t, int L, int p, const double* zc, const double* hs, double* mult,
+               double* contrib, const DevTables& tb, bool dword, cudaStream_t st) {
+    if (t.lvl_cnt[L + 1] <= 0) return;
     const int nr = ncoef_real(p);
     if (dword)
-        launch_m2m<dw>(t, child0, child1, p, zc, hs, mult, contrib,
+        launch_m2m<dw>(t, L + 1, p, zc, hs, mult, contrib,
                        RotTables<dw>{tb.swap_cos_dw, tb.swap_sin_dw, tb.zshift_dw}, st);
     else
-        launch_m2m<double>(t, child0, child1, p, zc, hs, mult, contrib,
+        launch_m2m<double>(t, L + 1, p, zc, hs, mult, contrib,
                            RotTables<double>{tb.swap_cos, tb.swap_sin, tb.zshift}, st);
-    const int64_t work = (int64_t)(parent1 - parent0) * nr;
-    (k_m2m_sum<<<(int)((work + 127) / 128), 128, 0, st>>>(t, parent0, parent1, nr, contrib, mult), note_launch());
+    const int64_t work = (int64_t)t.lvl_cnt[L] * nr;
+    (k_m2m_sum<<<(int)((work + 127) / 128), 128, 0, st>>>(t, L, nr, contrib, mult), note_launch());
 }
 
 }  // namespace gbfmm

@@ -272,13 +272,21 @@ __global__ void k_level_emit(const int8_t* __restrict__ lcp, const uint8_t* __re
     }
 }
 
+// (more nodes than node_cap, the size of the node arrays, raise the capacity
+// error and clamp the counts, so that no later kernel indexes past the arrays)
 __global__ void k_level_starts(const uint32_t* __restrict__ off, int nchunks, const uint32_t* total,
-                               DevScalars* ds) {
+                               int node_cap, DevScalars* ds) {
     const int L = threadIdx.x;
-    if (L <= kMaxLevel) ds->level_start[L] = (int)off[(int64_t)L * nchunks];
+    const uint32_t cap = (uint32_t)node_cap;
+    if (L <= kMaxLevel) {
+        const uint32_t v = off[(int64_t)L * nchunks];
+        ds->level_start[L] = (int)(v < cap ? v : cap);
+    }
     if (L == 0) {
-        ds->level_start[kMaxLevel + 1] = (int)*total;
-        ds->nnodes = (int)*total;
+        const uint32_t tot = *total;
+        ds->level_start[kMaxLevel + 1] = (int)(tot < cap ? tot : cap);
+        ds->nnodes = (int)(tot < cap ? tot : cap);
+        if (tot > cap) atomicOr(&ds->err, kErrCapacity);
     }
 }
 
@@ -290,7 +298,7 @@ __global__ void k_finalize(const uint64_t* __restrict__ keys, int64_t n, int lea
                            int* __restrict__ parent, int* __restrict__ first_child,
                            int* __restrict__ nchild) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nnodes) return;
+    if (k >= ds->nnodes) return;
     const int L = level[k];
     const int b = begin[k];
     const int cend = cid ? coff[cid[b] + 1] : (int)n;  // end of the node's cluster
@@ -336,7 +344,7 @@ __global__ void k_geometry_leaves(TreeView t, const double* __restrict__ xs,
                                   double* __restrict__ S, double* __restrict__ zc,
                                   double* __restrict__ r) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= t.nnodes || t.nchild[k] != 0) return;
+    if (k >= *t.dnn || t.nchild[k] != 0) return;
     double Mk = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
     const int b = t.begin[k], e = t.end[k];
     for (int i = b; i < e; ++i) {
@@ -360,11 +368,11 @@ __global__ void k_geometry_leaves(TreeView t, const double* __restrict__ xs,
 }
 
 // Internal geometry of one level: sums over children in order.
-__global__ void k_geometry_internal(TreeView t, int k0, int k1, double* __restrict__ M,
+__global__ void k_geometry_internal(TreeView t, int L, double* __restrict__ M,
                                     double* __restrict__ S, double* __restrict__ zc,
                                     double* __restrict__ r) {
-    const int k = k0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= k1 || t.nchild[k] == 0) return;
+    const int k = t.dls[L] + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= t.dls[L + 1] || t.nchild[k] == 0) return;
     const int c0 = t.first_child[k], c1 = c0 + t.nchild[k];
     double Mk = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
     for (int c = c0; c < c1; ++c) {
@@ -439,7 +447,7 @@ void tree_build_emit(TreeBuffers& b, cudaStream_t st) {
     const int64_t cells = (int64_t)(kMaxLevel + 1) * nchunks;
     (k_level_emit<<<blocks_for(nchunks, 128), 128, 0, st>>>(b.lcp, b.hi, n, nchunks, b.chunk_cnt,
                                                            b.level, b.begin, b.node_cap, &b.ds->err), note_launch());
-    (k_level_starts<<<1, 32, 0, st>>>(b.chunk_cnt, nchunks, b.chunk_cnt + cells, b.ds), note_launch());
+    (k_level_starts<<<1, 32, 0, st>>>(b.chunk_cnt, nchunks, b.chunk_cnt + cells, (int)b.node_cap, b.ds), note_launch());
 }
 
 void tree_build_phase2(TreeBuffers& b, const uint64_t* keys, int nnodes, const int* h_level_start,
@@ -455,12 +463,11 @@ void tree_build_phase2(TreeBuffers& b, const uint64_t* keys, int nnodes, const i
 void cell_geometry(const TreeView& t, const double* xs, const double* ys, const double* zs,
                    const double* ms, const int* h_level_start, double* M, double* S, double* zc,
                    double* r, cudaStream_t st) {
+    (void)h_level_start;
     (k_geometry_leaves<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, xs, ys, zs, ms, M, S, zc, r), note_launch());
-    for (int L = t.nlevels - 2; L >= 0; --L) {
-        const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
-        if (k1 > k0)
-            (k_geometry_internal<<<blocks_for(k1 - k0, 128), 128, 0, st>>>(t, k0, k1, M, S, zc, r), note_launch());
-    }
+    for (int L = t.nlevels - 2; L >= 0; --L)
+        if (t.lvl_cnt[L] > 0)
+            (k_geometry_internal<<<blocks_for(t.lvl_cnt[L], 128), 128, 0, st>>>(t, L, M, S, zc, r), note_launch());
 }
 
 }  // namespace gbfmm

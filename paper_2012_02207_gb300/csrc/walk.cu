@@ -214,20 +214,26 @@ __global__ void __launch_bounds__(256) k_walk_step(WalkCells c, const int2* __re
 }
 
 // the walk starts from the self pair (root, root) of every tree of the forest
-__global__ void k_walk_init(int2* f0, int nroots, unsigned long long* cnt, unsigned long long* list_cnt,
-                            int iters, int mode) {
+__global__ void k_walk_init(int2* f0, const int* __restrict__ dls, unsigned long long* cnt,
+                            unsigned long long* list_cnt, int iters, int mode) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nroots = dls[1];  // the nodes of level 0
     if (i < nroots) f0[i] = make_int2(i, i);
     if (i < iters) cnt[i] = (i == 0) ? (unsigned long long)nroots : 0ull;
     if (i < 2) list_cnt[2 * mode + i] = 0ull;
 }
 
 // directed keys target << nb | source
-__global__ void k_directed(const int2* __restrict__ pairs, int64_t np, int nb,
-                           uint64_t* __restrict__ keys, unsigned long long* count) {
+// (pairs past the device count *np, up to the grid's npcap, become two
+// markers: a list read back by the host has npcap == *np)
+__global__ void k_directed(const int2* __restrict__ pairs, const unsigned long long* __restrict__ np,
+                           int64_t npcap, int nb, uint64_t* __restrict__ keys, unsigned long long* count,
+                           unsigned long long* nkeys) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // two slots per pair; self pairs fill one and leave a marker the sort drops
-    if (q >= np) return;
+    const int64_t npr = (int64_t)*np < npcap ? (int64_t)*np : npcap;
+    if (q == 0) *nkeys = 2ull * (unsigned long long)npr;
+    // two slots per pair; self pairs fill one and leave a marker that sorts last
+    if (q >= npr) return;
     const int2 pr = pairs[q];
     const uint64_t a = (uint64_t)pr.x, b = (uint64_t)pr.y;
     keys[2 * q] = (b << nb) | a;
@@ -236,10 +242,13 @@ __global__ void k_directed(const int2* __restrict__ pairs, int64_t np, int nb,
 }
 
 // 32-bit form of k_directed (when 2 nb <= 32): marker 0xffffffff
-__global__ void k_directed32(const int2* __restrict__ pairs, int64_t np, int nb,
-                             uint32_t* __restrict__ keys, unsigned long long* count) {
+__global__ void k_directed32(const int2* __restrict__ pairs, const unsigned long long* __restrict__ np,
+                             int64_t npcap, int nb, uint32_t* __restrict__ keys, unsigned long long* count,
+                             unsigned long long* nkeys) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= np) return;
+    const int64_t npr = (int64_t)*np < npcap ? (int64_t)*np : npcap;
+    if (q == 0) *nkeys = 2ull * (unsigned long long)npr;
+    if (q >= npr) return;
     const int2 pr = pairs[q];
     const uint32_t a = (uint32_t)pr.x, b = (uint32_t)pr.y;
     keys[2 * q] = (b << nb) | a;
@@ -248,10 +257,13 @@ __global__ void k_directed32(const int2* __restrict__ pairs, int64_t np, int nb,
 }
 
 // sorted 32-bit keys -> the 64-bit keys the consumers read, and the CSR offsets
-__global__ void k_offsets_widen(const uint32_t* __restrict__ k32, int64_t nk, int nb, int nnodes,
+__global__ void k_offsets_widen(const uint32_t* __restrict__ k32, int64_t nk,
+                                const unsigned long long* __restrict__ dnk, int nb, const int* __restrict__ dnn,
                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ off) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int64_t)*dnk < nk) nk = (int64_t)*dnk;
     if (i > nk) return;
+    const int nnodes = *dnn;
     const uint32_t k = i < nk ? k32[i] : 0xffffffffu;
     if (i < nk) keys[i] = k == 0xffffffffu ? ~0ull : (uint64_t)k;
     int64_t t = (i < nk) ? (int64_t)(k >> nb) : (int64_t)nnodes;
@@ -261,10 +273,12 @@ __global__ void k_offsets_widen(const uint32_t* __restrict__ k32, int64_t nk, in
     for (int64_t u = tp + 1; u <= t && u <= nnodes; ++u) off[u] = (uint32_t)i;
 }
 
-__global__ void k_offsets(const uint64_t* __restrict__ keys, int64_t nk, int nb, int nnodes,
-                          uint32_t* __restrict__ off) {
+__global__ void k_offsets(const uint64_t* __restrict__ keys, int64_t nk, const unsigned long long* __restrict__ dnk,
+                          int nb, const int* __restrict__ dnn, uint32_t* __restrict__ off) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int64_t)*dnk < nk) nk = (int64_t)*dnk;
     if (i > nk) return;
+    const int nnodes = *dnn;
     // marker keys (all ones, from self pairs) sort last and count as "past the end"
     int64_t t = (i < nk) ? (int64_t)(keys[i] >> nb) : (int64_t)nnodes;
     int64_t tp = (i > 0) ? (int64_t)(keys[i - 1] >> nb) : -1;
@@ -275,11 +289,11 @@ __global__ void k_offsets(const uint64_t* __restrict__ keys, int64_t nk, int nb,
 
 // far part of the estimate: per cell, M_A / r^2 summed over theta-partners in
 // ascending order, r^2 from the FP32-rounded centre offsets.
-__global__ void k_far_f(int nnodes, const double* __restrict__ zc, const double* __restrict__ M,
+__global__ void k_far_f(const int* __restrict__ dnn, const double* __restrict__ zc, const double* __restrict__ M,
                         const uint64_t* __restrict__ keys, const uint32_t* __restrict__ off, int nb,
                         float* __restrict__ farf) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nnodes) return;
+    if (b >= *dnn) return;
     const uint64_t mask = (1ull << nb) - 1ull;
     const double bx = zc[3 * b], by = zc[3 * b + 1], bz = zc[3 * b + 2];
     float acc = 0.0f;
@@ -296,7 +310,7 @@ __global__ void k_far_f(int nnodes, const double* __restrict__ zc, const double*
 // g(k) = g(parent) + far(k), accumulated from the root down the ancestor chain
 __global__ void k_push_down(TreeView t, const float* __restrict__ farf, float* __restrict__ g) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= t.nnodes) return;
+    if (k >= *t.dnn) return;
     int chain[kMaxLevel + 1];
     int len = 0;
     for (int a = k; a >= 0; a = t.parent[a]) chain[len++] = a;
@@ -331,7 +345,7 @@ __global__ void k_near_f(TreeView t, const float4* __restrict__ xf, const uint64
 
 __global__ void k_leaf_of(TreeView t, int* __restrict__ leaf_of) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= t.nnodes || t.nchild[k] != 0) return;
+    if (k >= *t.dnn || t.nchild[k] != 0) return;
     for (int i = t.begin[k]; i < t.end[k]; ++i) leaf_of[i] = k;
 }
 
@@ -339,16 +353,16 @@ __global__ void k_leaf_of(TreeView t, int* __restrict__ leaf_of) {
 // (a minimum, so the order does not matter)
 __global__ void k_fmin_leaves(TreeView t, const float* __restrict__ f, float* __restrict__ fmin) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= t.nnodes || t.nchild[k] != 0) return;
+    if (k >= *t.dnn || t.nchild[k] != 0) return;
     const int b = t.begin[k], e = t.end[k];
     float mn = f[b];
     for (int i = b + 1; i < e; ++i) mn = f[i] < mn ? f[i] : mn;
     fmin[k] = mn;
 }
 
-__global__ void k_fmin_internal(TreeView t, int k0, int k1, float* __restrict__ fmin) {
-    const int k = k0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= k1 || t.nchild[k] == 0) return;
+__global__ void k_fmin_internal(TreeView t, int L, float* __restrict__ fmin) {
+    const int k = t.dls[L] + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= t.dls[L + 1] || t.nchild[k] == 0) return;
     const int c0 = t.first_child[k], c1 = c0 + t.nchild[k];
     float mn = fmin[c0];
     for (int c = c0 + 1; c < c1; ++c) mn = fmin[c] < mn ? fmin[c] : mn;
@@ -361,11 +375,11 @@ inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) /
 int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* r, const double* P,
                    const float* fmin, int p, double eps, const double* binom_row, const float4* zhi,
                    const float4* zlo, const float* r32, const float* Phat, WalkBuffers& wb,
-                   DevScalars* ds, DevScalars* h_ds, cudaStream_t st) {
+                   DevScalars* ds, DevScalars* h_ds, int fixed_iters, cudaStream_t st) {
     WalkCells c{t.nnodes, t.nchild, t.first_child, zc, r, P, fmin, binom_row, p, eps, zhi, zlo, r32, Phat};
     const int nroots = t.nroots;
     const int ninit = nroots > kMaxWalkIters + 2 ? nroots : kMaxWalkIters + 2;
-    (k_walk_init<<<blocks_for(ninit, 256), 256, 0, st>>>(wb.front0, nroots, ds->cnt, ds->list_cnt,
+    (k_walk_init<<<blocks_for(ninit, 256), 256, 0, st>>>(wb.front0, t.dls, ds->cnt, ds->list_cnt,
                                                           kMaxWalkIters + 2, mode), note_launch());
     int2* acc_list = wb.out[mode == 0 ? 0 : 2];
     int2* leaf_list = wb.out[mode == 0 ? 1 : 3];
@@ -374,6 +388,26 @@ int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* 
     unsigned long long* cnt_acc = ds->list_cnt + (mode == 0 ? 0 : 2);
     unsigned long long* cnt_leaf = ds->list_cnt + (mode == 0 ? 1 : 3);
     const int grid = 152 * 8;
+    if (fixed_iters > 0) {
+        // a planned number of steps with no read-back (a captured solve): steps
+        // past the end of the walk find an empty frontier and return at once;
+        // an overflow or a walk longer than planned shows in ds->err and in
+        // the count of the step after the last
+        const int nit = fixed_iters < kMaxWalkIters ? fixed_iters : kMaxWalkIters;
+        for (int it = 0; it < nit; ++it) {
+            int2* fi = (it & 1) ? wb.front1 : wb.front0;
+            int2* fo = (it & 1) ? wb.front0 : wb.front1;
+            if (mode == 0)
+                (k_walk_step<0><<<grid, 256, 0, st>>>(c, fi, ds->cnt + it, fo, ds->cnt + it + 1, wb.front_cap,
+                                                     acc_list, cnt_acc, cap_acc, leaf_list, cnt_leaf, cap_leaf,
+                                                     &ds->err), note_launch());
+            else
+                (k_walk_step<1><<<grid, 256, 0, st>>>(c, fi, ds->cnt + it, fo, ds->cnt + it + 1, wb.front_cap,
+                                                     acc_list, cnt_acc, cap_acc, leaf_list, cnt_leaf, cap_leaf,
+                                                     &ds->err), note_launch());
+        }
+        return nit;
+    }
     int it = 0;
     const int kCheck = 6;
     while (it < kMaxWalkIters) {
@@ -404,24 +438,34 @@ int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* 
     return it;
 }
 
-void pairs_to_directed(const int2* pairs, int64_t npairs, int nb, uint64_t* keys,
-                       unsigned long long* count, cudaStream_t st) {
-    if (npairs > 0) (k_directed<<<blocks_for(npairs, 256), 256, 0, st>>>(pairs, npairs, nb, keys, count), note_launch());
+__global__ void k_walk_check(DevScalars* ds, int nit) {
+    if (threadIdx.x == 0 && ds->cnt[nit] != 0) atomicOr(&ds->err, kErrCapacity);
 }
 
-void pairs_to_directed32(const int2* pairs, int64_t npairs, int nb, uint32_t* keys,
-                         unsigned long long* count, cudaStream_t st) {
-    if (npairs > 0) (k_directed32<<<blocks_for(npairs, 256), 256, 0, st>>>(pairs, npairs, nb, keys, count), note_launch());
+void walk_check_finished(DevScalars* ds, int nit, cudaStream_t st) {
+    (k_walk_check<<<1, 32, 0, st>>>(ds, nit), note_launch());
 }
 
-void directed_offsets_widen(const uint32_t* k32, int64_t nkeys, int nb, int nnodes, uint64_t* keys,
-                            uint32_t* off, cudaStream_t st) {
-    (k_offsets_widen<<<blocks_for(nkeys + 1, 256), 256, 0, st>>>(k32, nkeys, nb, nnodes, keys, off), note_launch());
+void pairs_to_directed(const int2* pairs, const unsigned long long* np, int64_t npcap, int nb, uint64_t* keys,
+                       unsigned long long* count, unsigned long long* nkeys, cudaStream_t st) {
+    (k_directed<<<blocks_for(npcap > 0 ? npcap : 1, 256), 256, 0, st>>>(pairs, np, npcap, nb, keys, count, nkeys),
+     note_launch());
 }
 
-void directed_offsets(const uint64_t* keys, int64_t nkeys, int nb, int nnodes, uint32_t* off,
-                      cudaStream_t st) {
-    (k_offsets<<<blocks_for(nkeys + 1, 256), 256, 0, st>>>(keys, nkeys, nb, nnodes, off), note_launch());
+void pairs_to_directed32(const int2* pairs, const unsigned long long* np, int64_t npcap, int nb, uint32_t* keys,
+                         unsigned long long* count, unsigned long long* nkeys, cudaStream_t st) {
+    (k_directed32<<<blocks_for(npcap > 0 ? npcap : 1, 256), 256, 0, st>>>(pairs, np, npcap, nb, keys, count, nkeys),
+     note_launch());
+}
+
+void directed_offsets_widen(const uint32_t* k32, int64_t nkeys, const unsigned long long* dnk, int nb,
+                            const int* dnn, uint64_t* keys, uint32_t* off, cudaStream_t st) {
+    (k_offsets_widen<<<blocks_for(nkeys + 1, 256), 256, 0, st>>>(k32, nkeys, dnk, nb, dnn, keys, off), note_launch());
+}
+
+void directed_offsets(const uint64_t* keys, int64_t nkeys, const unsigned long long* dnk, int nb, const int* dnn,
+                      uint32_t* off, cudaStream_t st) {
+    (k_offsets<<<blocks_for(nkeys + 1, 256), 256, 0, st>>>(keys, nkeys, dnk, nb, dnn, off), note_launch());
 }
 
 void scalar_force(const TreeView& t, const double* zc, const double* M, const float4* xf,
@@ -432,15 +476,14 @@ void scalar_force(const TreeView& t, const double* zc, const double* M, const fl
     // and the leaf index of every body after that.
     float* g = farf + t.nnodes;
     int* leaf_of = reinterpret_cast<int*>(farf + 2 * (size_t)t.nnodes);
-    (k_far_f<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.nnodes, zc, M, far_keys, far_off, nb, farf), note_launch());
+    (k_far_f<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.dnn, zc, M, far_keys, far_off, nb, farf), note_launch());
     (k_push_down<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, farf, g), note_launch());
     (k_leaf_of<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, leaf_of), note_launch());
     (k_near_f<<<blocks_for(t.n, 128), 128, 0, st>>>(t, xf, near_keys, near_off, nb, leaf_of, g, f), note_launch());
     (k_fmin_leaves<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, f, fmin), note_launch());
-    for (int L = t.nlevels - 2; L >= 0; --L) {
-        const int k0 = h_level_start[L], k1 = h_level_start[L + 1];
-        if (k1 > k0) (k_fmin_internal<<<blocks_for(k1 - k0, 128), 128, 0, st>>>(t, k0, k1, fmin), note_launch());
-    }
+    (void)h_level_start;
+    for (int L = t.nlevels - 2; L >= 0; --L)
+        if (t.lvl_cnt[L] > 0) (k_fmin_internal<<<blocks_for(t.lvl_cnt[L], 128), 128, 0, st>>>(t, L, fmin), note_launch());
 }
 
 }  // namespace gbfmm
