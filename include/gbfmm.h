@@ -12,7 +12,8 @@
  * Problem (Sec. 2.3, Sec. 3.1.1): given N bodies with positions x_i and masses
  * m_i, compute a_i = G sum_{j != i} m_j (x_j - x_i)/|x_j - x_i|^3 and
  * phi_i = -G sum_{j != i} m_j/|x_j - x_i|, approximately, with the expansion
- * order p and the tolerance eps of the MAC. No softening.
+ * order p and the tolerance eps of the MAC. Optionally with Plummer softening
+ * (Appendix B): |x_j - x_i|^2 -> |x_j - x_i|^2 + soft^2 in both sums.
  *
  * Conventions for every call:
  *  - All array arguments of fmm_solve/fmm_solve_batch are DEVICE pointers
@@ -66,6 +67,13 @@ typedef struct {
     unsigned flags;        /* reserved, 0 */
     unsigned fault_inject; /* test hook, 0 in production: bit 0 forces tiny list capacities
                               so the capacity-regrow path runs */
+    double soft;           /* Plummer softening length eps_soft >= 0 (Appendix B; 0: Newtonian).
+                              P2P, fmm_direct and the near part of the scalar-force estimate
+                              use the softened kernel; the far field stays the expansion of
+                              1/r, and the MAC adds the bound 1.5 M_A soft^2 / d_min^4
+                              (d_min = r - r_A - r_B) on what that leaves out, so accepted
+                              pairs keep the error within eps. Coincident bodies are still
+                              rejected (the octree cannot separate them). */
 } fmm_config;
 
 typedef struct {

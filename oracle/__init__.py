@@ -49,7 +49,7 @@ def lib():
             dp = ctypes.POINTER(ctypes.c_double)
             L.orc_run.restype = ctypes.c_void_p
             L.orc_run.argtypes = [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_int, ctypes.c_double,
-                                  ctypes.c_int, ctypes.c_double, ctypes.c_int]
+                                  ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
             L.orc_free.argtypes = [ctypes.c_void_p]
             L.orc_status.argtypes = [ctypes.c_void_p]
             L.orc_nnodes.argtypes = [ctypes.c_void_p]
@@ -71,8 +71,8 @@ def lib():
                                   ctypes.c_double, dp, dp, dp, dp]
             L.orc_eval_multipole.argtypes = [ctypes.c_int, ctypes.c_void_p] + [ctypes.c_double] * 6
             L.orc_eval_multipole.restype = ctypes.c_double
-            L.orc_direct.argtypes = [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_double, ctypes.c_int64,
-                                     ctypes.POINTER(ctypes.c_int64), dp, dp, dp, dp]
+            L.orc_direct.argtypes = [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), dp, dp, dp, dp]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_mac_values.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, dp]
             _lib = L
@@ -153,8 +153,9 @@ def eval_multipole(p, M, center, x):
 
 # -------------------------------------------------------------- direct sum
 
-def direct(pos, mass, G=1.0, targets=None):
-    """FP64 O(N^2) accelerations (N,3) and potentials (N,) at the targets."""
+def direct(pos, mass, G=1.0, targets=None, soft=0.0):
+    """FP64 O(N^2) accelerations (N,3) and potentials (N,) at the targets
+    (Plummer-softened with length soft > 0, Appendix B)."""
     pos = _c(pos)
     x, y, z = (np.ascontiguousarray(pos[:, d]) for d in range(3))
     m = _c(mass)
@@ -165,7 +166,8 @@ def direct(pos, mass, G=1.0, targets=None):
         tg = np.ascontiguousarray(targets, dtype=np.int64)
         nt, tp = len(tg), tg.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     ax, ay, az, pot = (np.zeros(nt) for _ in range(4))
-    lib().orc_direct(n, _dp(x), _dp(y), _dp(z), _dp(m), G, nt, tp, _dp(ax), _dp(ay), _dp(az), _dp(pot))
+    lib().orc_direct(n, _dp(x), _dp(y), _dp(z), _dp(m), G, float(soft), nt, tp, _dp(ax), _dp(ay), _dp(az),
+                     _dp(pot))
     return np.stack([ax, ay, az], axis=1), pot
 
 
@@ -177,15 +179,16 @@ STAGE_TREE, STAGE_F, STAGE_LISTS, STAGE_FULL = 1, 2, 3, 4
 class OracleRun:
     """Result of one oracle solve; every intermediate is kept."""
 
-    def __init__(self, pos, mass, p=8, eps=1e-7, leaf_size=64, G=1.0, stage=STAGE_FULL):
+    def __init__(self, pos, mass, p=8, eps=1e-7, leaf_size=64, G=1.0, stage=STAGE_FULL, soft=0.0):
         pos = _c(pos)
         self._x, self._y, self._z = (np.ascontiguousarray(pos[:, d]) for d in range(3))
         self._m = _c(mass)
         self.n = len(self._m)
         self.p, self.eps, self.leaf_size, self.G, self.stage = p, eps, leaf_size, G, stage
+        self.soft = float(soft)
         L = lib()
         self._h = L.orc_run(self.n, _dp(self._x), _dp(self._y), _dp(self._z), _dp(self._m),
-                            p, eps, leaf_size, G, stage)
+                            p, eps, leaf_size, G, self.soft, stage)
         self.status = L.orc_status(self._h)
         self.nnodes = L.orc_nnodes(self._h)
         self.nlevels = L.orc_nlevels(self._h)
@@ -245,8 +248,9 @@ class OracleRun:
         return self._get(code, np.int32, (self.npairs(which), 2))
 
     def mac_values(self, a, b):
-        """(E_AB M_A/r^2, E_BA M_B/r^2, eps f_B, eps f_A, theta test) of Sec. 2.3."""
-        out = np.zeros(5)
+        """(E_AB M_A/r^2, E_BA M_B/r^2, eps f_B, eps f_A, theta test) of Sec. 2.3, then the
+        softening bounds A->B and B->A (0 without softening)."""
+        out = np.zeros(7)
         lib().orc_mac_values(self._h, int(a), int(b), _dp(out))
         return out
 
@@ -255,9 +259,9 @@ class OracleRun:
         return acc, self._get(23, np.float64, self.n)
 
 
-def fmm(pos, mass, p=8, eps=1e-7, leaf_size=64, G=1.0):
+def fmm(pos, mass, p=8, eps=1e-7, leaf_size=64, G=1.0, soft=0.0):
     """Accelerations (N,3) and potentials (N,) from the oracle FMM."""
-    run = OracleRun(pos, mass, p=p, eps=eps, leaf_size=leaf_size, G=G, stage=STAGE_FULL)
+    run = OracleRun(pos, mass, p=p, eps=eps, leaf_size=leaf_size, G=G, stage=STAGE_FULL, soft=soft)
     if run.status != 0:
         raise RuntimeError(f"oracle status {run.status}")
     return run.forces()

@@ -30,6 +30,16 @@
  * The M2L here is the plain O(p^4) translation (the definition that the
  * rotation-accelerated form of Sec. 2.4 reproduces exactly), not the rotated
  * form.
+ *
+ * Plummer softening (Appendix B: phi(r) = -G m / sqrt(r^2 + eps_soft^2)).
+ * The paper gives only the kernel; the reading here (R17 of the design notes):
+ *  - the direct sum, P2P and the near part of f use the softened kernel;
+ *  - the far field stays the multipole expansion of 1/r;
+ *  - the MAC adds, on each side, the bound of what that omits: for bodies
+ *    at distance d >= d_min = r - r_A - r_B, the softened and Newtonian
+ *    accelerations of a body of mass m differ by at most 1.5 m eps_soft^2 /
+ *    d^4, so a cell of mass M_A differs by at most 1.5 M_A eps_soft^2 / d_min^4;
+ *  - eps_soft = 0 takes none of these branches (the Newtonian solve).
  */
 #include <math.h>
 #include <stdint.h>
@@ -252,10 +262,13 @@ double orc_eval_multipole(int p, const cplx* M, double cx, double cy, double cz,
 
 /* Plain O(N^2) FP64 sum over all j != i (the quantity the FMM approximates,
  * Sec. 2.3 and Sec. 3.1.1): a_i = G sum m_j (x_j - x_i)/|x_j - x_i|^3,
- * phi_i = -G sum m_j / |x_j - x_i|. Targets are the index list tgt. */
+ * phi_i = -G sum m_j / |x_j - x_i|. Targets are the index list tgt. With
+ * soft > 0 the kernel is Plummer-softened (Appendix B): |x_j - x_i|^2
+ * becomes |x_j - x_i|^2 + soft^2 in both sums. */
 void orc_direct(int64_t n, const double* x, const double* y, const double* z,
-                const double* m, double G, int64_t ntgt, const int64_t* tgt,
+                const double* m, double G, double soft, int64_t ntgt, const int64_t* tgt,
                 double* ax, double* ay, double* az, double* pot) {
+    const double soft2 = soft * soft;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < ntgt; ++t) {
         int64_t i = tgt ? tgt[t] : t;
@@ -264,6 +277,7 @@ void orc_direct(int64_t n, const double* x, const double* y, const double* z,
             if (j == i) continue;
             double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
             double r2 = dx * dx + dy * dy + dz * dz;
+            if (soft2 > 0.0) r2 = r2 + soft2;
             double r = sqrt(r2);
             double mr3 = m[j] / (r2 * r);
             sx += mr3 * dx; sy += mr3 * dy; sz += mr3 * dz;
@@ -278,6 +292,7 @@ void orc_direct(int64_t n, const double* x, const double* y, const double* z,
 typedef struct {
     /* inputs */
     int64_t n; int p; int leaf_size; double eps; double G;
+    double soft2;  /* squared Plummer softening length (0: Newtonian) */
     int stage;   /* 1: tree; 2: + geometry, multipoles, f; 3: + lists; 4: full */
     int status;  /* 0 ok, -5 coincident particles */
     /* box and tree */
@@ -550,15 +565,28 @@ static inline double mac_lhs(const orc_state* s, int32_t a, int32_t b, double r2
     return pre * h / (rp * r2);
 }
 
+/* Bound on the softening the far field leaves out (reading R17):
+ * 1.5 M_A soft^2 / d_min^4, d_min = r - r_A - r_B (> 0 once theta < 1). */
+static inline double soft_bound(const orc_state* s, int32_t a, int32_t b, double r) {
+    double dmin = r - s->r[a] - s->r[b];
+    double d2 = dmin * dmin;
+    return 1.5 * s->M[a] * s->soft2 / (d2 * d2);
+}
+
 /* Full MAC of Sec. 2.3:
  * theta < 1 and E_{A->B} M_A/r^2 < eps f_B and E_{B->A} M_B/r^2 < eps f_A,
- * with f_A the minimum scalar force over the particles of A. */
+ * with f_A the minimum scalar force over the particles of A. With softening
+ * each left side also carries soft_bound. */
 static int mac_eps(orc_state* s, int32_t a, int32_t b) {
     double r2, r;
     s->mac_tests += 1.0;
     if (!theta_ok(s, a, b, &r2, &r)) return 0;
     double lab = mac_lhs(s, a, b, r2, r);
     double lba = mac_lhs(s, b, a, r2, r);
+    if (s->soft2 > 0.0) {
+        lab = lab + soft_bound(s, a, b, r);
+        lba = lba + soft_bound(s, b, a, r);
+    }
     return lab < s->eps * (double)s->fmin[b] && lba < s->eps * (double)s->fmin[a];
 }
 
@@ -645,7 +673,8 @@ static void partner_csr(int32_t nnodes, int64_t npairs, const int32_t* pairs,
  *  - these far terms are pushed down: g(child) = g(parent) + far(child);
  *  - near leaf pairs are summed particle by particle over partner leaves in
  *    ascending order and their particles in sorted order, skipping j = i,
- *    on FP32 coordinates relative to the cube centre;
+ *    on FP32 coordinates relative to the cube centre; with softening the
+ *    term is the softened force magnitude m r / (r^2 + soft^2)^(3/2);
  *  - f_i = g(leaf) + near_i, and fmin(A) = min over the particles of A.
  * G cancels from both sides of the MAC and is left out. */
 static void scalar_force(orc_state* s) {
@@ -678,6 +707,7 @@ static void scalar_force(orc_state* s) {
         xf[4 * i + 3] = (float)s->ms[i];
     }
     partner_csr(nn, s->nnear, s->near, &off, &idx);
+    const float soft2f = (float)s->soft2;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int32_t b = 0; b < nn; ++b) {
         if (!is_leaf(s, b)) continue;
@@ -690,7 +720,13 @@ static void scalar_force(orc_state* s) {
                     if (j == i) continue;
                     float dx = xf[4 * j] - xi, dy = xf[4 * j + 1] - yi, dz = xf[4 * j + 2] - zi;
                     float r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 > 0.0f) acc = acc + xf[4 * j + 3] / r2;
+                    if (!(r2 > 0.0f)) continue;
+                    if (soft2f > 0.0f) {
+                        float s2 = r2 + soft2f;
+                        acc = acc + xf[4 * j + 3] * sqrtf(r2) / (s2 * sqrtf(s2));
+                    } else {
+                        acc = acc + xf[4 * j + 3] / r2;
+                    }
                 }
             }
             s->f[i] = g[b] + acc;
@@ -716,7 +752,7 @@ static void scalar_force(orc_state* s) {
 
 /* Far field: M2L both ways for every accepted pair (reading R11), gathered
  * per target; L2L down; L2P per particle. Near field: P2P over leaf pairs,
- * both directions, and within a leaf over j != i. */
+ * both directions, and within a leaf over j != i, softened when soft > 0. */
 static void forces(orc_state* s) {
     int p = s->p, nc = ncoef(p);
     int32_t nn = s->nnodes;
@@ -765,6 +801,7 @@ static void forces(orc_state* s) {
                     if (j == i) continue;
                     double dx = s->xs[j] - s->xs[i], dy = s->ys[j] - s->ys[i], dz = s->zs[j] - s->zs[i];
                     double r2 = dx * dx + dy * dy + dz * dz;
+                    if (s->soft2 > 0.0) r2 = r2 + s->soft2;
                     double r = sqrt(r2);
                     double mr3 = s->ms[j] / (r2 * r);
                     sx += mr3 * dx; sy += mr3 * dy; sz += mr3 * dz;
@@ -789,10 +826,11 @@ void orc_free(orc_state* s);
 
 /* Run the solve up to `stage` and keep every intermediate for inspection. */
 orc_state* orc_run(int64_t n, const double* x, const double* y, const double* z, const double* m,
-                   int p, double eps, int leaf_size, double G, int stage) {
+                   int p, double eps, int leaf_size, double G, double soft, int stage) {
     init_tables();
     orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
     s->n = n; s->p = p; s->leaf_size = leaf_size; s->eps = eps; s->G = G; s->stage = stage;
+    s->soft2 = soft * soft;
     if (n < 1 || p < 1 || p > ORC_MAXP || leaf_size < 1) { s->status = -1; return s; }
     s->keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n);
     s->perm = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
@@ -909,7 +947,9 @@ int orc_num_threads(void) {
 }
 
 /* The two sides of the MAC for a pair of cells: out = {E_{A->B} M_A/r^2,
- * E_{B->A} M_B/r^2, eps f_B, eps f_A, theta-test passed}. */
+ * E_{B->A} M_B/r^2, eps f_B, eps f_A, theta-test passed, softening bound
+ * A->B, softening bound B->A} (the bounds are 0 without softening or when
+ * the theta test fails). */
 void orc_mac_values(orc_state* s, int32_t a, int32_t b, double* out) {
     double r2, r;
     int ok = theta_ok(s, a, b, &r2, &r);
@@ -918,4 +958,6 @@ void orc_mac_values(orc_state* s, int32_t a, int32_t b, double* out) {
     out[2] = s->eps * (double)s->fmin[b];
     out[3] = s->eps * (double)s->fmin[a];
     out[4] = (double)ok;
+    out[5] = (ok && s->soft2 > 0.0) ? soft_bound(s, a, b, r) : 0.0;
+    out[6] = (ok && s->soft2 > 0.0) ? soft_bound(s, b, a, r) : 0.0;
 }

@@ -35,7 +35,7 @@ class FmmError(RuntimeError):
 class _Config(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("eps", ctypes.c_double), ("leaf_size", ctypes.c_int),
                 ("precision", ctypes.c_int), ("G", ctypes.c_double), ("flags", ctypes.c_uint),
-                ("fault_inject", ctypes.c_uint)]
+                ("fault_inject", ctypes.c_uint), ("soft", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -109,16 +109,17 @@ class Config:
     precision: int = FMM_PRECISION_MIXED
     G: float = 1.0
     fault_inject: int = 0
+    soft: float = 0.0
 
 
 class FMM:
     """One solver context (fmm_create/fmm_destroy) on the current CUDA device."""
 
-    def __init__(self, p=8, eps=1e-7, leaf_size=64, precision="mixed", G=1.0, fault_inject=0):
+    def __init__(self, p=8, eps=1e-7, leaf_size=64, precision="mixed", G=1.0, fault_inject=0, soft=0.0):
         if isinstance(precision, str):
             precision = {"fp64": FMM_PRECISION_FP64, "mixed": FMM_PRECISION_MIXED}[precision]
-        self.config = Config(p, eps, leaf_size, precision, G, fault_inject)
-        cfg = _Config(p, eps, leaf_size, precision, G, 0, fault_inject)
+        self.config = Config(p, eps, leaf_size, precision, G, fault_inject, soft)
+        cfg = _Config(p, eps, leaf_size, precision, G, 0, fault_inject, soft)
         h = ctypes.c_void_p()
         rc = lib().fmm_create(ctypes.byref(h), ctypes.byref(cfg))
         if rc != 0:

@@ -286,8 +286,8 @@ int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
         }
         dual_tree_walk(mode, t, as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->Pk),
                        as<float>(ctx->fmin), p, ctx->cfg.eps, binom_row0, as<float4>(ctx->zhi),
-                       as<float4>(ctx->zlo), as<float>(ctx->r32), as<float>(ctx->Phat), wb,
-                       ctx->ds, ctx->h_ds, g->walk_iters[mode], st);
+                       as<float4>(ctx->zlo), as<float>(ctx->r32), as<float>(ctx->Phat), as<double>(ctx->M),
+                       ctx->cfg.soft, wb, ctx->ds, ctx->h_ds, g->walk_iters[mode], st);
         walk_check_finished(ctx->ds, g->walk_iters[mode], st);
         CK(cudaGetLastError());
         return FMM_OK;
@@ -311,8 +311,8 @@ int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
         CK(cudaMemsetAsync(&ctx->ds->err, 0, sizeof(unsigned), st));
         const int it = dual_tree_walk(mode, t, as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->Pk),
                                       as<float>(ctx->fmin), p, ctx->cfg.eps, binom_row, as<float4>(ctx->zhi),
-                                      as<float4>(ctx->zlo), as<float>(ctx->r32), as<float>(ctx->Phat), wb,
-                                      ctx->ds, ctx->h_ds, 0, st);
+                                      as<float4>(ctx->zlo), as<float>(ctx->r32), as<float>(ctx->Phat),
+                                      as<double>(ctx->M), ctx->cfg.soft, wb, ctx->ds, ctx->h_ds, 0, st);
         if (it == FMM_ERR_CAPACITY) {
             // the counters kept counting past the capacity: grow to what was asked for
             CK(cudaMemcpyAsync(ctx->h_ds, ctx->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
@@ -500,7 +500,8 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     if ((rc = build_directed(ctx, 0, st)) || (rc = build_directed(ctx, 1, st))) return rc;
     scalar_force(t, as<double>(ctx->zc), as<double>(ctx->M), as<float4>(ctx->xf), as<uint64_t>(ctx->dkeys[0]),
                  as<uint32_t>(ctx->doff[0]), as<uint64_t>(ctx->dkeys[1]), as<uint32_t>(ctx->doff[1]), ctx->nb,
-                 ctx->h_level_start, as<float>(ctx->fscratch), as<float>(ctx->f), as<float>(ctx->fmin), st);
+                 ctx->h_level_start, ctx->cfg.soft, as<float>(ctx->fscratch), as<float>(ctx->f),
+                 as<float>(ctx->fmin), st);
     CK(rec(3));
     // ---- error-controlled walk
     if ((rc = run_walk(ctx, 1, st))) return rc;
@@ -550,6 +551,8 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     leaf_items_fill(t, item_first, as<int>(ctx->item_leaf), htot[0], as<int>(ctx->leaf_of), st);
     LeafArgs la{};
     la.t = t; la.p = p; la.G = ctx->cfg.G;
+    la.soft2 = ctx->cfg.soft * ctx->cfg.soft;
+    la.soft2f = (float)la.soft2;
     la.xs = as<double>(ctx->xs); la.ys = as<double>(ctx->ys); la.zs = as<double>(ctx->zs); la.ms = as<double>(ctx->ms);
     la.zc = as<double>(ctx->zc); la.hs = as<double>(ctx->hs);
     la.zhi = as<float4>(ctx->zhi); la.zlo = as<float4>(ctx->zlo);
@@ -606,6 +609,7 @@ int check_cfg(const fmm_config* c, std::string& why) {
     if (c->precision != FMM_PRECISION_FP64 && c->precision != FMM_PRECISION_MIXED) { why = "unknown precision"; return FMM_ERR_ARG; }
     if (c->precision == FMM_PRECISION_MIXED && c->p > kMaxPF32) { why = "mixed precision supports p <= 16"; return FMM_ERR_ARG; }
     if (!std::isfinite(c->G)) { why = "G must be finite"; return FMM_ERR_ARG; }
+    if (!(c->soft >= 0.0) || !std::isfinite(c->soft)) { why = "soft must be finite and >= 0"; return FMM_ERR_ARG; }
     return FMM_OK;
 }
 
@@ -945,7 +949,7 @@ int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const 
     if (n < 0 || ntargets < 0) return fail(ctx, FMM_ERR_ARG, "negative size");
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    direct_sum_f64(n, x, y, z, m, ctx->cfg.G, targets ? ntargets : n, targets, ax, ay, az, pot, st);
+    direct_sum_f64(n, x, y, z, m, ctx->cfg.G, ctx->cfg.soft, targets ? ntargets : n, targets, ax, ay, az, pot, st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     return FMM_OK;

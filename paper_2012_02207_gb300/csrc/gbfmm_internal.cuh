@@ -181,10 +181,11 @@ struct WalkBuffers {
 // mode 1: the error-controlled MAC (lists m2l/p2p). Returns iterations or a
 // negative fmm_status. Counts land in ds->list_cnt.
 constexpr int kWalkBadIndex = -100;  // dual_tree_walk: a frontier entry out of range
+// M: cell masses, soft: Plummer softening length (0: Newtonian MAC)
 int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* r, const double* P,
                    const float* fmin, int p, double eps, const double* binom_row, const float4* zhi,
-                   const float4* zlo, const float* r32, const float* Phat, WalkBuffers& wb,
-                   DevScalars* ds, DevScalars* h_ds, int fixed_iters, cudaStream_t st);
+                   const float4* zlo, const float* r32, const float* Phat, const double* M, double soft,
+                   WalkBuffers& wb, DevScalars* ds, DevScalars* h_ds, int fixed_iters, cudaStream_t st);
 // a walk run for a planned nit steps must have an empty frontier after them
 // (else kErrCapacity)
 void walk_check_finished(DevScalars* ds, int nit, cudaStream_t st);
@@ -192,8 +193,8 @@ void walk_check_finished(DevScalars* ds, int nit, cudaStream_t st);
 // per-target CSR (sorted directed keys target<<nb | source).
 void scalar_force(const TreeView& t, const double* zc, const double* M, const float4* xf,
                   const uint64_t* far_keys, const uint32_t* far_off, const uint64_t* near_keys,
-                  const uint32_t* near_off, int nb, const int* h_level_start, float* farf, float* f,
-                  float* fmin, cudaStream_t st);
+                  const uint32_t* near_off, int nb, const int* h_level_start, double soft, float* farf,
+                  float* f, float* fmin, cudaStream_t st);
 // directed entries of a pair list: (B<-A) and (A<-B), a self pair once and a
 // marker that sorts last; np: the device count of pairs, npcap >= *np the
 // pairs the grid covers; *nkeys (device) <- 2 min(*np, npcap), the keys written.
@@ -285,6 +286,8 @@ struct LeafArgs {
     const float4* prel;  // leaf-relative FP32 bodies (mixed)
     double2 *part_hi, *part_lo;  // P2P partials: (ax, ay), (az, pot)
     DevTables tb;
+    double soft2;  // squared Plummer softening length (0: Newtonian P2P)
+    float soft2f;  // the same, rounded to FP32 (mixed P2P)
 };
 void leaf_items_plan(const TreeView& t, const uint32_t* p2p_off, uint32_t* item_first, uint32_t* slot_first,
                      uint32_t* totals, cudaStream_t st);
@@ -298,8 +301,9 @@ void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_
                cudaStream_t st);
 void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, const double* zs,
                        const double* ms, const double* zc, float4* prel, cudaStream_t st);
+// soft: Plummer softening length (0: Newtonian)
 void direct_sum_f64(int64_t n, const double* x, const double* y, const double* z, const double* m,
-                    double G, int64_t ntgt, const int64_t* tgt, double* ax, double* ay, double* az,
+                    double G, double soft, int64_t ntgt, const int64_t* tgt, double* ax, double* ay, double* az,
                     double* pot, cudaStream_t st);
 
 }  // namespace gbfmm

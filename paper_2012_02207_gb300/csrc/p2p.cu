@@ -160,9 +160,11 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
     return y;
 }
 
-template <typename T, bool GUARD, int GC>
+// SOFT: Plummer softening (Appendix B), 1/r -> 1/sqrt(r^2 + s2); the body
+// itself (r2 = 0; coincident bodies are rejected) still contributes nothing.
+template <typename T, bool GUARD, int GC, bool SOFT>
 __device__ __forceinline__ void p2p_pack_g(const Body4<T>* __restrict__ sm, int cnt, int sub, int Gr, T tx, T ty,
-                                           T tz, NearAcc<T>& acc) {
+                                           T tz, T s2, NearAcc<T>& acc) {
     const int G = GC > 0 ? GC : Gr;  // lanes per target (compile-time when GC > 0)
     auto term = [&](int k, T& px, T& py, T& pz, T& pp) {
         const Body4<T> sv = sm[k];
@@ -170,10 +172,11 @@ __device__ __forceinline__ void p2p_pack_g(const Body4<T>* __restrict__ sm, int 
         const T r2 = dx * dx + dy * dy + dz * dz;
         T rinv;
         if (sizeof(T) == 4) {
-            rinv = (T)rsqrtf((float)r2);
+            rinv = (T)rsqrtf((float)(SOFT ? r2 + s2 : r2));
             if (GUARD && !(r2 > T(0))) rinv = T(0);  // the body itself
         } else {
-            rinv = (T)rsqrt_nr((double)r2);
+            rinv = (T)rsqrt_nr((double)(SOFT ? r2 + s2 : r2));
+            if (SOFT && GUARD && !(r2 > T(0))) rinv = T(0);
         }
         const T mr = sv.w * rinv;
         const T mr3 = mr * rinv * rinv;
@@ -201,16 +204,16 @@ __device__ __forceinline__ void p2p_pack_g(const Body4<T>* __restrict__ sm, int 
     }
 }
 
-template <typename T, bool GUARD>
+template <typename T, bool GUARD, bool SOFT>
 __device__ __forceinline__ void p2p_pack(const Body4<T>* __restrict__ sm, int cnt, int sub, int G, T tx, T ty,
-                                         T tz, NearAcc<T>& acc) {
-    if (G == 1) p2p_pack_g<T, GUARD, 1>(sm, cnt, sub, G, tx, ty, tz, acc);
-    else if (G == 2) p2p_pack_g<T, GUARD, 2>(sm, cnt, sub, G, tx, ty, tz, acc);
-    else if (G == 4) p2p_pack_g<T, GUARD, 4>(sm, cnt, sub, G, tx, ty, tz, acc);
-    else p2p_pack_g<T, GUARD, 0>(sm, cnt, sub, G, tx, ty, tz, acc);
+                                         T tz, T s2, NearAcc<T>& acc) {
+    if (G == 1) p2p_pack_g<T, GUARD, 1, SOFT>(sm, cnt, sub, G, tx, ty, tz, s2, acc);
+    else if (G == 2) p2p_pack_g<T, GUARD, 2, SOFT>(sm, cnt, sub, G, tx, ty, tz, s2, acc);
+    else if (G == 4) p2p_pack_g<T, GUARD, 4, SOFT>(sm, cnt, sub, G, tx, ty, tz, s2, acc);
+    else p2p_pack_g<T, GUARD, 0, SOFT>(sm, cnt, sub, G, tx, ty, tz, s2, acc);
 }
 
-template <typename T>
+template <typename T, bool SOFT>
 __global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __restrict__ item_leaf,
                                                     const uint32_t* __restrict__ item_first,
                                                     const uint32_t* __restrict__ slot_first,
@@ -293,8 +296,9 @@ __global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __rest
                 }
                 __syncwarp();
                 if (!act) continue;
-                if (selfin) p2p_pack<T, true>(sm, cnt, sub, G, tx, ty, tz, acc);
-                else p2p_pack<T, false>(sm, cnt, sub, G, tx, ty, tz, acc);
+                const T s2 = SOFT ? (sizeof(T) == 4 ? (T)a.soft2f : (T)a.soft2) : T(0);
+                if (selfin) p2p_pack<T, true, SOFT>(sm, cnt, sub, G, tx, ty, tz, s2, acc);
+                else p2p_pack<T, false, SOFT>(sm, cnt, sub, G, tx, ty, tz, s2, acc);
             }
             float &hx = acc.hx, &hy = acc.hy, &hz = acc.hz, &hp = acc.hp;
             float &lx = acc.lx, &ly = acc.ly, &lz = acc.lz, &lp = acc.lp;
@@ -434,9 +438,9 @@ __global__ void k_leaf_relative(TreeView t, const double* __restrict__ xs, const
 __global__ void __launch_bounds__(256) k_direct(int64_t n, const double* __restrict__ x,
                                                 const double* __restrict__ y,
                                                 const double* __restrict__ z,
-                                                const double* __restrict__ m, double G, int64_t ntgt,
-                                                const int64_t* __restrict__ tgt, double* ax, double* ay,
-                                                double* az, double* pot) {
+                                                const double* __restrict__ m, double G, double soft2,
+                                                int64_t ntgt, const int64_t* __restrict__ tgt, double* ax,
+                                                double* ay, double* az, double* pot) {
     __shared__ double4 tile[256];
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = t < ntgt;
@@ -452,7 +456,7 @@ __global__ void __launch_bounds__(256) k_direct(int64_t n, const double* __restr
             if (j0 + k == i) continue;
             const double4 s = tile[k];
             const double dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
-            const double r2 = dx * dx + dy * dy + dz * dz;
+            const double r2 = dx * dx + dy * dy + dz * dz + soft2;  // soft2 = 0: Newtonian
             const double rinv = rsqrt_nr(r2);
             const double mr = s.w * rinv;
             const double mr3 = mr * rinv * rinv;
@@ -516,11 +520,14 @@ void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_
                const uint32_t* slot_first, const uint32_t* nitems, unsigned* work, const int* leaf_of,
                cudaStream_t st) {
     cudaMemsetAsync(work, 0, sizeof(unsigned), st);
+    const bool soft = a.soft2 > 0.0;
     if (fp32) {
-        (k_p2p_items<float><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        if (soft) (k_p2p_items<float, true><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        else (k_p2p_items<float, false><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
         (k_leaf_reduce<float><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch());
     } else {
-        (k_p2p_items<double><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        if (soft) (k_p2p_items<double, true><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        else (k_p2p_items<double, false><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
         (k_leaf_reduce<double><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch());
     }
 }
@@ -531,9 +538,11 @@ void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, co
 }
 
 void direct_sum_f64(int64_t n, const double* x, const double* y, const double* z, const double* m,
-                    double G, int64_t ntgt, const int64_t* tgt, double* ax, double* ay, double* az,
+                    double G, double soft, int64_t ntgt, const int64_t* tgt, double* ax, double* ay, double* az,
                     double* pot, cudaStream_t st) {
-    if (ntgt > 0) (k_direct<<<blocks_for(ntgt, 256), 256, 0, st>>>(n, x, y, z, m, G, ntgt, tgt, ax, ay, az, pot), note_launch());
+    if (ntgt > 0)
+        (k_direct<<<blocks_for(ntgt, 256), 256, 0, st>>>(n, x, y, z, m, G, soft * soft, ntgt, tgt, ax, ay, az, pot),
+         note_launch());
 }
 
 }  // namespace gbfmm

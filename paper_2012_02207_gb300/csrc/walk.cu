@@ -32,6 +32,12 @@ struct WalkCells {
     const float4* zlo;
     const float* r32;
     const float* Phat;
+    // Plummer softening (Appendix B): the MAC adds 1.5 M_A soft^2 / d_min^4,
+    // d_min = r - r_A - r_B, the bound on what the Newtonian far field leaves
+    // out (reading R17); soft2 = 0 skips it
+    const double* M;
+    double soft2;
+    float soft2f;
 };
 
 // Relative margins of the FP32 screen. Its error is below 1e-5 (positive
@@ -152,12 +158,26 @@ __global__ void __launch_bounds__(256) k_walk_step(WalkCells c, const int2* __re
                     accept = theta == 1;
                 }
                 if (MODE == 1 && accept) {
-                    const float lab32 = mac_lhs32(c, a, fra, frb, ah.w, fr, binom32);
-                    const float lba32 = mac_lhs32(c, b, frb, fra, bh.w, fr, binom32);
+                    float lab32 = mac_lhs32(c, a, fra, frb, ah.w, fr, binom32);
+                    float lba32 = mac_lhs32(c, b, frb, fra, bh.w, fr, binom32);
                     const float rb32 = eps32 * c.fmin[b], ra32 = eps32 * c.fmin[a];
-                    if (lab32 < rb32 * (1.0f - kMacMargin) && lba32 < ra32 * (1.0f - kMacMargin)) {
+                    // softening term in FP32 only well inside theta < 1, where
+                    // d_min = r - r_A - r_B > r/4 keeps its relative error near 1e-5
+                    bool screen = true;
+                    if (c.soft2 > 0.0) {
+                        const float dmin32 = fr - fra - frb;
+                        if (dmin32 > 0.25f * fr) {
+                            const float d2 = dmin32 * dmin32;
+                            const float d4 = d2 * d2;
+                            lab32 = lab32 + 1.5f * (float)c.M[a] * c.soft2f / d4;
+                            lba32 = lba32 + 1.5f * (float)c.M[b] * c.soft2f / d4;
+                        } else {
+                            screen = false;
+                        }
+                    }
+                    if (screen && lab32 < rb32 * (1.0f - kMacMargin) && lba32 < ra32 * (1.0f - kMacMargin)) {
                         accept = true;
-                    } else if (lab32 > rb32 * (1.0f + kMacMargin) || lba32 > ra32 * (1.0f + kMacMargin)) {
+                    } else if (screen && (lab32 > rb32 * (1.0f + kMacMargin) || lba32 > ra32 * (1.0f + kMacMargin))) {
                         accept = false;
                     } else {
                         if (!have64) {
@@ -168,8 +188,14 @@ __global__ void __launch_bounds__(256) k_walk_step(WalkCells c, const int2* __re
                             r = sqrt(r2);
                         }
                         const double ra = c.r[a], rb = c.r[b];
-                        const double lab = mac_lhs(c, a, ra, rb, r, r2);
-                        const double lba = mac_lhs(c, b, rb, ra, r, r2);
+                        double lab = mac_lhs(c, a, ra, rb, r, r2);
+                        double lba = mac_lhs(c, b, rb, ra, r, r2);
+                        if (c.soft2 > 0.0) {
+                            const double dab = r - ra - rb, dba = r - rb - ra;
+                            const double qab = dab * dab, qba = dba * dba;
+                            lab = lab + 1.5 * c.M[a] * c.soft2 / (qab * qab);
+                            lba = lba + 1.5 * c.M[b] * c.soft2 / (qba * qba);
+                        }
                         accept = lab < c.eps * (double)c.fmin[b] && lba < c.eps * (double)c.fmin[a];
                     }
                 }
@@ -322,7 +348,7 @@ __global__ void k_push_down(TreeView t, const float* __restrict__ farf, float* _
 // near part per body: partner leaves ascending, their bodies in order, j != i
 __global__ void k_near_f(TreeView t, const float4* __restrict__ xf, const uint64_t* __restrict__ keys,
                          const uint32_t* __restrict__ off, int nb, const int* __restrict__ leaf_of,
-                         const float* __restrict__ g, float* __restrict__ f) {
+                         const float* __restrict__ g, float soft2f, float* __restrict__ f) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= t.n) return;
     const int b = leaf_of[i];
@@ -337,7 +363,14 @@ __global__ void k_near_f(TreeView t, const float4* __restrict__ xf, const uint64
             const float4 pj = xf[j];
             const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 > 0.0f) acc = acc + pj.w / r2;
+            if (!(r2 > 0.0f)) continue;
+            if (soft2f > 0.0f) {
+                // softened magnitude m r / (r^2 + soft^2)^{3/2} (reading R17)
+                const float s2 = r2 + soft2f;
+                acc = acc + pj.w * sqrtf(r2) / (s2 * sqrtf(s2));
+            } else {
+                acc = acc + pj.w / r2;
+            }
         }
     }
     f[i] = g[b] + acc;
@@ -374,9 +407,10 @@ inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) /
 
 int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* r, const double* P,
                    const float* fmin, int p, double eps, const double* binom_row, const float4* zhi,
-                   const float4* zlo, const float* r32, const float* Phat, WalkBuffers& wb,
-                   DevScalars* ds, DevScalars* h_ds, int fixed_iters, cudaStream_t st) {
-    WalkCells c{t.nnodes, t.nchild, t.first_child, zc, r, P, fmin, binom_row, p, eps, zhi, zlo, r32, Phat};
+                   const float4* zlo, const float* r32, const float* Phat, const double* M, double soft,
+                   WalkBuffers& wb, DevScalars* ds, DevScalars* h_ds, int fixed_iters, cudaStream_t st) {
+    WalkCells c{t.nnodes, t.nchild, t.first_child, zc, r, P, fmin, binom_row, p, eps, zhi, zlo, r32, Phat,
+                M, soft * soft, (float)(soft * soft)};
     const int nroots = t.nroots;
     const int ninit = nroots > kMaxWalkIters + 2 ? nroots : kMaxWalkIters + 2;
     (k_walk_init<<<blocks_for(ninit, 256), 256, 0, st>>>(wb.front0, t.dls, ds->cnt, ds->list_cnt,
@@ -470,8 +504,8 @@ void directed_offsets(const uint64_t* keys, int64_t nkeys, const unsigned long l
 
 void scalar_force(const TreeView& t, const double* zc, const double* M, const float4* xf,
                   const uint64_t* far_keys, const uint32_t* far_off, const uint64_t* near_keys,
-                  const uint32_t* near_off, int nb, const int* h_level_start, float* farf, float* f,
-                  float* fmin, cudaStream_t st) {
+                  const uint32_t* near_off, int nb, const int* h_level_start, double soft, float* farf,
+                  float* f, float* fmin, cudaStream_t st) {
     // farf doubles as scratch: [0, nnodes) far sums, [nnodes, 2 nnodes) pushed-down g,
     // and the leaf index of every body after that.
     float* g = farf + t.nnodes;
@@ -479,7 +513,8 @@ void scalar_force(const TreeView& t, const double* zc, const double* M, const fl
     (k_far_f<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.dnn, zc, M, far_keys, far_off, nb, farf), note_launch());
     (k_push_down<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, farf, g), note_launch());
     (k_leaf_of<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, leaf_of), note_launch());
-    (k_near_f<<<blocks_for(t.n, 128), 128, 0, st>>>(t, xf, near_keys, near_off, nb, leaf_of, g, f), note_launch());
+    (k_near_f<<<blocks_for(t.n, 128), 128, 0, st>>>(t, xf, near_keys, near_off, nb, leaf_of, g,
+                                                    (float)(soft * soft), f), note_launch());
     (k_fmin_leaves<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, f, fmin), note_launch());
     (void)h_level_start;
     for (int L = t.nlevels - 2; L >= 0; --L)

@@ -70,6 +70,9 @@ def main():
     ap.add_argument("--bh-mass", type=float, default=0.01, help="central point mass (0: a plain Plummer sphere)")
     ap.add_argument("--forces", default="fmm", choices=["fmm", "direct"],
                     help="force solve: the mixed-precision FMM, or the FP64 direct sum (O(N^2), a reference)")
+    ap.add_argument("--soft", type=float, default=0.0,
+                    help="Plummer softening length (Appendix B uses 1/N); 0: Newtonian")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
     if args.bh_mass > 0:
         pos, vel, m = ics.nucleus(args.n, args.seed, bh_mass=args.bh_mass)
@@ -79,7 +82,7 @@ def main():
     P = torch.tensor(pos, device=dev)
     V = torch.tensor(vel, device=dev)
     M = torch.tensor(m, device=dev)
-    fmm = FMM(p=args.p, eps=args.eps, precision="mixed")
+    fmm = FMM(p=args.p, eps=args.eps, precision=args.precision, soft=args.soft)
     t0 = time.perf_counter()
     es = integrate(fmm, P, V, M, args.dt, args.steps, direct=args.forces == "direct")
     torch.cuda.synchronize()
@@ -87,7 +90,8 @@ def main():
     drift = [abs(e - es[0]) / abs(es[0]) for e in es]
     name = f"nucleus_plummer_n{args.n}_plus_point_mass_{args.bh_mass:g}" if args.bh_mass > 0 else f"plummer_n{args.n}"
     print(json.dumps({"workload": name, "n_bodies": len(m), "forces": args.forces, "p": args.p,
-                      "eps": args.eps, "dt": args.dt, "steps": args.steps, "E0": es[0], "E_final": es[-1],
+                      "eps": args.eps, "soft": args.soft, "precision": args.precision, "dt": args.dt,
+                      "steps": args.steps, "E0": es[0], "E_final": es[-1],
                       "max_rel_energy_error": max(drift), "final_rel_energy_error": drift[-1],
                       "wall_s": wall, "solves_per_s": (args.steps + 1) / wall}))
 

@@ -19,26 +19,28 @@ from paper_2012_02207_gb300 import leapfrog  # noqa: E402
 DEV = torch.device("cuda:0")
 
 
-def cpu_leapfrog(pos, vel, m, dt, steps):
+def cpu_leapfrog(pos, vel, m, dt, steps, soft=0.0):
     pos, vel = pos.copy(), vel.copy()
-    acc, pot = oracle.direct(pos, m)
+    acc, pot = oracle.direct(pos, m, soft=soft)
     es = [0.5 * (m * (vel * vel).sum(1)).sum() + 0.5 * (m * pot).sum()]
     for _ in range(steps):
         vel += 0.5 * dt * acc
         pos += dt * vel
-        acc, pot = oracle.direct(pos, m)
+        acc, pot = oracle.direct(pos, m, soft=soft)
         vel += 0.5 * dt * acc
         es.append(0.5 * (m * (vel * vel).sum(1)).sum() + 0.5 * (m * pot).sum())
     return pos, vel, np.array(es)
 
 
-def test_leapfrog_tracks_direct_integration_and_conserves_energy():
+@pytest.mark.parametrize("soft", [0.0, 1.0 / 4097])
+def test_leapfrog_tracks_direct_integration_and_conserves_energy(soft):
+    """soft = 1/N is Appendix B's softening length."""
     n, dt, steps = 4096, 1.0 / 1024, 12
     pos, vel, m = ics.nucleus(n, 5)
     P, V, M = (torch.tensor(a, device=DEV) for a in (pos, vel, m))
-    fmm = gb.FMM(p=10, eps=1e-8, precision="mixed")
+    fmm = gb.FMM(p=10, eps=1e-8, precision="mixed", soft=soft)
     es = np.array(leapfrog.integrate(fmm, P, V, M, dt, steps))
-    ref_pos, ref_vel, ref_es = cpu_leapfrog(pos, vel, m, dt, steps)
+    ref_pos, ref_vel, ref_es = cpu_leapfrog(pos, vel, m, dt, steps, soft=soft)
     # Henon-unit Plummer plus a point mass: E0 is close to -1/4 (more bound by the point mass)
     assert -0.4 < es[0] < -0.2
     assert np.allclose(es, ref_es, rtol=1e-6, atol=0)

@@ -451,3 +451,116 @@ def test_mac_error_estimate_bounds_the_true_m2l_error():
     # an estimate, not a strict bound: it covers 99% of particles and is
     # never off by more than 2x; and it is not loose by orders of magnitude
     assert q99 <= 1.0 and worst <= 2.0 and q90 > 0.02, (q90, q99, worst)
+
+
+# --------------------------------------------------------------- softening
+
+def test_softened_direct_two_body_closed_form():
+    """Appendix B: phi(r) = -G m / sqrt(r^2 + soft^2), so a body at d from a
+    mass m feels G m d / (|d|^2 + soft^2)^{3/2}."""
+    pos = np.array([[0.1, -0.2, 0.3], [0.4, 0.2, -0.1]])
+    m = np.array([2.0, 3.0])
+    soft, G = 0.07, 1.5
+    acc, pot = oracle.direct(pos, m, G=G, soft=soft)
+    d = pos[1] - pos[0]
+    s2 = d @ d + soft * soft
+    assert np.allclose(acc[0], G * 3.0 * d / s2 ** 1.5, rtol=1e-15, atol=0)
+    assert np.allclose(acc[1], -G * 2.0 * d / s2 ** 1.5, rtol=1e-15, atol=0)
+    assert np.allclose(pot, [-G * 3.0 / math.sqrt(s2), -G * 2.0 / math.sqrt(s2)], rtol=1e-15)
+
+
+def test_softened_direct_obeys_newtons_third_law_and_tends_to_newton():
+    pos, _, m = ics.plummer(1500, 91)
+    m = ics.kroupa_masses(1500, 92)
+    acc, _ = oracle.direct(pos, m, soft=1e-2)
+    mom = (m[:, None] * acc).sum(0)
+    assert np.abs(mom).max() < 1e-12 * (m[:, None] * np.abs(acc)).sum()
+    # a softening far below every separation changes nothing visible
+    a0, p0 = oracle.direct(pos, m)
+    a1, p1 = oracle.direct(pos, m, soft=1e-12)
+    assert np.allclose(a1, a0, rtol=1e-9) and np.allclose(p1, p0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("n", [2, 65, 300])
+def test_softened_solve_is_the_softened_direct_sum_when_eps_is_zero(n):
+    pos, _, m = ics.plummer(n, 200 + n)
+    run = oracle.OracleRun(pos, m, p=4, eps=0.0, leaf_size=8, soft=0.03)
+    assert run.status == 0 and run.npairs("m2l") == 0
+    acc, pot = run.forces()
+    ad, pd = oracle.direct(pos, m, soft=0.03)
+    assert np.abs(acc - ad).max() <= 1e-12 * np.abs(ad).max()
+    assert np.abs(pot - pd).max() <= 1e-12 * np.abs(pd).max()
+
+
+def test_softening_bound_is_the_leading_term_for_two_bodies():
+    """For two single-body cells (r_A = r_B = 0, so d_min = d) the MAC's
+    softening term 1.5 M_A soft^2 / d^4 is the leading term of the exact
+    difference m/d^2 - m d/(d^2 + soft^2)^{3/2}: their ratio is 1 - O(soft^2/d^2)."""
+    pos = np.array([[0.0, 0.0, 0.0], [0.3, -0.4, 0.0]])  # d = 0.5
+    m = np.array([2.0, 5.0])
+    for soft in (5e-4, 5e-3):
+        run = oracle.OracleRun(pos, m, p=4, eps=1e-6, leaf_size=1, stage=oracle.STAGE_LISTS, soft=soft)
+        t = run.tree()
+        leaves = [k for k in range(run.nnodes) if t["nchild"][k] == 0]
+        a, b = leaves
+        ma, mb = m[t["perm"][t["begin"][a]]], m[t["perm"][t["begin"][b]]]
+        v = run.mac_values(a, b)
+        d = 0.5
+        for mass, bound in ((ma, v[5]), (mb, v[6])):
+            exact = mass / d ** 2 - mass * d / (d * d + soft * soft) ** 1.5
+            u = soft * soft / (d * d)
+            assert 1.0 - 2.0 * u < exact / bound <= 1.0, (soft, exact / bound)
+
+
+def test_softening_bound_covers_every_accepted_pair():
+    """On the pairs a softened solve accepts, the bound covers the exact
+    softened-minus-Newtonian acceleration of A's bodies at every body of B."""
+    n, soft = 1200, 0.02
+    pos, _, m = ics.plummer(n, 93)
+    run = oracle.OracleRun(pos, m, p=6, eps=1e-4, leaf_size=16, stage=oracle.STAGE_LISTS, soft=soft)
+    t = run.tree()
+    ps, ms = pos[t["perm"]], m[t["perm"]]
+    pairs = run.pairs("m2l")
+    assert len(pairs) > 50
+    tight = 0.0
+    for a, b in pairs[np.random.default_rng(2).choice(len(pairs), size=min(200, len(pairs)), replace=False)]:
+        v = run.mac_values(a, b)
+        assert v[4] == 1.0 and v[0] + v[5] < v[2] and v[1] + v[6] < v[3]
+        for src, dst, bound in ((a, b, v[5]), (b, a, v[6])):
+            js = np.arange(t["begin"][src], t["end"][src])
+            for i in range(t["begin"][dst], t["end"][dst]):
+                d = ps[js] - ps[i]
+                r2 = (d * d).sum(1)
+                diff = (ms[js, None] * d * (r2[:, None] ** -1.5 - (r2[:, None] + soft * soft) ** -1.5)).sum(0)
+                err = np.linalg.norm(diff)
+                assert err <= bound * (1 + 1e-9), (err, bound)
+                tight = max(tight, err / bound)
+    assert tight > 0.05  # the bound is not loose by orders of magnitude
+
+
+def test_softened_solve_meets_the_tolerance():
+    """With a softening large enough to matter (soft = 0.01 against cell
+    separations of ~0.05 in the core), the far field alone would be off by
+    ~1.5 (soft/d)^2 ~ 6%; the MAC's softening term keeps the error at the
+    tolerance."""
+    pos, _, m = ics.plummer(4000, 94)
+    soft, eps = 0.01, 1e-6
+    ad, _ = oracle.direct(pos, m, soft=soft)
+    acc, _ = oracle.fmm(pos, m, p=8, eps=eps, soft=soft)
+    st = oracle.error_stats(acc, ad)
+    assert st["median"] < eps and st["rms"] < 10 * eps and st["max"] < 1e-3, st
+
+
+def test_softened_scalar_force_estimate_is_exact_when_all_near():
+    """With one leaf the softened estimate is sum_j m_j r_ij / (r_ij^2 + soft^2)^{3/2}
+    in FP32."""
+    pos, _, m = ics.plummer(50, 3)
+    soft = 0.05
+    run = oracle.OracleRun(pos, m, leaf_size=64, stage=oracle.STAGE_F, soft=soft)
+    f = run.geometry()["f"]
+    ps, ms = pos[run.tree()["perm"]], m[run.tree()["perm"]]
+    d = ps[:, None, :] - ps[None, :, :]
+    r2 = (d * d).sum(-1)
+    term = ms[None, :] * np.sqrt(r2) / (r2 + soft * soft) ** 1.5
+    np.fill_diagonal(term, 0.0)
+    assert np.allclose(f, term.sum(1), rtol=2e-5)
