@@ -73,6 +73,16 @@ def lib():
             L.orc_eval_multipole.restype = ctypes.c_double
             L.orc_direct.argtypes = [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), dp, dp, dp, dp]
+            L.orc_direct_jerk.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, dp, dp, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                          dp, dp, dp]
+            L.orc_regular_grad.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_p2m_dipole.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, dp, dp, dp, dp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
+            L.orc_l2p_hessian.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, dp]
+            L.orc_jerk.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp, dp]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_mac_values.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, dp]
             _lib = L
@@ -171,6 +181,48 @@ def direct(pos, mass, G=1.0, targets=None, soft=0.0):
     return np.stack([ax, ay, az], axis=1), pot
 
 
+def direct_jerk(pos, vel, mass, G=1.0, targets=None, soft=0.0):
+    """FP64 O(N^2) jerks (N,3), the time derivative of the direct-sum accelerations."""
+    pos, vel = _c(pos), _c(vel)
+    x, y, z = (np.ascontiguousarray(pos[:, d]) for d in range(3))
+    vx, vy, vz = (np.ascontiguousarray(vel[:, d]) for d in range(3))
+    m = _c(mass)
+    n = len(m)
+    if targets is None:
+        nt, tp = n, None
+    else:
+        tg = np.ascontiguousarray(targets, dtype=np.int64)
+        nt, tp = len(tg), tg.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    jx, jy, jz = (np.zeros(nt) for _ in range(3))
+    lib().orc_direct_jerk(n, _dp(x), _dp(y), _dp(z), _dp(vx), _dp(vy), _dp(vz), _dp(m), G, float(soft), nt, tp,
+                          _dp(jx), _dp(jy), _dp(jz))
+    return np.stack([jx, jy, jz], axis=1)
+
+
+def regular_grad(p, x, y, z):
+    """d/dx, d/dy, d/dz of Upsilon_n^m at (x, y, z), each packed like regular()."""
+    g = [np.zeros(NCOEF(p), dtype=np.complex128) for _ in range(3)]
+    lib().orc_regular_grad(p, x, y, z, *(a.ctypes.data for a in g))
+    return g
+
+
+def p2m_dipole(p, pos, dip, center):
+    """Multipoles -sum_j D_j . grad Upsilon_n^m(x_j - c) of point dipoles D_j at x_j."""
+    pos, dip = _c(pos), _c(dip)
+    cols = [np.ascontiguousarray(pos[:, d]) for d in range(3)] + [np.ascontiguousarray(dip[:, d]) for d in range(3)]
+    M = np.zeros(NCOEF(p), dtype=np.complex128)
+    lib().orc_p2m_dipole(p, len(pos), *(_dp(a) for a in cols), *map(float, center), M.ctypes.data)
+    return M
+
+
+def l2p_hessian(p, F, d):
+    """(xx, yy, zz, xy, xz, yz) second derivatives of sum conj(Upsilon(d)) F at d."""
+    F = np.ascontiguousarray(F, dtype=np.complex128)
+    h = np.zeros(6)
+    lib().orc_l2p_hessian(p, F.ctypes.data, *map(float, d), _dp(h))
+    return h
+
+
 # ------------------------------------------------------------------- solve
 
 STAGE_TREE, STAGE_F, STAGE_LISTS, STAGE_FULL = 1, 2, 3, 4
@@ -257,6 +309,17 @@ class OracleRun:
     def forces(self):
         acc = np.stack([self._get(20 + d, np.float64, self.n) for d in range(3)], axis=1)
         return acc, self._get(23, np.float64, self.n)
+
+    def jerk(self, vel):
+        """Jerks (N,3) of the bodies moving with velocities vel (N,3), on this
+        solve's tree and lists (needs a full solve)."""
+        vel = _c(vel)
+        v = [np.ascontiguousarray(vel[:, d]) for d in range(3)]
+        j = [np.zeros(self.n) for _ in range(3)]
+        rc = lib().orc_jerk(self._h, *(_dp(a) for a in v), *(_dp(a) for a in j))
+        if rc != 0:
+            raise RuntimeError("the jerk needs a full solve")
+        return np.stack(j, axis=1)
 
 
 def fmm(pos, mass, p=8, eps=1e-7, leaf_size=64, G=1.0, soft=0.0):

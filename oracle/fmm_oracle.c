@@ -258,6 +258,81 @@ double orc_eval_multipole(int p, const cplx* M, double cx, double cy, double cz,
     return -s;
 }
 
+/* ---------------------------------------------------------- derivatives */
+
+/* Derivative c (0: x, 1: y, 2: z) of a family X_n^m that obeys the ladder
+ * relations of the regular harmonics, with d+ = dx + i dy, d- = dx - i dy:
+ *   dz X_n^m = X_{n-1}^m,  d+ X_n^m = -X_{n-1}^{m+1},  d- X_n^m = X_{n-1}^{m-1}
+ * (they follow from the recurrences above; the pins check them against
+ * finite differences). So
+ *   dx X_n^m = (X_{n-1}^{m-1} - X_{n-1}^{m+1}) / 2
+ *   dy X_n^m = i (X_{n-1}^{m+1} + X_{n-1}^{m-1}) / 2.
+ * X holds degrees 0..p-1; out gets degrees 0..p (out_0^0 = 0). Derivatives
+ * of the family obey the same relations, so applying this twice gives the
+ * second derivatives. */
+static void ladder(int c, int p, const cplx* X, cplx* out) {
+    out[0].re = 0.0; out[0].im = 0.0;
+    for (int n = 1; n <= p; ++n)
+        for (int m = 0; m <= n; ++m) {
+            cplx lo = (m - 1 >= -(n - 1) && m - 1 <= n - 1) ? getc(X, n - 1, m - 1) : (cplx){0.0, 0.0};
+            cplx hi = (m + 1 <= n - 1) ? getc(X, n - 1, m + 1) : (cplx){0.0, 0.0};
+            cplx mid = (m <= n - 1) ? getc(X, n - 1, m) : (cplx){0.0, 0.0};
+            cplx v;
+            if (c == 0) {
+                v.re = 0.5 * (lo.re - hi.re); v.im = 0.5 * (lo.im - hi.im);
+            } else if (c == 1) {
+                /* i (hi + lo) / 2 */
+                v.re = -0.5 * (hi.im + lo.im); v.im = 0.5 * (hi.re + lo.re);
+            } else {
+                v = mid;
+            }
+            out[tri(n, m)] = v;
+        }
+}
+
+/* Gradient of the regular harmonics: g[c][tri(n,m)] = d_c Upsilon_n^m(x,y,z),
+ * n <= p. */
+void orc_regular_grad(int p, double x, double y, double z, cplx* gx, cplx* gy, cplx* gz) {
+    cplx R[ncoef(ORC_MAXP)];
+    orc_regular(p > 0 ? p - 1 : 0, x, y, z, R);
+    ladder(0, p, R, gx);
+    ladder(1, p, R, gy);
+    ladder(2, p, R, gz);
+}
+
+/* Multipoles of point dipoles (the far field of the jerk, see orc_jerk): a
+ * dipole D at s has the potential D . grad_x (1 / |s - x|) =
+ * -D . grad_s (1 / |x - s|), so with 1/|x - s| = sum conj(Upsilon(s - c))
+ * Theta(x - c) its moments are M_n^m = -D . grad Upsilon_n^m(s - c). */
+void orc_p2m_dipole(int p, int64_t n, const double* x, const double* y, const double* z,
+                    const double* dx, const double* dy, const double* dz, double cx, double cy, double cz,
+                    cplx* M) {
+    cplx gx[ncoef(ORC_MAXP)], gy[ncoef(ORC_MAXP)], gz[ncoef(ORC_MAXP)];
+    for (int64_t i = 0; i < n; ++i) {
+        orc_regular_grad(p, x[i] - cx, y[i] - cy, z[i] - cz, gx, gy, gz);
+        for (int k = 0; k < ncoef(p); ++k) {
+            M[k].re -= dx[i] * gx[k].re + dy[i] * gy[k].re + dz[i] * gz[k].re;
+            M[k].im -= dx[i] * gx[k].im + dy[i] * gy[k].im + dz[i] * gz[k].im;
+        }
+    }
+}
+
+/* Hessian of Psi(x) = sum_{n,m} conj(Upsilon_n^m(d)) F_n^m (= -phi without
+ * G) at d: h = {xx, yy, zz, xy, xz, yz}, from the second derivatives of the
+ * harmonics. */
+void orc_l2p_hessian(int p, const cplx* F, double dx, double dy, double dz, double* h) {
+    cplx g[3][ncoef(ORC_MAXP)], H[ncoef(ORC_MAXP)];
+    orc_regular_grad(p > 0 ? p - 1 : 0, dx, dy, dz, g[0], g[1], g[2]);
+    const int kc[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int e = 0; e < 6; ++e) {
+        ladder(kc[e][1], p, g[kc[e][0]], H);
+        double s = 0.0;
+        for (int n = 0; n <= p; ++n)
+            for (int m = -n; m <= n; ++m) s += cmul(cconj(getc(H, n, m)), getc(F, n, m)).re;
+        h[e] = s;
+    }
+}
+
 /* ------------------------------------------------------------ direct sum */
 
 /* Plain O(N^2) FP64 sum over all j != i (the quantity the FMM approximates,
@@ -284,6 +359,35 @@ void orc_direct(int64_t n, const double* x, const double* y, const double* z,
             sp += m[j] / r;
         }
         ax[t] = G * sx; ay[t] = G * sy; az[t] = G * sz; pot[t] = -G * sp;
+    }
+}
+
+/* Plain O(N^2) FP64 jerk, the time derivative of the direct-sum acceleration:
+ * j_i = G sum_{j != i} m_j [v_ij / r^3 - 3 (r_ij . v_ij) r_ij / r^5],
+ * r_ij = x_j - x_i, v_ij = v_j - v_i, r = |r_ij| (r^2 + soft^2 with
+ * softening). */
+void orc_direct_jerk(int64_t n, const double* x, const double* y, const double* z, const double* vx,
+                     const double* vy, const double* vz, const double* m, double G, double soft,
+                     int64_t ntgt, const int64_t* tgt, double* jx, double* jy, double* jz) {
+    const double soft2 = soft * soft;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < ntgt; ++t) {
+        int64_t i = tgt ? tgt[t] : t;
+        double sx = 0, sy = 0, sz = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+            double ux = vx[j] - vx[i], uy = vy[j] - vy[i], uz = vz[j] - vz[i];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (soft2 > 0.0) r2 = r2 + soft2;
+            double r = sqrt(r2);
+            double r3 = r2 * r, r5 = r3 * r2;
+            double rv = dx * ux + dy * uy + dz * uz;
+            sx += m[j] * (ux / r3 - 3.0 * rv * dx / r5);
+            sy += m[j] * (uy / r3 - 3.0 * rv * dy / r5);
+            sz += m[j] * (uz / r3 - 3.0 * rv * dz / r5);
+        }
+        jx[t] = G * sx; jy[t] = G * sy; jz[t] = G * sz;
     }
 }
 
@@ -820,6 +924,113 @@ static void forces(orc_state* s) {
         s->pot[o] = s->G * fp[i];
     }
     free(fx); free(fy); free(fz); free(fp);
+}
+
+/* Jerk (the time derivative of the acceleration) on the tree and lists of a
+ * full solve, as a sum of three parts (derivation in the design notes):
+ *   j_i = G [ -grad chi(x_i) + H(x_i) v_i + near_i ]
+ *  - chi(x) = sum_j m_j v_j . grad_x (1 / |x_j - x|) is the potential of
+ *    point dipoles m_j v_j; its far part is one more expansion through the
+ *    same tree and lists (dipole P2M, M2M, M2L both ways, L2L) and its
+ *    gradient comes from the degree-1 local coefficients, as the
+ *    acceleration does;
+ *  - H = grad grad Psi is the Hessian of Psi = sum_j m_j / |x_j - x| from the
+ *    solve's own local expansion (orc_l2p_hessian);
+ *  - near_i is the direct jerk over the P2P leaf pairs (softened as P2P is).
+ * Velocities and the outputs are in the caller's order. */
+int orc_jerk(orc_state* s, const double* vx, const double* vy, const double* vz,
+             double* jx_out, double* jy_out, double* jz_out) {
+    if (s->status != 0 || s->stage < 4) return -1;
+    int p = s->p, nc = ncoef(p);
+    int32_t nn = s->nnodes;
+    int64_t n = s->n;
+    double* vs = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* ds = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t o = s->perm[i];
+        vs[i] = vx[o]; vs[n + i] = vy[o]; vs[2 * n + i] = vz[o];
+        ds[i] = s->ms[i] * vx[o]; ds[n + i] = s->ms[i] * vy[o]; ds[2 * n + i] = s->ms[i] * vz[o];
+    }
+    cplx* mj = (cplx*)calloc((size_t)nc * nn, sizeof(cplx));
+    cplx* lj = (cplx*)calloc((size_t)nc * nn, sizeof(cplx));
+    for (int32_t L = s->nlevels - 1; L >= 0; --L) {
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int32_t k = s->level_start[L]; k < s->level_start[L + 1]; ++k) {
+            cplx* Mk = mj + (size_t)nc * k;
+            const double* z = s->zc + 3 * k;
+            if (is_leaf(s, k)) {
+                int32_t b = s->begin[k];
+                orc_p2m_dipole(p, s->end[k] - b, s->xs + b, s->ys + b, s->zs + b, ds + b, ds + n + b,
+                               ds + 2 * n + b, z[0], z[1], z[2], Mk);
+            } else {
+                for (int32_t c = s->first_child[k]; c < s->first_child[k] + s->nchild[k]; ++c) {
+                    const double* zc = s->zc + 3 * c;
+                    orc_m2m(p, mj + (size_t)nc * c, zc[0] - z[0], zc[1] - z[1], zc[2] - z[2], Mk);
+                }
+            }
+        }
+    }
+    int64_t* off; int32_t* idx;
+    partner_csr(nn, s->nm2l, s->m2l, &off, &idx);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int32_t b = 0; b < nn; ++b) {
+        const double* zb = s->zc + 3 * b;
+        for (int64_t q = off[b]; q < off[b + 1]; ++q) {
+            int32_t a = idx[q];
+            const double* za = s->zc + 3 * a;
+            orc_m2l(p, mj + (size_t)nc * a, za[0] - zb[0], za[1] - zb[1], za[2] - zb[2], lj + (size_t)nc * b);
+        }
+    }
+    free(off); free(idx);
+    for (int32_t L = 1; L < s->nlevels; ++L) {
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int32_t k = s->level_start[L]; k < s->level_start[L + 1]; ++k) {
+            int32_t par = s->parent[k];
+            const double* zk = s->zc + 3 * k;
+            const double* zp = s->zc + 3 * par;
+            orc_l2l(p, lj + (size_t)nc * par, zk[0] - zp[0], zk[1] - zp[1], zk[2] - zp[2], lj + (size_t)nc * k);
+        }
+    }
+    partner_csr(nn, s->np2p, s->p2p, &off, &idx);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int32_t b = 0; b < nn; ++b) {
+        if (!is_leaf(s, b)) continue;
+        const double* zb = s->zc + 3 * b;
+        for (int32_t i = s->begin[b]; i < s->end[b]; ++i) {
+            double dx = s->xs[i] - zb[0], dy = s->ys[i] - zb[1], dz = s->zs[i] - zb[2];
+            double phi, gx, gy, gz, h[6];
+            orc_l2p(p, lj + (size_t)nc * b, dx, dy, dz, &phi, &gx, &gy, &gz);
+            orc_l2p_hessian(p, s->loc + (size_t)nc * b, dx, dy, dz, h);
+            double vix = vs[i], viy = vs[n + i], viz = vs[2 * n + i];
+            double fx = -gx + h[0] * vix + h[3] * viy + h[4] * viz;
+            double fy = -gy + h[3] * vix + h[1] * viy + h[5] * viz;
+            double fz = -gz + h[4] * vix + h[5] * viy + h[2] * viz;
+            double sx = 0, sy = 0, sz = 0;
+            for (int64_t q = off[b]; q < off[b + 1]; ++q) {
+                int32_t a = idx[q];
+                for (int32_t j = s->begin[a]; j < s->end[a]; ++j) {
+                    if (j == i) continue;
+                    double rx = s->xs[j] - s->xs[i], ry = s->ys[j] - s->ys[i], rz = s->zs[j] - s->zs[i];
+                    double ux = vs[j] - vix, uy = vs[n + j] - viy, uz = vs[2 * n + j] - viz;
+                    double r2 = rx * rx + ry * ry + rz * rz;
+                    if (s->soft2 > 0.0) r2 = r2 + s->soft2;
+                    double r = sqrt(r2);
+                    double r3 = r2 * r, r5 = r3 * r2;
+                    double rv = rx * ux + ry * uy + rz * uz;
+                    sx += s->ms[j] * (ux / r3 - 3.0 * rv * rx / r5);
+                    sy += s->ms[j] * (uy / r3 - 3.0 * rv * ry / r5);
+                    sz += s->ms[j] * (uz / r3 - 3.0 * rv * rz / r5);
+                }
+            }
+            int64_t o = s->perm[i];
+            jx_out[o] = s->G * (fx + sx);
+            jy_out[o] = s->G * (fy + sy);
+            jz_out[o] = s->G * (fz + sz);
+        }
+    }
+    free(off); free(idx);
+    free(mj); free(lj); free(vs); free(ds);
+    return 0;
 }
 
 void orc_free(orc_state* s);

@@ -564,3 +564,108 @@ def test_softened_scalar_force_estimate_is_exact_when_all_near():
     term = ms[None, :] * np.sqrt(r2) / (r2 + soft * soft) ** 1.5
     np.fill_diagonal(term, 0.0)
     assert np.allclose(f, term.sum(1), rtol=2e-5)
+
+
+# ------------------------------------------------------------------- jerks
+
+def _fd_regular(p, v, h=1e-6):
+    out = []
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = h
+        out.append((oracle.regular(p, *(v + e)) - oracle.regular(p, *(v - e))) / (2 * h))
+    return out
+
+
+def test_regular_gradient_matches_finite_differences():
+    """The ladder relations d_z U_n^m = U_{n-1}^m, (d_x + i d_y) U_n^m = -U_{n-1}^{m+1},
+    (d_x - i d_y) U_n^m = U_{n-1}^{m-1} against central differences of the recurrences."""
+    p = 12
+    for _ in range(4):
+        v = RNG.normal(size=3) * 0.6
+        g = oracle.regular_grad(p, *v)
+        fd = _fd_regular(p, v)
+        for a, b in zip(g, fd):
+            assert np.abs(a - b).max() < 1e-8 * max(1.0, np.abs(b).max())
+
+
+def test_l2p_hessian_is_the_derivative_of_the_l2p_acceleration():
+    p = 10
+    pos = RNG.normal(size=(40, 3)) * 0.2 + np.array([3.0, -2.0, 1.5])
+    m = RNG.uniform(0.5, 1.5, 40)
+    F = oracle.m2l(p, oracle.p2m(p, pos, m, pos.mean(0)), pos.mean(0))
+    d = np.array([0.11, -0.07, 0.05])
+    h = oracle.l2p_hessian(p, F, d)
+    H = np.array([[h[0], h[3], h[4]], [h[3], h[1], h[5]], [h[4], h[5], h[2]]])
+    e = 1e-5
+    for c in range(3):
+        dp, dm = d.copy(), d.copy()
+        dp[c] += e
+        dm[c] -= e
+        ap = np.array(oracle.l2p(p, F, dp)[1:])
+        am = np.array(oracle.l2p(p, F, dm)[1:])
+        assert np.allclose((ap - am) / (2 * e), H[:, c], rtol=1e-6, atol=1e-9 * np.abs(H).max())
+    assert abs(h[0] + h[1] + h[2]) < 1e-10 * np.abs(h).max()  # harmonic: traceless
+
+
+def test_dipole_multipoles_give_the_dipole_far_field():
+    """chi(x) = sum_j D_j . grad_x (1/|x_j - x|) = sum_j D_j . (x_j - x)/|x_j - x|^3."""
+    p = 14
+    c = np.array([0.2, -0.1, 0.3])
+    pos = c + RNG.normal(size=(30, 3)) * 0.1
+    dip = RNG.normal(size=(30, 3))
+    M = oracle.p2m_dipole(p, pos, dip, c)
+    assert abs(M[0]) == 0.0  # dipoles carry no monopole
+    for x in (np.array([2.0, 1.0, -1.5]), np.array([-3.0, 0.5, 0.2])):
+        d = pos - x
+        chi = (dip * d).sum(1) @ (1.0 / np.linalg.norm(d, axis=1) ** 3)
+        assert np.isclose(-oracle.eval_multipole(p, M, c, x), chi, rtol=1e-10)
+
+
+def test_direct_jerk_is_the_time_derivative_of_the_acceleration():
+    pos, vel, m = ics.plummer(300, 41)
+    for soft in (0.0, 0.02):
+        j = oracle.direct_jerk(pos, vel, m, G=1.3, soft=soft)
+        h = 1e-6
+        ap, _ = oracle.direct(pos + h * vel, m, G=1.3, soft=soft)
+        am, _ = oracle.direct(pos - h * vel, m, G=1.3, soft=soft)
+        fd = (ap - am) / (2 * h)
+        assert np.abs(fd - j).max() < 1e-5 * np.abs(j).max()
+
+
+@pytest.mark.parametrize("soft", [0.0, 0.03])
+def test_jerk_is_the_direct_jerk_when_eps_is_zero(soft):
+    pos, vel, m = ics.plummer(400, 42)
+    run = oracle.OracleRun(pos, m, p=4, eps=0.0, leaf_size=8, soft=soft)
+    j = run.jerk(vel)
+    jd = oracle.direct_jerk(pos, vel, m, soft=soft)
+    assert np.abs(j - jd).max() <= 1e-11 * np.abs(jd).max()
+
+
+def test_jerk_error_falls_with_eps():
+    """The far part (dipole moments, M2M, M2L, L2L, the gradient of chi and
+    the Hessian term) converges: as the MAC tolerance falls the jerk error
+    falls with it. A wrong sign or index in any far term leaves an O(1)
+    error that no tolerance removes. (A purely geometric MAC is no test here:
+    pairs at theta near 1 converge like theta^p, slower for the second
+    derivatives than for the force.)"""
+    pos, vel, m = ics.plummer(3000, 43)
+    jd = oracle.direct_jerk(pos, vel, m)
+    med = []
+    for eps in (1e-3, 1e-5, 1e-7, 1e-9):
+        run = oracle.OracleRun(pos, m, p=8, eps=eps, leaf_size=16)
+        assert run.npairs("m2l") > 1000
+        j = run.jerk(vel)
+        d = np.linalg.norm(j - jd, axis=1) / np.linalg.norm(jd, axis=1)
+        med.append(np.median(d))
+    assert all(b < 0.1 * a for a, b in zip(med, med[1:])), med
+    assert med[-1] < 1e-7, med
+
+
+def test_jerk_meets_a_tolerance_like_the_acceleration():
+    pos, vel, m = ics.plummer(4000, 44)
+    jd = oracle.direct_jerk(pos, vel, m)
+    run = oracle.OracleRun(pos, m, p=10, eps=1e-8, leaf_size=32)
+    j = run.jerk(vel)
+    d = np.linalg.norm(j - jd, axis=1) / np.linalg.norm(jd, axis=1)
+    assert np.median(d) < 1e-6 and np.sqrt(np.mean(d * d)) < 1e-4, (np.median(d), np.sqrt(np.mean(d * d)))
