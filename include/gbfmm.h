@@ -87,6 +87,7 @@ typedef struct {
     int64_t kernel_launches;  /* kernels the library launched in the last solve */
     int32_t graph_replays;    /* 1 if the last fmm_solve_graph call replayed its captured graph */
     int32_t reserved;
+    double ms_jerk;           /* the jerk pass of the last fmm_solve_jerk (0 otherwise) */
 } fmm_stats;
 
 typedef struct fmm_ctx fmm_ctx;
@@ -151,6 +152,24 @@ int fmm_solve_batch(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, con
 int fmm_solve_graph(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, int64_t n, const double* x,
                     const double* y, const double* z, const double* m, double* ax, double* ay,
                     double* az, double* pot, void* cuda_stream);
+
+/* The solve of fmm_solve plus the jerk, the time derivative of the
+ * acceleration for bodies moving with velocities (vx, vy, vz):
+ * j_i = G sum_{j != i} m_j [v_ij / r^3 - 3 (r_ij . v_ij) r_ij / r^5],
+ * r_ij = x_j - x_i, v_ij = v_j - v_i (Plummer-softened like P2P when soft > 0).
+ * The paper (Sec. 6) computes jerks within the FMM after Dehnen (2014) for
+ * Hermite integrators; the form here: j_i = G [-grad chi(x_i) + H(x_i) v_i
+ * + near_i], with chi the potential of point dipoles m_j v_j, expanded on
+ * the same tree and interaction lists (one more P2M/M2M/M2L/L2L pass, in
+ * the context's precision), H the Hessian of the solve's own local
+ * expansion, and near_i the direct jerk over the P2P leaf pairs. The lists
+ * come from the acceleration's MAC, so the jerk's error is not controlled
+ * by eps directly (measured: it tracks eps within a small factor).
+ * All arrays are device pointers of n FP64 values in the caller's order
+ * (pot may be NULL). Errors as fmm_solve. */
+int fmm_solve_jerk(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z, const double* vx,
+                   const double* vy, const double* vz, const double* m, double* ax, double* ay, double* az,
+                   double* pot, double* jx, double* jy, double* jz, void* cuda_stream);
 
 /* Plain FP64 O(N * ntargets) direct sum at the given target indices (a
  * device int64 array, or NULL for all n bodies): the exact quantity the FMM

@@ -46,7 +46,7 @@ class Stats(ctypes.Structure):
                 ("ms_walk", ctypes.c_double), ("ms_m2l", ctypes.c_double), ("ms_downward", ctypes.c_double),
                 ("ms_leaf", ctypes.c_double), ("ms_total", ctypes.c_double), ("walk_iters", ctypes.c_int32),
                 ("regrows", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
-                ("graph_replays", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("graph_replays", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ms_jerk", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -73,6 +73,7 @@ def lib():
             L.fmm_solve_host.argtypes = [vp, i64] + [dp] * 8 + [vp]
             L.fmm_solve_batch.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)] + [dp] * 8 + [vp]
             L.fmm_solve_graph.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), i64] + [dp] * 8 + [vp]
+            L.fmm_solve_jerk.argtypes = [vp, i64] + [dp] * 14 + [vp]
             L.fmm_direct.argtypes = [vp, i64, dp, dp, dp, dp, i64, dp, dp, dp, dp, dp, vp]
             L.fmm_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
             L.fmm_export_tree.argtypes = [vp] + [dp] * 8
@@ -210,6 +211,22 @@ class FMM:
         self._check(lib().fmm_solve_graph(self._h, ncl, optr, n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(ax),
                                           _ptr(ay), _ptr(az), _ptr(pot), _stream_handle(stream)))
         return ax, ay, az, pot
+
+    def solve_jerk(self, x, y, z, vx, vy, vz, m, out=None, stream=None):
+        """Accelerations, potentials and jerks (the time derivative of the
+        acceleration) of bodies moving with velocities (vx, vy, vz): device FP64
+        tensors in, (ax, ay, az, pot, jx, jy, jz) out (see fmm_solve_jerk)."""
+        import torch  # noqa: PLC0415
+        n = x.numel()
+        for t in (x, y, z, vx, vy, vz, m):
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("positions, velocities and masses must be contiguous CUDA float64 tensors "
+                                 "of equal length")
+        if out is None:
+            out = tuple(torch.empty(n, dtype=torch.float64, device=x.device) for _ in range(7))
+        self._check(lib().fmm_solve_jerk(self._h, n, *(_ptr(t) for t in (x, y, z, vx, vy, vz, m)),
+                                         *(_ptr(o) for o in out), _stream_handle(stream)))
+        return out
 
     def direct(self, x, y, z, m, targets=None, stream=None):
         """FP64 direct sum at device int64 target indices (all bodies if None)."""

@@ -90,6 +90,9 @@ struct fmm_ctx {
         fmin, fscratch, zhi, zlo, contrib, Phat, r32;
     // P2P work items
     Buf item_first, slot_first, item_leaf, leaf_of, part_hi, part_lo, work;
+    // jerks: sorted velocities (FP64, FP32), dipole weights, order p-1 moments,
+    // dipole multipoles and locals (FP64 and FP32)
+    Buf jv, jv32, jw, jmom, jmult, jmult32, jloc, jloc32;
     // walk and lists
     // per list: sorted directed keys, the sort's second buffer (its own, so a
     // buffer never moves to a list of another size), CSR offsets
@@ -601,6 +604,74 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     return FMM_OK;
 }
 
+// Jerks on the tree, lists and locals of the solve that just ran (see
+// jerk_leaves): the dipole field chi of the weights m_i v_i goes through an
+// order p - 1 P2M of each component, the dipole moments, M2M, M2L over the
+// same directed list and L2L, in the solve's precision.
+int jerk_pass(fmm_ctx* ctx, const double* vx, const double* vy, const double* vz, double* jx, double* jy,
+              double* jz, cudaStream_t st) {
+    const int p = ctx->cfg.p;
+    const bool mixed = ctx->cfg.precision == FMM_PRECISION_MIXED;
+    const bool m2l32 = mixed && m2l32_supported(p);
+    const size_t N = (size_t)ctx->n, K = (size_t)ctx->nnodes;
+    const size_t nr = ncoef_real(p), nq = ncoef_real(p - 1), pad = (nr + 3) & ~(size_t)3;
+    int rc;
+    if ((rc = ensure(ctx, ctx->jv, 24 * N)) || (rc = ensure(ctx, ctx->jw, 24 * N)) ||
+        (rc = ensure(ctx, ctx->jv32, 16 * N)) || (rc = ensure(ctx, ctx->jmom, 24 * K * nq)) ||
+        (rc = ensure(ctx, ctx->jmult, 8 * K * nr)))
+        return rc;
+    if (!m2l32 && (rc = ensure(ctx, ctx->jloc, 8 * K * nr))) return rc;
+    if (mixed && ((rc = ensure(ctx, ctx->jloc32, 4 * K * nr)) || (m2l32 && (rc = ensure(ctx, ctx->jmult32, 4 * K * pad)))))
+        return rc;
+    TreeView t = view(ctx);
+    const uint32_t* perm = as<uint32_t>(ctx->sorted_in_1 ? ctx->v1 : ctx->v0);
+    const double *xs = as<double>(ctx->xs), *ys = as<double>(ctx->ys), *zs = as<double>(ctx->zs);
+    const double *zc = as<double>(ctx->zc), *hs = as<double>(ctx->hs);
+    double* w = as<double>(ctx->jw);
+    double* mom = as<double>(ctx->jmom);
+    CK(cudaEventRecord(ctx->ev[8], st));
+    jerk_inputs((int)N, perm, as<double>(ctx->ms), vx, vy, vz, as<double>(ctx->jv), w, as<float4>(ctx->jv32), st);
+    for (int c = 0; c < 3; ++c) p2m_weights(t, p - 1, xs, ys, zs, w + c * N, zc, hs, mom + c * K * nq, ctx->tb, st);
+    dipole_moments(t, p, mom, mom + K * nq, mom + 2 * K * nq, hs, as<double>(ctx->jmult), st);
+    for (int L = t.nlevels - 2; L >= 0; --L)
+        m2m_level(t, L, p, zc, hs, as<double>(ctx->jmult), as<double>(ctx->contrib), ctx->tb, false, st);
+    const uint64_t* mk = as<uint64_t>(ctx->dkeys[2]);
+    const uint32_t* mo = as<uint32_t>(ctx->doff[2]);
+    if (m2l32) {
+        multipoles_to_f32_padded(as<double>(ctx->jmult), as<float>(ctx->jmult32), t, (int)nr, (int)pad, st);
+        m2l_f32(t.dnn, p, mk, mo, ctx->nb, as<float>(ctx->jmult32), as<float4>(ctx->zhi), as<float4>(ctx->zlo),
+                as<float>(ctx->jloc32), &ctx->ds->queue, st);
+    } else {
+        m2l_f64(t.dnn, p, mk, mo, ctx->nb, as<double>(ctx->jmult), zc, hs, as<double>(ctx->jloc), ctx->tb,
+                &ctx->ds->queue, st);
+        if (mixed) multipoles_to_f32(as<double>(ctx->jloc), as<float>(ctx->jloc32), t, (int)nr, st);
+    }
+    if (mixed) downward_pass_f32(t, ctx->h_level_start, p, zc, hs, as<float>(ctx->jloc32), ctx->tb, st);
+    else downward_pass_f64(t, ctx->h_level_start, p, zc, hs, as<double>(ctx->jloc), ctx->tb, st);
+    LeafArgs la{};
+    la.t = t; la.p = p; la.G = ctx->cfg.G;
+    la.soft2 = ctx->cfg.soft * ctx->cfg.soft;
+    la.soft2f = (float)la.soft2;
+    la.xs = xs; la.ys = ys; la.zs = zs; la.ms = as<double>(ctx->ms);
+    la.zc = zc; la.hs = hs;
+    la.zhi = as<float4>(ctx->zhi); la.zlo = as<float4>(ctx->zlo);
+    la.p2p_keys = as<uint64_t>(ctx->dkeys[3]); la.p2p_off = as<uint32_t>(ctx->doff[3]); la.nb = ctx->nb;
+    la.perm = perm;
+    la.tb = ctx->tb;
+    la.prel = as<float4>(ctx->prel);
+    la.loc = mixed ? ctx->loc32.ptr : ctx->loc.ptr;
+    jerk_leaves(la, mixed, mixed ? ctx->jloc32.ptr : ctx->jloc.ptr, as<double>(ctx->jv), as<float4>(ctx->jv32), jx,
+                jy, jz, st);
+    CK(cudaEventRecord(ctx->ev[9], st));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    unsigned err = 0;
+    CK(cudaMemcpy(&err, &ctx->ds->err, 4, cudaMemcpyDeviceToHost));
+    if (err) return fail(ctx, FMM_ERR_CAPACITY, "an internal list overflowed");
+    ctx->stats.ms_jerk = elapsed(ctx->ev[8], ctx->ev[9]);
+    return FMM_OK;
+}
+
 int check_cfg(const fmm_config* c, std::string& why) {
     if (!c) { why = "cfg is NULL"; return FMM_ERR_ARG; }
     if (c->p < 1 || c->p > kMaxP) { why = "p must be in [1, 30]"; return FMM_ERR_ARG; }
@@ -729,7 +800,8 @@ void fmm_destroy(fmm_ctx* ctx) {
                   &ctx->front0, &ctx->front1, &ctx->dcount, &ctx->zhi, &ctx->zlo, &ctx->contrib, &ctx->Phat, &ctx->r32,
                   &ctx->item_first, &ctx->slot_first, &ctx->item_leaf, &ctx->leaf_of, &ctx->part_hi,
                   &ctx->part_lo, &ctx->work, &ctx->coff, &ctx->box, &ctx->ck0, &ctx->ck1, &ctx->cv0,
-                  &ctx->cv1, &ctx->cid};
+                  &ctx->cv1, &ctx->cid, &ctx->jv, &ctx->jv32, &ctx->jw, &ctx->jmom, &ctx->jmult,
+                  &ctx->jmult32, &ctx->jloc, &ctx->jloc32};
     for (Buf* b : all) release(*b);
     drop_plan(ctx->plan);
     if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
@@ -758,6 +830,20 @@ int fmm_solve(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const d
         return fail(ctx, FMM_ERR_ARG, "NULL input or output pointer");
     cudaSetDevice(ctx->device);
     return solve_device(ctx, n, 1, nullptr, x, y, z, m, ax, ay, az, pot, (cudaStream_t)cuda_stream);
+}
+
+int fmm_solve_jerk(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z, const double* vx,
+                   const double* vy, const double* vz, const double* m, double* ax, double* ay, double* az,
+                   double* pot, double* jx, double* jy, double* jz, void* cuda_stream) {
+    if (!ctx) return FMM_ERR_ARG;
+    if (n < 0 || n > (int64_t)1 << 30) return fail(ctx, FMM_ERR_ARG, "n must be in [0, 2^30]");
+    if (n > 0 && (!x || !y || !z || !vx || !vy || !vz || !m || !ax || !ay || !az || !jx || !jy || !jz))
+        return fail(ctx, FMM_ERR_ARG, "NULL input or output pointer");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc = solve_device(ctx, n, 1, nullptr, x, y, z, m, ax, ay, az, pot, st);
+    if (rc != FMM_OK || n == 0) return rc;
+    return jerk_pass(ctx, vx, vy, vz, jx, jy, jz, st);
 }
 
 int fmm_solve_host(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,

@@ -372,6 +372,57 @@ __global__ void k_node_centres(const int* __restrict__ dnn, const double* __rest
 inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 
 TabF64 tab64(const DevTables& tb) { return TabF64{tb.w, tb.iw, tb.rec_a, tb.rec_b, tb.diag, tb.sub}; }
+
+// Hat multipoles of the point dipoles D_i = m_i v_i of a leaf (the jerk's
+// chi field): M_n^m = -sum_i D_i . grad Upsilon_n^m(x_i - z). With the ladder
+// relations d_z U_n^m = U_{n-1}^m, (d_x + i d_y) U_n^m = -U_{n-1}^{m+1},
+// (d_x - i d_y) U_n^m = U_{n-1}^{m-1}, this is
+//   M_n^m = -[ Z_{n-1}^m + (X + iY)_{n-1}^{m-1} / 2 + (-X + iY)_{n-1}^{m+1} / 2 ]
+// with X, Y, Z the order p-1 moments of the weights D_x, D_y, D_z. In the hat
+// basis (Xhat = X w / s^n) the degree ratios become
+// w_n^m / w_{n-1}^{m'} = sqrt((n+m)(n-m)), sqrt((n+m)(n+m-1)), sqrt((n-m)(n-m-1))
+// for m' = m, m-1, m+1, and one factor 1/s. One thread per leaf.
+__global__ void k_dipole_moments(TreeView t, int p, const double* __restrict__ X, const double* __restrict__ Y,
+                                 const double* __restrict__ Z, const double* __restrict__ hs,
+                                 double* __restrict__ mult) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= *t.dnn || t.nchild[k] != 0) return;
+    const int nr = ncoef_real(p), nq = ncoef_real(p - 1);
+    const double* x = X + (size_t)nq * k;
+    const double* y = Y + (size_t)nq * k;
+    const double* z = Z + (size_t)nq * k;
+    const double is = 1.0 / hs[k];
+    double* out = mult + (size_t)nr * k;
+    out[0] = 0.0;  // a dipole has no monopole
+    for (int n = 1; n <= p; ++n) {
+        for (int m = 0; m <= n; ++m) {
+            double re = 0.0, im = 0.0;
+            if (m <= n - 1) {  // Z_{n-1}^m
+                const double c = sqrt((double)((n + m) * (n - m)));
+                re += c * z[hre(n - 1, m)];
+                im += c * (m ? z[him(n - 1, m)] : 0.0);
+            }
+            if (m >= 1 || n >= 2) {  // (X + iY)_{n-1}^{m-1} / 2
+                const int ml = m - 1, am = ml < 0 ? -ml : ml;
+                double xr = x[hre(n - 1, am)], xi = am ? x[him(n - 1, am)] : 0.0;
+                double yr = y[hre(n - 1, am)], yi = am ? y[him(n - 1, am)] : 0.0;
+                if (ml < 0) { xr = -xr; yr = -yr; }  // X^{-1} = -conj(X^1): (-re, +im)
+                const double c = 0.5 * sqrt((double)((n + m) * (n + m - 1)));
+                re += c * (xr - yi);
+                im += c * (xi + yr);
+            }
+            if (m + 1 <= n - 1) {  // (-X + iY)_{n-1}^{m+1} / 2
+                const double xr = x[hre(n - 1, m + 1)], xi = x[him(n - 1, m + 1)];
+                const double yr = y[hre(n - 1, m + 1)], yi = y[him(n - 1, m + 1)];
+                const double c = 0.5 * sqrt((double)((n - m) * (n - m - 1)));
+                re += c * (-xr - yi);
+                im += c * (-xi + yr);
+            }
+            out[hre(n, m)] = -re * is;
+            if (m) out[him(n, m)] = -im * is;
+        }
+    }
+}
 }  // namespace
 
 void upload_expansion_tables(const HostTables& h) {
@@ -423,6 +474,20 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
     (void)h_level_start;
     for (int L = t.nlevels - 2; L >= 0; --L) m2m_level(t, L, p, zc, hs, mult, contrib, tbl, dword, st);
     (k_pnorm<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.dnn, p, mult, r, hs, Pk, Phat, r32), note_launch());
+}
+
+void p2m_weights(const TreeView& t, int p, const double* xs, const double* ys, const double* zs, const double* w,
+                 const double* zc, const double* hs, double* mult, const DevTables& tbl, cudaStream_t st) {
+    const TabF64 tb = tab64(tbl);
+    if (p <= 16)
+        (k_p2m<16, 4><<<152 * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, w, zc, hs, mult), note_launch());
+    else
+        (k_p2m<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, tb, xs, ys, zs, w, zc, hs, mult), note_launch());
+}
+
+void dipole_moments(const TreeView& t, int p, const double* X, const double* Y, const double* Z, const double* hs,
+                    double* mult, cudaStream_t st) {
+    (k_dipole_moments<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, p, X, Y, Z, hs, mult), note_launch());
 }
 
 void hat_scales(const TreeView& t, const int* parent, const double* r, double* hs, cudaStream_t st) {

@@ -225,6 +225,13 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
                  const double* ys, const double* zs, const double* ms, const double* zc,
                  const double* r, const double* hs, double* mult, double* Pk, float* Phat, float* r32,
                  double* contrib, const DevTables& tb, bool dword, cudaStream_t st);
+// FP64 hat P2M of the leaves with per-body weights w (in place of masses)
+void p2m_weights(const TreeView& t, int p, const double* xs, const double* ys, const double* zs, const double* w,
+                 const double* zc, const double* hs, double* mult, const DevTables& tb, cudaStream_t st);
+// hat multipoles (order p) of the point dipoles of each leaf from the order
+// p - 1 hat moments X, Y, Z of their x, y, z components (the jerk's chi field)
+void dipole_moments(const TreeView& t, int p, const double* X, const double* Y, const double* Z, const double* hs,
+                    double* mult, cudaStream_t st);
 // rotation-accelerated M2M of one level: the children (level L + 1) into their
 // parents (level L); contrib: (p+1)^2 doubles per node (scratch); dword:
 // double-word FP32 arithmetic instead of FP64
@@ -301,6 +308,15 @@ void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_
                cudaStream_t st);
 void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, const double* zs,
                        const double* ms, const double* zc, float4* prel, cudaStream_t st);
+// Jerk inputs in sorted order: velocities vs (3n, FP64) and v32 (FP32), and
+// the dipole weights w = m v (3n).
+void jerk_inputs(int n, const uint32_t* perm, const double* ms, const double* vx, const double* vy,
+                 const double* vz, double* vs, double* w, float4* v32, cudaStream_t st);
+// Jerk of every body: -grad chi from the dipole locals locj, the Hessian of
+// the mass locals a.loc times v_i, and the direct jerk over the P2P list;
+// G-scaled, to the caller's order through a.perm.
+void jerk_leaves(const LeafArgs& a, bool fp32, const void* locj, const double* vs, const float4* v32, double* jx,
+                 double* jy, double* jz, cudaStream_t st);
 // soft: Plummer softening length (0: Newtonian)
 void direct_sum_f64(int64_t n, const double* x, const double* y, const double* z, const double* m,
                     double G, double soft, int64_t ntgt, const int64_t* tgt, double* ax, double* ay, double* az,

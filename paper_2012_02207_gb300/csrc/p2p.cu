@@ -476,6 +476,204 @@ __global__ void __launch_bounds__(256) k_direct(int64_t n, const double* __restr
 }
 
 inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+// ---------------------------------------------------------------------------
+// Jerks (the time derivative of the acceleration). With Psi = sum_j m_j /
+// |x_j - x| (-phi without G), chi = sum_j m_j v_j . grad_x (1/|x_j - x|)
+// (the potential of point dipoles m_j v_j) and H the Hessian of Psi,
+//   j_i = G [ -grad chi(x_i) + H(x_i) v_i + near_i ],
+// near_i the direct jerk over the P2P leaf pairs. The far part of chi is one
+// more expansion through the same tree and lists; its gradient comes from
+// l2p_hat like the acceleration. H comes from the degree-2 coefficients of
+// the solve's own local expansion shifted to the body.
+
+// Fhat_n^m for m in [-n, n] from the real layout (X^{-m} = (-1)^m conj(X^m)).
+template <typename T>
+__device__ __forceinline__ void fget(const T* __restrict__ F, int n, int m, T& re, T& im) {
+    const int am = m < 0 ? -m : m;
+    re = F[hre(n, am)];
+    im = am ? F[him(n, am)] : T(0);
+    if (m < 0) {
+        if (am & 1) re = -re;
+        else im = -im;
+    }
+}
+
+// Hessian of Psi at dhat = d / s from a hat local F:
+//   F_2^m(x) = (1/s^2) sum_{k, l} conj(Shat_k^l(dhat)) w_{2+k}^{m+l} / w_k^l Fhat_{2+k}^{m+l}, m = 0, 1, 2
+// (the shift of the local to the body, degree 2), then
+//   xx = (Re F_2^2 - F_2^0)/2, yy = -(Re F_2^2 + F_2^0)/2, zz = F_2^0,
+//   xy = Im F_2^2 / 2, xz = Re F_2^1, yz = Im F_2^1.
+// h = {xx, yy, zz, xy, xz, yz}.
+template <typename T, typename Tab>
+__device__ void l2p_hess_hat(int p, const T* __restrict__ F, T x, T y, T z, T inv_s, const Tab& tb, T* h) {
+    const T r2 = x * x + y * y + z * z;
+    T gr[3] = {T(0), T(0), T(0)}, gi[3] = {T(0), T(0), T(0)};
+    T dre = T(1), dim = T(0);  // Shat_l^l
+    for (int l = 0; l <= p - 2; ++l) {
+        if (l > 0) {
+            const T t = dre * x - dim * y;
+            dim = dre * y + dim * x;
+            dre = t;
+            dre *= tb.D(l);
+            dim *= tb.D(l);
+        }
+        T s1r = dre, s1i = dim, s2r = T(0), s2i = T(0);
+        for (int k = l; k <= p - 2; ++k) {
+            T sr, si;
+            if (k == l) { sr = dre; si = dim; }
+            else if (k == l + 1) { sr = tb.Sb(l) * z * s1r; si = tb.Sb(l) * z * s1i; }
+            else {
+                const T a = tb.A(k, l) * z, b = tb.B(k, l) * r2;
+                sr = a * s1r - b * s2r;
+                si = a * s1i - b * s2i;
+            }
+            if (k > l) { s2r = s1r; s2i = s1i; s1r = sr; s1i = si; }
+            const T iw = tb.IW(k, l);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                // +l: conj(S) w_{2+k}^{m+l} Fhat_{2+k}^{m+l}
+                T fr, fi;
+                fget(F, 2 + k, m + l, fr, fi);
+                const T c = tb.W(2 + k, m + l) * iw;
+                gr[m] += c * (sr * fr + si * fi);
+                gi[m] += c * (sr * fi - si * fr);
+                if (l > 0) {
+                    // -l: conj(Shat_k^{-l}) = (-1)^l Shat_k^l, times w_{2+k}^{|m-l|} Fhat_{2+k}^{m-l}
+                    fget(F, 2 + k, m - l, fr, fi);
+                    const int am = m - l < 0 ? l - m : m - l;
+                    const T c2 = (l & 1 ? -tb.W(2 + k, am) : tb.W(2 + k, am)) * iw;
+                    gr[m] += c2 * (sr * fr - si * fi);
+                    gi[m] += c2 * (sr * fi + si * fr);
+                }
+            }
+        }
+    }
+    const T q = inv_s * inv_s;
+    const T f20 = gr[0] * q, f21r = gr[1] * q, f21i = gi[1] * q, f22r = gr[2] * q, f22i = gi[2] * q;
+    h[0] = T(0.5) * (f22r - f20);
+    h[1] = T(-0.5) * (f22r + f20);
+    h[2] = f20;
+    h[3] = T(0.5) * f22i;
+    h[4] = f21r;
+    h[5] = f21i;
+}
+
+// Sorted-order jerk inputs: velocities (FP64, and an FP32 copy for the mixed
+// near field) and the dipole weights m_i v_i.
+__global__ void k_jerk_inputs(int n, const uint32_t* __restrict__ perm, const double* __restrict__ ms,
+                              const double* __restrict__ vx, const double* __restrict__ vy,
+                              const double* __restrict__ vz, double* __restrict__ vs, double* __restrict__ w,
+                              float4* __restrict__ v32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t o = perm[i];
+    const double a = vx[o], b = vy[o], c = vz[o], m = ms[i];
+    vs[i] = a; vs[n + i] = b; vs[2 * (size_t)n + i] = c;
+    w[i] = m * a; w[n + i] = m * b; w[2 * (size_t)n + i] = m * c;
+    v32[i] = make_float4((float)a, (float)b, (float)c, 0.0f);
+}
+
+// One warp per target leaf, one lane per target body (32 at a time): far
+// part from the two local expansions, near part over the leaf's P2P list in
+// list order (FP64, or FP32 on leaf-relative positions with each source
+// leaf's partial added in FP64).
+template <typename T>
+__global__ void __launch_bounds__(128) k_jerk_leaf(LeafArgs a, const void* __restrict__ locj,
+                                                    const double* __restrict__ vs, const float4* __restrict__ v32,
+                                                    double* __restrict__ jx, double* __restrict__ jy,
+                                                    double* __restrict__ jz) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nr = ncoef_real(a.p);
+    const uint64_t mask = (1ull << a.nb) - 1ull;
+    const int n = a.t.n;
+    for (int B = warp, nn = *a.t.dnn; B < nn; B += nwarps) {
+        if (a.t.nchild[B] != 0) continue;
+        const int b0 = a.t.begin[B], b1 = a.t.end[B];
+        for (int i = b0 + lane; i - lane < b1; i += 32) {
+            const bool act = i < b1;
+            const int ii = act ? i : b0;
+            const double vix = vs[ii], viy = vs[n + ii], viz = vs[2 * (size_t)n + ii];
+            double fx, fy, fz;
+            T h[6];
+            T gx, gy, gz, phi;
+            if constexpr (sizeof(T) == 4) {
+                const TabL32 tb;
+                const float inv_s = 1.0f / a.zhi[B].w;
+                const float4 v = a.prel[ii];
+                const float ux = v.x * inv_s, uy = v.y * inv_s, uz = v.z * inv_s;
+                l2p_hat<float>(a.p, reinterpret_cast<const float*>(locj) + (size_t)nr * B, ux, uy, uz, inv_s, tb,
+                               phi, gx, gy, gz);
+                l2p_hess_hat<float>(a.p, reinterpret_cast<const float*>(a.loc) + (size_t)nr * B, ux, uy, uz, inv_s,
+                                    tb, h);
+            } else {
+                const TabL64 tb{a.tb.w, a.tb.iw, a.tb.rec_a, a.tb.rec_b, a.tb.diag, a.tb.sub};
+                const double inv_s = 1.0 / a.hs[B];
+                const double ux = (a.xs[ii] - a.zc[3 * B]) * inv_s, uy = (a.ys[ii] - a.zc[3 * B + 1]) * inv_s,
+                             uz = (a.zs[ii] - a.zc[3 * B + 2]) * inv_s;
+                l2p_hat<double>(a.p, reinterpret_cast<const double*>(locj) + (size_t)nr * B, ux, uy, uz, inv_s, tb,
+                                phi, gx, gy, gz);
+                l2p_hess_hat<double>(a.p, reinterpret_cast<const double*>(a.loc) + (size_t)nr * B, ux, uy, uz,
+                                     inv_s, tb, h);
+            }
+            (void)phi;
+            fx = -(double)gx + (double)h[0] * vix + (double)h[3] * viy + (double)h[4] * viz;
+            fy = -(double)gy + (double)h[3] * vix + (double)h[1] * viy + (double)h[5] * viz;
+            fz = -(double)gz + (double)h[4] * vix + (double)h[5] * viy + (double)h[2] * viz;
+            // near part
+            const float4 bh = a.zhi[B], bl = a.zlo[B];
+            const float4 ti = sizeof(T) == 4 ? a.prel[ii] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 tv = v32[ii];
+            for (uint32_t q = a.p2p_off[B]; q < a.p2p_off[B + 1]; ++q) {
+                const int A = (int)(a.p2p_keys[q] & mask);
+                const int a0 = a.t.begin[A], a1 = a.t.end[A];
+                if constexpr (sizeof(T) == 4) {
+                    const float4 ah = a.zhi[A], al = a.zlo[A];
+                    const float ox = (ah.x - bh.x) + (al.x - bl.x), oy = (ah.y - bh.y) + (al.y - bl.y),
+                                oz = (ah.z - bh.z) + (al.z - bl.z);
+                    float sx = 0.f, sy = 0.f, sz = 0.f;
+                    for (int j = a0; j < a1; ++j) {
+                        if (j == ii) continue;
+                        const float4 pj = a.prel[j], vj = v32[j];
+                        const float rx = (pj.x + ox) - ti.x, ry = (pj.y + oy) - ti.y, rz = (pj.z + oz) - ti.z;
+                        const float wx = vj.x - tv.x, wy = vj.y - tv.y, wz = vj.z - tv.z;
+                        const float r2 = rx * rx + ry * ry + rz * rz + a.soft2f;
+                        const float ri = rsqrtf(r2);
+                        const float ri2 = ri * ri;
+                        const float mr3 = pj.w * ri * ri2;
+                        const float c = 3.0f * (rx * wx + ry * wy + rz * wz) * ri2;
+                        sx += mr3 * (wx - c * rx);
+                        sy += mr3 * (wy - c * ry);
+                        sz += mr3 * (wz - c * rz);
+                    }
+                    fx += (double)sx; fy += (double)sy; fz += (double)sz;
+                } else {
+                    for (int j = a0; j < a1; ++j) {
+                        if (j == ii) continue;
+                        const double rx = a.xs[j] - a.xs[ii], ry = a.ys[j] - a.ys[ii], rz = a.zs[j] - a.zs[ii];
+                        const double wx = vs[j] - vix, wy = vs[n + j] - viy, wz = vs[2 * (size_t)n + j] - viz;
+                        const double r2 = rx * rx + ry * ry + rz * rz + a.soft2;
+                        const double ri = rsqrt_nr(r2);
+                        const double ri2 = ri * ri;
+                        const double mr3 = a.ms[j] * ri * ri2;
+                        const double c = 3.0 * (rx * wx + ry * wy + rz * wz) * ri2;
+                        fx += mr3 * (wx - c * rx);
+                        fy += mr3 * (wy - c * ry);
+                        fz += mr3 * (wz - c * rz);
+                    }
+                }
+            }
+            if (act) {
+                const uint32_t o = a.perm[i];
+                jx[o] = a.G * fx;
+                jy[o] = a.G * fy;
+                jz[o] = a.G * fz;
+            }
+        }
+    }
+}
 }  // namespace
 
 void upload_leaf_tables(const HostTables& h) {
@@ -530,6 +728,17 @@ void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_
         else (k_p2p_items<double, false><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
         (k_leaf_reduce<double><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch());
     }
+}
+
+void jerk_inputs(int n, const uint32_t* perm, const double* ms, const double* vx, const double* vy,
+                 const double* vz, double* vs, double* w, float4* v32, cudaStream_t st) {
+    if (n > 0) (k_jerk_inputs<<<blocks_for(n, 256), 256, 0, st>>>(n, perm, ms, vx, vy, vz, vs, w, v32), note_launch());
+}
+
+void jerk_leaves(const LeafArgs& a, bool fp32, const void* locj, const double* vs, const float4* v32, double* jx,
+                 double* jy, double* jz, cudaStream_t st) {
+    if (fp32) (k_jerk_leaf<float><<<152 * 8, 128, 0, st>>>(a, locj, vs, v32, jx, jy, jz), note_launch());
+    else (k_jerk_leaf<double><<<152 * 8, 128, 0, st>>>(a, locj, vs, v32, jx, jy, jz), note_launch());
 }
 
 void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, const double* zs,
