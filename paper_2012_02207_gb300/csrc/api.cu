@@ -660,8 +660,11 @@ int jerk_pass(fmm_ctx* ctx, const double* vx, const double* vy, const double* vz
     la.tb = ctx->tb;
     la.prel = as<float4>(ctx->prel);
     la.loc = mixed ? ctx->loc32.ptr : ctx->loc.ptr;
-    jerk_leaves(la, mixed, mixed ? ctx->jloc32.ptr : ctx->jloc.ptr, as<double>(ctx->jv), as<float4>(ctx->jv32), jx,
-                jy, jz, st);
+    la.part_hi = as<double2>(ctx->part_hi); la.part_lo = as<double2>(ctx->part_lo);
+    la.slots_cap = ctx->items_total[1];
+    jerk_leaves(la, mixed, mixed ? ctx->jloc32.ptr : ctx->jloc.ptr, as<double>(ctx->jv), as<float4>(ctx->jv32),
+                as<int>(ctx->item_leaf), as<uint32_t>(ctx->item_first), as<uint32_t>(ctx->slot_first),
+                as<uint32_t>(ctx->work) + 4, as<unsigned>(ctx->work), as<int>(ctx->leaf_of), jx, jy, jz, st);
     CK(cudaEventRecord(ctx->ev[9], st));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));

@@ -313,10 +313,12 @@ void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, co
 void jerk_inputs(int n, const uint32_t* perm, const double* ms, const double* vx, const double* vy,
                  const double* vz, double* vs, double* w, float4* v32, cudaStream_t st);
 // Jerk of every body: -grad chi from the dipole locals locj, the Hessian of
-// the mass locals a.loc times v_i, and the direct jerk over the P2P list;
-// G-scaled, to the caller's order through a.perm.
-void jerk_leaves(const LeafArgs& a, bool fp32, const void* locj, const double* vs, const float4* v32, double* jx,
-                 double* jy, double* jz, cudaStream_t st);
+// the mass locals a.loc times v_i, and the direct jerk over the P2P list (on
+// the solve's P2P work items, partials in a.part_hi/part_lo); G-scaled, to
+// the caller's order through a.perm.
+void jerk_leaves(const LeafArgs& a, bool fp32, const void* locj, const double* vs, const float4* v32,
+                 const int* item_leaf, const uint32_t* item_first, const uint32_t* slot_first, const uint32_t* nitems,
+                 unsigned* work, const int* leaf_of, double* jx, double* jy, double* jz, cudaStream_t st);
 // soft: Plummer softening length (0: Newtonian)
 void direct_sum_f64(int64_t n, const double* x, const double* y, const double* z, const double* m,
                     double G, double soft, int64_t ntgt, const int64_t* tgt, double* ax, double* ay, double* az,

@@ -574,105 +574,214 @@ __global__ void k_jerk_inputs(int n, const uint32_t* __restrict__ perm, const do
     v32[i] = make_float4((float)a, (float)b, (float)c, 0.0f);
 }
 
-// One warp per target leaf, one lane per target body (32 at a time): far
-// part from the two local expansions, near part over the leaf's P2P list in
-// list order (FP64, or FP32 on leaf-relative positions with each source
-// leaf's partial added in FP64).
-template <typename T>
-__global__ void __launch_bounds__(128) k_jerk_leaf(LeafArgs a, const void* __restrict__ locj,
-                                                    const double* __restrict__ vs, const float4* __restrict__ v32,
-                                                    double* __restrict__ jx, double* __restrict__ jy,
-                                                    double* __restrict__ jz) {
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int nr = ncoef_real(a.p);
+// Near jerk over the same bounded work items as the P2P (a target leaf and
+// at most kLeavesPerItem of its source leaves, fetched dynamically): source
+// positions and velocities staged per warp in shared memory, G lanes per
+// target, runs of kRun terms folded into the accumulators (two-sum pairs in
+// FP32), one partial per (item, body) in part_hi = (jx, jy), part_lo.x = jz.
+// k_jerk_reduce adds a body's partials in item order.
+template <typename T, bool SOFT>
+__device__ __forceinline__ void jerk_pack(const Body4<T>* __restrict__ sm, const Body4<T>* __restrict__ su, int cnt,
+                                          int sub, int G, T tx, T ty, T tz, T tvx, T tvy, T tvz, T s2,
+                                          NearAcc<T>& acc) {
+    for (int k0 = sub; k0 < cnt; k0 += kRun * G) {
+        const int k1 = k0 + kRun * G < cnt ? k0 + kRun * G : cnt;
+        T px = T(0), py = T(0), pz = T(0);
+#pragma unroll 4
+        for (int k = k0; k < k1; k += G) {
+            const Body4<T> sv = sm[k], uv = su[k];
+            const T dx = sv.x - tx, dy = sv.y - ty, dz = sv.z - tz;
+            const T wx = uv.x - tvx, wy = uv.y - tvy, wz = uv.z - tvz;
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            T rinv;
+            if constexpr (sizeof(T) == 4) rinv = rsqrtf(SOFT ? r2 + s2 : r2);
+            else rinv = rsqrt_nr(SOFT ? r2 + s2 : r2);
+            if (!(r2 > T(0))) rinv = T(0);  // the body itself
+            const T ri2 = rinv * rinv;
+            const T mr3 = sv.w * rinv * ri2;
+            const T c = T(3) * (dx * wx + dy * wy + dz * wz) * ri2;
+            px += mr3 * (wx - c * dx);
+            py += mr3 * (wy - c * dy);
+            pz += mr3 * (wz - c * dz);
+        }
+        acc.add(px, py, pz, T(0));
+    }
+}
+
+template <typename T, bool SOFT>
+__global__ void __launch_bounds__(128) k_jerk_items(LeafArgs a, const double* __restrict__ vs,
+                                                     const float4* __restrict__ v32, const int* __restrict__ item_leaf,
+                                                     const uint32_t* __restrict__ item_first,
+                                                     const uint32_t* __restrict__ slot_first,
+                                                     const uint32_t* __restrict__ nitems_p,
+                                                     unsigned* __restrict__ work) {
+    constexpr int kCap = sizeof(T) == 8 ? kStageCap / 2 : kStageCap;  // 32 KB of staging per block
+    __shared__ Body4<T> stage[4][kCap];
+    __shared__ Body4<T> vstage[4][kCap];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    Body4<T>* sm = stage[wib];
+    Body4<T>* su = vstage[wib];
     const uint64_t mask = (1ull << a.nb) - 1ull;
-    const int n = a.t.n;
-    for (int B = warp, nn = *a.t.dnn; B < nn; B += nwarps) {
-        if (a.t.nchild[B] != 0) continue;
-        const int b0 = a.t.begin[B], b1 = a.t.end[B];
-        for (int i = b0 + lane; i - lane < b1; i += 32) {
-            const bool act = i < b1;
-            const int ii = act ? i : b0;
-            const double vix = vs[ii], viy = vs[n + ii], viz = vs[2 * (size_t)n + ii];
-            double fx, fy, fz;
-            T h[6];
-            T gx, gy, gz, phi;
-            if constexpr (sizeof(T) == 4) {
-                const TabL32 tb;
-                const float inv_s = 1.0f / a.zhi[B].w;
-                const float4 v = a.prel[ii];
-                const float ux = v.x * inv_s, uy = v.y * inv_s, uz = v.z * inv_s;
-                l2p_hat<float>(a.p, reinterpret_cast<const float*>(locj) + (size_t)nr * B, ux, uy, uz, inv_s, tb,
-                               phi, gx, gy, gz);
-                l2p_hess_hat<float>(a.p, reinterpret_cast<const float*>(a.loc) + (size_t)nr * B, ux, uy, uz, inv_s,
-                                    tb, h);
-            } else {
-                const TabL64 tb{a.tb.w, a.tb.iw, a.tb.rec_a, a.tb.rec_b, a.tb.diag, a.tb.sub};
-                const double inv_s = 1.0 / a.hs[B];
-                const double ux = (a.xs[ii] - a.zc[3 * B]) * inv_s, uy = (a.ys[ii] - a.zc[3 * B + 1]) * inv_s,
-                             uz = (a.zs[ii] - a.zc[3 * B + 2]) * inv_s;
-                l2p_hat<double>(a.p, reinterpret_cast<const double*>(locj) + (size_t)nr * B, ux, uy, uz, inv_s, tb,
-                                phi, gx, gy, gz);
-                l2p_hess_hat<double>(a.p, reinterpret_cast<const double*>(a.loc) + (size_t)nr * B, ux, uy, uz,
-                                     inv_s, tb, h);
-            }
-            (void)phi;
-            fx = -(double)gx + (double)h[0] * vix + (double)h[3] * viy + (double)h[4] * viz;
-            fy = -(double)gy + (double)h[3] * vix + (double)h[1] * viy + (double)h[5] * viz;
-            fz = -(double)gz + (double)h[4] * vix + (double)h[5] * viy + (double)h[2] * viz;
-            // near part
-            const float4 bh = a.zhi[B], bl = a.zlo[B];
-            const float4 ti = sizeof(T) == 4 ? a.prel[ii] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 tv = v32[ii];
-            for (uint32_t q = a.p2p_off[B]; q < a.p2p_off[B + 1]; ++q) {
-                const int A = (int)(a.p2p_keys[q] & mask);
-                const int a0 = a.t.begin[A], a1 = a.t.end[A];
+    const int nitems = (int)*nitems_p;
+    const size_t n = (size_t)a.t.n;
+    const T s2 = sizeof(T) == 4 ? (T)a.soft2f : (T)a.soft2;
+    for (;;) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(work, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if ((int)it >= nitems) break;
+        const int B = item_leaf[it];
+        const int j = (int)(it - item_first[B]);
+        const uint32_t q0 = a.p2p_off[B] + (uint32_t)j * kLeavesPerItem;
+        const uint32_t qe = a.p2p_off[B + 1];
+        const uint32_t q1 = q0 + kLeavesPerItem < qe ? q0 + kLeavesPerItem : qe;
+        const int b0 = a.t.begin[B], nB = a.t.end[B] - b0;
+        const uint32_t slot0 = slot_first[B] + (uint32_t)j * (uint32_t)nB;
+        const float4 bh = a.zhi[B], bl = a.zlo[B];
+        for (int tc = 0; tc < nB; tc += 32) {
+            const int nt = nB - tc < 32 ? nB - tc : 32;
+            const int G = 32 / nt;
+            const int t = lane / G, sub = lane - t * G;
+            const bool act = t < nt;
+            T tx = T(0), ty = T(0), tz = T(0), tvx = T(0), tvy = T(0), tvz = T(0);
+            if (act) {
+                const int ib = b0 + tc + t;
                 if constexpr (sizeof(T) == 4) {
-                    const float4 ah = a.zhi[A], al = a.zlo[A];
-                    const float ox = (ah.x - bh.x) + (al.x - bl.x), oy = (ah.y - bh.y) + (al.y - bl.y),
-                                oz = (ah.z - bh.z) + (al.z - bl.z);
-                    float sx = 0.f, sy = 0.f, sz = 0.f;
-                    for (int j = a0; j < a1; ++j) {
-                        if (j == ii) continue;
-                        const float4 pj = a.prel[j], vj = v32[j];
-                        const float rx = (pj.x + ox) - ti.x, ry = (pj.y + oy) - ti.y, rz = (pj.z + oz) - ti.z;
-                        const float wx = vj.x - tv.x, wy = vj.y - tv.y, wz = vj.z - tv.z;
-                        const float r2 = rx * rx + ry * ry + rz * rz + a.soft2f;
-                        const float ri = rsqrtf(r2);
-                        const float ri2 = ri * ri;
-                        const float mr3 = pj.w * ri * ri2;
-                        const float c = 3.0f * (rx * wx + ry * wy + rz * wz) * ri2;
-                        sx += mr3 * (wx - c * rx);
-                        sy += mr3 * (wy - c * ry);
-                        sz += mr3 * (wz - c * rz);
-                    }
-                    fx += (double)sx; fy += (double)sy; fz += (double)sz;
+                    const float4 v = a.prel[ib], u = v32[ib];
+                    tx = v.x; ty = v.y; tz = v.z;
+                    tvx = u.x; tvy = u.y; tvz = u.z;
                 } else {
-                    for (int j = a0; j < a1; ++j) {
-                        if (j == ii) continue;
-                        const double rx = a.xs[j] - a.xs[ii], ry = a.ys[j] - a.ys[ii], rz = a.zs[j] - a.zs[ii];
-                        const double wx = vs[j] - vix, wy = vs[n + j] - viy, wz = vs[2 * (size_t)n + j] - viz;
-                        const double r2 = rx * rx + ry * ry + rz * rz + a.soft2;
-                        const double ri = rsqrt_nr(r2);
-                        const double ri2 = ri * ri;
-                        const double mr3 = a.ms[j] * ri * ri2;
-                        const double c = 3.0 * (rx * wx + ry * wy + rz * wz) * ri2;
-                        fx += mr3 * (wx - c * rx);
-                        fy += mr3 * (wy - c * ry);
-                        fz += mr3 * (wz - c * rz);
-                    }
+                    tx = a.xs[ib]; ty = a.ys[ib]; tz = a.zs[ib];
+                    tvx = vs[ib]; tvy = vs[n + ib]; tvz = vs[2 * n + ib];
                 }
             }
-            if (act) {
-                const uint32_t o = a.perm[i];
-                jx[o] = a.G * fx;
-                jy[o] = a.G * fy;
-                jz[o] = a.G * fz;
+            NearAcc<T> acc;
+            uint32_t q = q0;
+            int soff = 0;
+            while (q < q1) {
+                __syncwarp();
+                int cnt = 0;
+                while (q < q1) {
+                    const int A = (int)(a.p2p_keys[q] & mask);
+                    const int a0 = a.t.begin[A], nA = a.t.end[A] - a0;
+                    const int rem = nA - soff;
+                    int take = rem;
+                    if (cnt + take > kCap) {
+                        if (cnt > 0) break;
+                        take = kCap;
+                    }
+                    float ox = 0.f, oy = 0.f, oz = 0.f;
+                    if constexpr (sizeof(T) == 4) {
+                        const float4 ah = a.zhi[A], al = a.zlo[A];
+                        ox = (ah.x - bh.x) + (al.x - bl.x);
+                        oy = (ah.y - bh.y) + (al.y - bl.y);
+                        oz = (ah.z - bh.z) + (al.z - bl.z);
+                    }
+                    for (int l = lane; l < take; l += 32) {
+                        const int jj = a0 + soff + l;
+                        if constexpr (sizeof(T) == 4) {
+                            const float4 u = a.prel[jj], w = v32[jj];
+                            sm[cnt + l] = {u.x + ox, u.y + oy, u.z + oz, u.w};
+                            su[cnt + l] = {w.x, w.y, w.z, 0.0f};
+                        } else {
+                            sm[cnt + l] = {a.xs[jj], a.ys[jj], a.zs[jj], a.ms[jj]};
+                            su[cnt + l] = {vs[jj], vs[n + jj], vs[2 * n + jj], 0.0};
+                        }
+                    }
+                    cnt += take;
+                    if (take < rem) { soff += take; break; }
+                    soff = 0;
+                    ++q;
+                }
+                __syncwarp();
+                if (act) jerk_pack<T, SOFT>(sm, su, cnt, sub, G, tx, ty, tz, tvx, tvy, tvz, s2, acc);
+            }
+            // combine the G sub-lanes of each target in sub-lane order
+            const int leader = t * G;
+            for (int s = 1; s < G; ++s) {
+                const int src = leader + s < 32 ? leader + s : 31;
+                if constexpr (sizeof(T) == 4) {
+                    const float vx = __shfl_sync(0xffffffffu, acc.hx, src), vy = __shfl_sync(0xffffffffu, acc.hy, src),
+                                vz = __shfl_sync(0xffffffffu, acc.hz, src);
+                    const float wx = __shfl_sync(0xffffffffu, acc.lx, src), wy = __shfl_sync(0xffffffffu, acc.ly, src),
+                                wz = __shfl_sync(0xffffffffu, acc.lz, src);
+                    if (sub == 0 && act) {
+                        two_sum(acc.hx, acc.lx, vx); acc.lx += wx;
+                        two_sum(acc.hy, acc.ly, vy); acc.ly += wy;
+                        two_sum(acc.hz, acc.lz, vz); acc.lz += wz;
+                    }
+                } else {
+                    const double vx = __shfl_sync(0xffffffffu, acc.dx, src), vy = __shfl_sync(0xffffffffu, acc.dy, src),
+                                 vz = __shfl_sync(0xffffffffu, acc.dz, src);
+                    if (sub == 0 && act) { acc.dx += vx; acc.dy += vy; acc.dz += vz; }
+                }
+            }
+            if (act && sub == 0) {
+                const uint32_t slot = slot0 + (uint32_t)(tc + t);
+                if constexpr (sizeof(T) == 4) {
+                    a.part_hi[slot] = make_double2((double)acc.hx + (double)acc.lx, (double)acc.hy + (double)acc.ly);
+                    a.part_lo[slot] = make_double2((double)acc.hz + (double)acc.lz, 0.0);
+                } else {
+                    a.part_hi[slot] = make_double2(acc.dx, acc.dy);
+                    a.part_lo[slot] = make_double2(acc.dz, 0.0);
+                }
             }
         }
     }
+}
+
+// One thread per body: -grad chi from the dipole locals and the Hessian of
+// the mass locals times v_i, plus the near partials of its leaf's items in
+// item order; G-scaled, to the caller's order.
+template <typename T>
+__global__ void __launch_bounds__(128) k_jerk_reduce(LeafArgs a, const void* __restrict__ locj,
+                                                      const double* __restrict__ vs, const int* __restrict__ leaf_of,
+                                                      const uint32_t* __restrict__ item_first,
+                                                      const uint32_t* __restrict__ slot_first,
+                                                      double* __restrict__ jx, double* __restrict__ jy,
+                                                      double* __restrict__ jz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.t.n) return;
+    const int n = a.t.n;
+    const int B = leaf_of[i];
+    const int b0 = a.t.begin[B], nB = a.t.end[B] - b0;
+    const int nr = ncoef_real(a.p);
+    T h[6];
+    T gx, gy, gz, phi;
+    if constexpr (sizeof(T) == 4) {
+        const TabL32 tb;
+        const float inv_s = 1.0f / a.zhi[B].w;
+        const float4 v = a.prel[i];
+        const float ux = v.x * inv_s, uy = v.y * inv_s, uz = v.z * inv_s;
+        l2p_hat<float>(a.p, reinterpret_cast<const float*>(locj) + (size_t)nr * B, ux, uy, uz, inv_s, tb, phi, gx,
+                       gy, gz);
+        l2p_hess_hat<float>(a.p, reinterpret_cast<const float*>(a.loc) + (size_t)nr * B, ux, uy, uz, inv_s, tb, h);
+    } else {
+        const TabL64 tb{a.tb.w, a.tb.iw, a.tb.rec_a, a.tb.rec_b, a.tb.diag, a.tb.sub};
+        const double inv_s = 1.0 / a.hs[B];
+        const double ux = (a.xs[i] - a.zc[3 * B]) * inv_s, uy = (a.ys[i] - a.zc[3 * B + 1]) * inv_s,
+                     uz = (a.zs[i] - a.zc[3 * B + 2]) * inv_s;
+        l2p_hat<double>(a.p, reinterpret_cast<const double*>(locj) + (size_t)nr * B, ux, uy, uz, inv_s, tb, phi, gx,
+                        gy, gz);
+        l2p_hess_hat<double>(a.p, reinterpret_cast<const double*>(a.loc) + (size_t)nr * B, ux, uy, uz, inv_s, tb, h);
+    }
+    (void)phi;
+    const double vix = vs[i], viy = vs[n + i], viz = vs[2 * (size_t)n + i];
+    double fx = -(double)gx + (double)h[0] * vix + (double)h[3] * viy + (double)h[4] * viz;
+    double fy = -(double)gy + (double)h[3] * vix + (double)h[1] * viy + (double)h[5] * viz;
+    double fz = -(double)gz + (double)h[4] * vix + (double)h[5] * viy + (double)h[2] * viz;
+    const uint32_t i0 = item_first[B], i1 = item_first[B + 1];
+    const uint32_t s0 = slot_first[B] + (uint32_t)(i - b0);
+    for (uint32_t it = i0; it < i1; ++it) {
+        const uint32_t slot = s0 + (it - i0) * (uint32_t)nB;
+        if (slot >= a.slots_cap) break;
+        const double2 u = a.part_hi[slot], w = a.part_lo[slot];
+        fx += u.x; fy += u.y; fz += w.x;
+    }
+    const uint32_t o = a.perm[i];
+    jx[o] = a.G * fx;
+    jy[o] = a.G * fy;
+    jz[o] = a.G * fz;
 }
 }  // namespace
 
@@ -735,10 +844,20 @@ void jerk_inputs(int n, const uint32_t* perm, const double* ms, const double* vx
     if (n > 0) (k_jerk_inputs<<<blocks_for(n, 256), 256, 0, st>>>(n, perm, ms, vx, vy, vz, vs, w, v32), note_launch());
 }
 
-void jerk_leaves(const LeafArgs& a, bool fp32, const void* locj, const double* vs, const float4* v32, double* jx,
-                 double* jy, double* jz, cudaStream_t st) {
-    if (fp32) (k_jerk_leaf<float><<<152 * 8, 128, 0, st>>>(a, locj, vs, v32, jx, jy, jz), note_launch());
-    else (k_jerk_leaf<double><<<152 * 8, 128, 0, st>>>(a, locj, vs, v32, jx, jy, jz), note_launch());
+void jerk_leaves(const LeafArgs& a, bool fp32, const void* locj, const double* vs, const float4* v32,
+                 const int* item_leaf, const uint32_t* item_first, const uint32_t* slot_first, const uint32_t* nitems,
+                 unsigned* work, const int* leaf_of, double* jx, double* jy, double* jz, cudaStream_t st) {
+    cudaMemsetAsync(work, 0, sizeof(unsigned), st);
+    const bool soft = a.soft2 > 0.0;
+    if (fp32) {
+        if (soft) (k_jerk_items<float, true><<<152 * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        else (k_jerk_items<float, false><<<152 * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        (k_jerk_reduce<float><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, locj, vs, leaf_of, item_first, slot_first, jx, jy, jz), note_launch());
+    } else {
+        if (soft) (k_jerk_items<double, true><<<152 * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        else (k_jerk_items<double, false><<<152 * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        (k_jerk_reduce<double><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, locj, vs, leaf_of, item_first, slot_first, jx, jy, jz), note_launch());
+    }
 }
 
 void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, const double* zs,
