@@ -10,7 +10,7 @@
  *
  * Everything is FP64 except the scalar-force estimate f, which the MAC uses
  * only as an estimate (Section 2.3) and which is evaluated in FP32 with a
- * fixed operation order (reading R7 of the design notes). Compile with
+ * fixed operation order (the paper fixes neither). Compile with
  * -ffp-contract=off so that no multiply-add is fused.
  *
  * Notation follows Section 2.2 of the paper and the solid harmonics of
@@ -32,7 +32,7 @@
  * form.
  *
  * Plummer softening (Appendix B: phi(r) = -G m / sqrt(r^2 + eps_soft^2)).
- * The paper gives only the kernel; the reading here (R17 of the design notes):
+ * The paper gives only the kernel; the reading here:
  *  - the direct sum, P2P and the near part of f use the softened kernel;
  *  - the far field stays the multipole expansion of 1/r;
  *  - the MAC adds, on each side, the bound of what that omits: for bodies
@@ -88,7 +88,7 @@ static inline cplx getc(const cplx* a, int n, int m) {
 }
 
 /* Regular solid harmonics Upsilon_n^m(x,y,z), 0 <= m <= n <= p, by the
- * recurrences of Dehnen (2014) eqs. 52-54 as restated in the design notes:
+ * recurrences of Dehnen (2014) eqs. 52-54, which the paper cites:
  *   U_0^0 = 1, U_m^m = (x+iy) U_{m-1}^{m-1} / (2m), U_{m+1}^m = z U_m^m,
  *   U_n^m = [(2n-1) z U_{n-1}^m - r^2 U_{n-2}^m] / ((n+m)(n-m)).          */
 void orc_regular(int p, double x, double y, double z, cplx* out) {
@@ -435,7 +435,7 @@ static int cmp_keyidx(const void* a, const void* b) {
 
 static inline double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-/* Bounding cube (reading R1): centre c = (min+max)/2 per axis, half-size
+/* Bounding cube: centre c = (min+max)/2 per axis, half-size
  * h = max_axis (max-min)/2; quantise (x - (c-h)) / (2h) * 2^21, clamp to
  * [0, 2^21 - 1]; interleave with x in the high bit of each 3-bit digit. */
 static void build_keys(orc_state* s, const double* x, const double* y, const double* z) {
@@ -483,7 +483,7 @@ static inline int digit_at(uint64_t key, int level) { /* level 1..21 */
     return (int)((key >> (3 * (ORC_MAXLEVEL - level))) & 7);
 }
 
-/* Octree (reading R2): split a node while it holds more than leaf_size
+/* Octree: split a node while it holds more than leaf_size
  * particles and is above level 21; empty children are omitted; nodes are
  * numbered level by level and, within a level, in key order (breadth-first). */
 static void build_nodes(orc_state* s) {
@@ -535,7 +535,7 @@ static void build_nodes(orc_state* s) {
 
 static inline int is_leaf(const orc_state* s, int32_t a) { return s->nchild[a] == 0; }
 
-/* Coincident particles (reading R14): two particles at exactly the same
+/* Coincident particles: two particles at exactly the same
  * position. They share a key, so they sit in the same run of equal keys. */
 static int check_coincident(const orc_state* s) {
     int64_t n = s->n, i = 0;
@@ -550,7 +550,7 @@ static int check_coincident(const orc_state* s) {
     return 0;
 }
 
-/* Cell geometry (readings R3, R4): mass M_A, mass moment S_A = sum m x, the
+/* Cell geometry: mass M_A, mass moment S_A = sum m x, the
  * expansion centre z_A = S_A / M_A (centre of mass) and size r_A. For a leaf
  * the sums run over its particles in sorted order and r_A is the largest
  * particle distance from z_A; an internal cell sums its children's M and S in
@@ -640,7 +640,7 @@ static void push_pair(int32_t** arr, int64_t* cnt, int64_t* cap, int32_t a, int3
     ++*cnt;
 }
 
-/* Geometric part of the MAC (reading R6): theta = (r_A + r_B)/r < 1 with
+/* Geometric part of the MAC: theta = (r_A + r_B)/r < 1 with
  * r = |z_A - z_B|, tested as r_A + r_B < r. */
 static inline int theta_ok(const orc_state* s, int32_t a, int32_t b, double* r2out, double* rout) {
     const double* za = s->zc + 3 * a;
@@ -652,7 +652,7 @@ static inline int theta_ok(const orc_state* s, int32_t a, int32_t b, double* r2o
     return s->r[a] + s->r[b] < r;
 }
 
-/* E_{A->B} M_A / r^2 of Sec. 2.3 (reading R8):
+/* E_{A->B} M_A / r^2 of Sec. 2.3:
  *   [8 max(r_A,r_B)/(r_A+r_B)] * sum_{k=0}^{p} C(p,k) P_{k,A} r_B^{p-k} / (r^p r^2),
  * the sum in Horner form over k ascending, r^p by repeated multiplication,
  * and the prefactor taken as 4 when r_A + r_B = 0. */
@@ -669,7 +669,7 @@ static inline double mac_lhs(const orc_state* s, int32_t a, int32_t b, double r2
     return pre * h / (rp * r2);
 }
 
-/* Bound on the softening the far field leaves out (reading R17):
+/* Bound on the softening the far field leaves out:
  * 1.5 M_A soft^2 / d_min^4, d_min = r - r_A - r_B (> 0 once theta < 1). */
 static inline double soft_bound(const orc_state* s, int32_t a, int32_t b, double r) {
     double dmin = r - s->r[a] - s->r[b];
@@ -694,7 +694,7 @@ static int mac_eps(orc_state* s, int32_t a, int32_t b) {
     return lab < s->eps * (double)s->fmin[b] && lba < s->eps * (double)s->fmin[a];
 }
 
-/* Dual-tree walk (reading R9): a self pair of a leaf goes to P2P, of an
+/* Dual-tree walk: a self pair of a leaf goes to P2P, of an
  * internal cell to the pairs (C_i, C_j), i <= j, of its children; another
  * pair is accepted by the MAC, or, if both cells are leaves, goes to P2P, or
  * else the cell with the larger r is split (A on a tie; never a leaf). */
@@ -769,8 +769,8 @@ static void partner_csr(int32_t nnodes, int64_t npairs, const int32_t* pairs,
     *idx_out = idx;
 }
 
-/* Scalar-force estimate f_i = sum_{j != i} m_j / |x_i - x_j|^2 (Sec. 2.3,
- * reading R7), in FP32 with a fixed order:
+/* Scalar-force estimate f_i = sum_{j != i} m_j / |x_i - x_j|^2 (Sec. 2.3),
+ * in FP32 with a fixed order (the paper fixes neither):
  *  - a walk with theta < 1 only; an accepted pair adds M_A/r^2 to cell B and
  *    M_B/r^2 to cell A, with r^2 from the FP32-rounded centre offsets;
  *    a cell sums its terms over its partners in ascending node order;
@@ -854,7 +854,7 @@ static void scalar_force(orc_state* s) {
     free(far); free(g);
 }
 
-/* Far field: M2L both ways for every accepted pair (reading R11), gathered
+/* Far field: M2L both ways for every accepted pair, gathered
  * per target; L2L down; L2P per particle. Near field: P2P over leaf pairs,
  * both directions, and within a leaf over j != i, softened when soft > 0. */
 static void forces(orc_state* s) {
@@ -927,7 +927,8 @@ static void forces(orc_state* s) {
 }
 
 /* Jerk (the time derivative of the acceleration) on the tree and lists of a
- * full solve, as a sum of three parts (derivation in the design notes):
+ * full solve. With T(y) = grad_y (y / |y|^3) = -grad grad (1 / |y|), the jerk
+ * G sum_j m_j T(x_j - x_i) (v_j - v_i) splits into three parts:
  *   j_i = G [ -grad chi(x_i) + H(x_i) v_i + near_i ]
  *  - chi(x) = sum_j m_j v_j . grad_x (1 / |x_j - x|) is the potential of
  *    point dipoles m_j v_j; its far part is one more expansion through the

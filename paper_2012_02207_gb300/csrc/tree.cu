@@ -5,7 +5,7 @@
 // and keys are exactly those of a plain sequential evaluation of the same
 // formulas.
 //
-// Octree (Fig. 1, Sec. 2.1; readings R1, R2): a node is split while it holds
+// Octree (Fig. 1, Sec. 2.1): a node is split while it holds
 // more than leaf_size bodies and is above level 21; empty children are
 // omitted; nodes are numbered level by level, in key order inside a level.
 // The build needs no per-level loop: with lcp_i the number of leading 3-bit
@@ -69,7 +69,7 @@ __global__ void k_bbox_partial(const double* __restrict__ x, const double* __res
     if (bad) atomicOr(err, kErrNonfinite);
 }
 
-// Cube of each cluster (reading R1): centre c = (min+max)/2 per axis,
+// Cube of each cluster: centre c = (min+max)/2 per axis,
 // half-size h = the largest (max-min)/2 (h = 1 if all its bodies coincide,
 // e.g. one body). box[8c ..]: cx, cy, cz, h, lox, loy, loz, size.
 __global__ void k_bbox_final(const double* __restrict__ part, int nclusters, int slices,

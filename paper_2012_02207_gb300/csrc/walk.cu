@@ -4,7 +4,7 @@
 // one IEEE operation per source operation, in program order, so the
 // decisions are a plain function of the cell data.
 //
-// The walk (Sec. 2.1; reading R9) runs level-synchronously: each launch
+// The walk (Sec. 2.1) runs level-synchronously: each launch
 // classifies every pair of the current frontier and appends, with
 // warp-aggregated atomics, the accepted pairs, the leaf pairs and the child
 // pairs of the next frontier. The order of the lists is therefore not fixed;
@@ -34,7 +34,7 @@ struct WalkCells {
     const float* Phat;
     // Plummer softening (Appendix B): the MAC adds 1.5 M_A soft^2 / d_min^4,
     // d_min = r - r_A - r_B, the bound on what the Newtonian far field leaves
-    // out (reading R17); soft2 = 0 skips it
+    // out; soft2 = 0 skips it
     const double* M;
     double soft2;
     float soft2f;
@@ -63,7 +63,7 @@ __device__ __forceinline__ float mac_lhs32(const WalkCells& c, int a, float ra, 
     return pre * h * ir * ir;
 }
 
-// E_{A->B} M_A / r^2 of Sec. 2.3 (reading R8), Horner over k ascending.
+// E_{A->B} M_A / r^2 of Sec. 2.3, Horner over k ascending.
 __device__ double mac_lhs(const WalkCells& c, int a, double ra, double rb, double r, double r2) {
     const double sum = ra + rb;
     const double pre = (sum > 0.0) ? 8.0 * (ra > rb ? ra : rb) / sum : 4.0;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_walk_step(WalkCells c, const int2* __re
                 double r2 = 0.0, r = 0.0;
                 bool have64 = false;
                 if (theta == 2) {
-                    // theta = (r_A + r_B)/r < 1 in FP64 (reading R6)
+                    // theta = (r_A + r_B)/r < 1 in FP64
                     const double* za = c.zc + 3 * a;
                     const double* zb = c.zc + 3 * b;
                     const double dx = zb[0] - za[0], dy = zb[1] - za[1], dz = zb[2] - za[2];
@@ -365,7 +365,7 @@ __global__ void k_near_f(TreeView t, const float4* __restrict__ xf, const uint64
             const float r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 > 0.0f)) continue;
             if (soft2f > 0.0f) {
-                // softened magnitude m r / (r^2 + soft^2)^{3/2} (reading R17)
+                // softened magnitude m r / (r^2 + soft^2)^{3/2}
                 const float s2 = r2 + soft2f;
                 acc = acc + pj.w * sqrtf(r2) / (s2 * sqrtf(s2));
             } else {

@@ -86,7 +86,7 @@ def test_fp64_forces_match_oracle_fmm(n, p, eps):
     _, acc, pot = solve(pos, m, p=p, eps=eps, precision="fp64")
     oacc, opot = oracle.fmm(pos, m, p=p, eps=eps)
     # per-body relative error; bodies near the centre have |a| << sum |a_j|, so
-    # the error is also measured against the scalar force estimate (reading R16)
+    # the error is also measured against the scalar force estimate f_i of Sec. 2.3
     run = oracle.OracleRun(pos, m, p=p, eps=eps, stage=oracle.STAGE_F)
     fi = np.empty(n)
     fi[run.tree()["perm"]] = run.geometry()["f"]

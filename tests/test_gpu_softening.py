@@ -1,6 +1,6 @@
 """Plummer softening (Appendix B): the CUDA path against the CPU oracle.
 
-The reading (R17): P2P, the direct sum and the near part of the scalar-force
+The reading of Appendix B: P2P, the direct sum and the near part of the scalar-force
 estimate use the softened kernel 1/sqrt(r^2 + soft^2); the far field stays
 the multipole expansion of 1/r, and the MAC adds, on each side, the bound
 1.5 M_A soft^2 / d_min^4 on what that leaves out.
