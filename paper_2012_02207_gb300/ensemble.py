@@ -78,6 +78,24 @@ class Ensemble:
             ts.append(e0.elapsed_time(e1))
         return out, min(ts)
 
+    def time_graph(self, fmm, steps=5):
+        """The same forest solve replayed from a captured CUDA graph
+        (fmm_solve_graph): the first call solves and captures, the timed calls
+        replay (one graph launch and one status read each, host to host)."""
+        import time  # noqa: PLC0415
+
+        import torch  # noqa: PLC0415
+        out = tuple(torch.empty(self.n, dtype=torch.float64, device=self.dev) for _ in range(4))
+        for _ in range(2):
+            fmm.solve_graph(*self.cols, self.mass, out=out, offsets=self.offsets)
+        ts = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fmm.solve_graph(*self.cols, self.mass, out=out, offsets=self.offsets)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return out, min(ts), fmm.stats()["graph_replays"] == 1
+
     def time_loop(self, make, steps=2):
         """The same clusters solved one after the other (one solve per cluster)."""
         import torch  # noqa: PLC0415
@@ -138,6 +156,11 @@ def main():
     ap.add_argument("--sample", type=int, default=0,
                     help="bodies per cluster in the error check (0: all; the RMS hangs on a few outliers)")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner and use --leaf, --p, --eps")
+    ap.add_argument("--leaf", type=int, default=128)
+    ap.add_argument("--p", type=int, default=12)
+    ap.add_argument("--eps", type=float, default=3e-8)
     args = ap.parse_args()
 
     def log(s):
@@ -146,7 +169,9 @@ def main():
     offsets, pos, mass, sizes, _ = ics.ensemble(args.clusters, args.seed)
     ens = Ensemble(offsets, pos, mass, sample=args.sample)
     k = args.clusters if args.tune_clusters <= 0 else min(args.tune_clusters, args.clusters)
-    if k == args.clusters:
+    if args.no_tune:
+        best, trials, k = {"leaf": args.leaf, "p": args.p, "eps": args.eps}, [], 0
+    elif k == args.clusters:
         best, trials = autotune(ens, args.target, log=log)
     else:
         tune_ens = Ensemble(offsets[:k + 1], pos[:offsets[k]], mass[:offsets[k]], sample=args.sample)
@@ -156,12 +181,17 @@ def main():
     out, ms = ens.time_batch(f, steps=5)
     rms = ens.errors(out)
     st = f.stats()
+    g = FMM(p=best["p"], eps=best["eps"], leaf_size=best["leaf"], precision="mixed")
+    gout, ms_graph, replayed = ens.time_graph(g)
+    graph_equal = all(bool((a == b).all()) for a, b in zip(gout, out))
     _, ms_loop = ens.time_loop(lambda: FMM(p=best["p"], eps=best["eps"], leaf_size=best["leaf"], precision="mixed"))
     doc = {"workload": f"ensemble of {args.clusters} Plummer clusters, N_c = floor(2^U[10,17]) (seed {args.seed}, "
                        f"cluster c drawn with seed 1000+c), virial radii U[0.5,2], equal masses 1/N_c",
            "n_bodies": ens.n, "precision": "mixed", "target_rms": args.target,
            "tuned_on_clusters": k, "tuned": best,
            "forest_ms": ms, "forest_particles_per_s": ens.n / (ms * 1e-3),
+           "graph_replay_ms_host": ms_graph, "graph_particles_per_s": ens.n / (ms_graph * 1e-3),
+           "graph_replayed": replayed, "graph_equals_batch": graph_equal,
            "loop_ms": ms_loop, "loop_particles_per_s": ens.n / (ms_loop * 1e-3),
            "worst_cluster_rms": float(rms.max()), "median_cluster_rms": float(np.median(rms)),
            "kernel_launches_forest": st["kernel_launches"], "nnodes": st["nnodes"],
