@@ -83,6 +83,14 @@ def lib():
             L.orc_l2p_hessian.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, dp]
             L.orc_jerk.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp, dp]
+            L.orc_tau_pair.argtypes = [ctypes.c_double] * 9 + [ctypes.c_int]
+            L.orc_tau_pair.restype = ctypes.c_double
+            L.orc_hold.argtypes = [ctypes.c_int64] + [dp] * 7 + [ctypes.c_double] * 3 + [ctypes.c_int, ctypes.c_double,
+                                                                                     ctypes.c_int64, ctypes.c_double,
+                                                                                     ctypes.POINTER(ctypes.c_int64)]
+            L.orc_taus.argtypes = [ctypes.c_int64] + [dp] * 7 + [ctypes.c_double] * 2 + [ctypes.c_int, dp]
+            L.orc_energy.argtypes = [ctypes.c_int64] + [dp] * 7 + [ctypes.c_double] * 2
+            L.orc_energy.restype = ctypes.c_double
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_mac_values.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, dp]
             _lib = L
@@ -221,6 +229,42 @@ def l2p_hessian(p, F, d):
     h = np.zeros(6)
     lib().orc_l2p_hessian(p, F.ctypes.data, *map(float, d), _dp(h))
     return h
+
+
+# ------------------------------------------------------------- integrator
+
+def tau_pair(r, v, mij, G=1.0, eta=0.03, sym=False):
+    """Step size of a pair (Appendix A): separation r, relative velocity v."""
+    return lib().orc_tau_pair(*map(float, r), *map(float, v), float(mij), float(G), float(eta), int(bool(sym)))
+
+
+def taus(pos, vel, mass, eta=0.03, sym=False, G=1.0):
+    """Per-body step size: min over the other bodies of tau_pair."""
+    pos, vel = _c(pos), _c(vel)
+    cols = [np.ascontiguousarray(pos[:, d]) for d in range(3)] + [np.ascontiguousarray(vel[:, d]) for d in range(3)]
+    out = np.zeros(len(mass))
+    lib().orc_taus(len(mass), *(_dp(a) for a in cols), _dp(_c(mass)), float(G), float(eta), int(bool(sym)), _dp(out))
+    return out
+
+
+def hold(pos, vel, mass, dt, nsteps, eta=0.03, sym=True, G=1.0, soft=0.0, dt_min=0.0):
+    """nsteps HOLD steps (Appendix A) with direct FP64 forces. Returns the new
+    positions and velocities and {kicks, pair force evaluations, deepest level}."""
+    pos, vel = _c(pos).copy(), _c(vel).copy()
+    cols = [np.ascontiguousarray(pos[:, d]) for d in range(3)] + [np.ascontiguousarray(vel[:, d]) for d in range(3)]
+    m = _c(mass)
+    st = np.zeros(3, dtype=np.int64)
+    lib().orc_hold(len(m), *(_dp(a) for a in cols), _dp(m), float(G), float(soft), float(eta), int(bool(sym)),
+                   float(dt), int(nsteps), float(dt_min), st.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return (np.stack(cols[:3], 1), np.stack(cols[3:], 1),
+            {"kicks": int(st[0]), "pair_forces": int(st[1]), "max_depth": int(st[2])})
+
+
+def energy(pos, vel, mass, G=1.0, soft=0.0):
+    """Kinetic plus potential energy, direct FP64."""
+    pos, vel = _c(pos), _c(vel)
+    cols = [np.ascontiguousarray(pos[:, d]) for d in range(3)] + [np.ascontiguousarray(vel[:, d]) for d in range(3)]
+    return lib().orc_energy(len(mass), *(_dp(a) for a in cols), _dp(_c(mass)), float(G), float(soft))
 
 
 # ------------------------------------------------------------------- solve

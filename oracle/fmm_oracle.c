@@ -391,6 +391,196 @@ void orc_direct_jerk(int64_t n, const double* x, const double* y, const double* 
     }
 }
 
+/* ----------------------------------------------- HOLD integrator (App. A) */
+
+/* Step size of body i against body j (Appendix A): the smaller of the
+ * free-fall time eta sqrt(r / a) with a = G (m_i + m_j) / r^2 and the fly-by
+ * time eta r / v (r, v: separation and relative speed). With sym != 0 each is
+ * replaced by tau / (1 - tau'/2) (Eq. step_symm), tau' its time derivative
+ * along the two-body motion: for the free-fall time 1.5 tau (r . v) / r^2,
+ * for the fly-by time tau ((r . v) / r^2 - (v . a_rel) / v^2) with the
+ * two-body relative acceleration a_rel = -G (m_i + m_j) r / r^3. The
+ * derivative is capped at 1 (the factor at 2) where the paper gives no rule.
+ * Plain FP64, one IEEE operation per source operation (no contraction). */
+double orc_tau_pair(double rx, double ry, double rz, double ux, double uy, double uz, double mij, double G,
+                    double eta, int sym) {
+    double r2 = rx * rx + ry * ry + rz * rz;
+    double r = sqrt(r2);
+    double v2 = ux * ux + uy * uy + uz * uz;
+    double v = sqrt(v2);
+    double gm = G * mij;
+    double tff = eta * sqrt(r2 * r / gm);
+    double tfl = v > 0.0 ? eta * r / v : INFINITY;
+    if (sym) {
+        double rv = rx * ux + ry * uy + rz * uz;
+        double dff = 1.5 * tff * rv / r2;
+        if (dff > 1.0) dff = 1.0;
+        tff = tff / (1.0 - 0.5 * dff);
+        if (v > 0.0) {
+            double va = -gm * rv / (r2 * r);  /* v . a_rel */
+            double dfl = tfl * (rv / r2 - va / v2);
+            if (dfl > 1.0) dfl = 1.0;
+            tfl = tfl / (1.0 - 0.5 * dfl);
+        }
+    }
+    return tff < tfl ? tff : tfl;
+}
+
+/* tau_i = min over j in the set (j != i) of orc_tau_pair, for every member
+ * i of the set idx[0..k). */
+static void hold_taus(int64_t k, const int64_t* idx, const double* x, const double* y, const double* z,
+                      const double* vx, const double* vy, const double* vz, const double* m, double G,
+                      double eta, int sym, double* tau) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t a = 0; a < k; ++a) {
+        int64_t i = idx[a];
+        double t = INFINITY;
+        for (int64_t b = 0; b < k; ++b) {
+            int64_t j = idx[b];
+            if (j == i) continue;
+            double tij = orc_tau_pair(x[j] - x[i], y[j] - y[i], z[j] - z[i], vx[j] - vx[i], vy[j] - vy[i],
+                                      vz[j] - vz[i], m[i] + m[j], G, eta, sym);
+            if (tij < t) t = tij;
+        }
+        tau[a] = t;
+    }
+}
+
+/* tau_i over all n bodies (the set of every body). */
+void orc_taus(int64_t n, const double* x, const double* y, const double* z, const double* vx, const double* vy,
+              const double* vz, const double* m, double G, double eta, int sym, double* tau) {
+    int64_t* all = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) all[i] = i;
+    hold_taus(n, all, x, y, z, vx, vy, vz, m, G, eta, sym, tau);
+    free(all);
+}
+
+/* Acceleration of the sinks from the sources (index lists), direct FP64,
+ * softened like orc_direct; a body does not act on itself. */
+static void hold_accel(int64_t ns, const int64_t* sink, int64_t nsrc, const int64_t* src, const double* x,
+                       const double* y, const double* z, const double* m, double G, double soft2, double* ax,
+                       double* ay, double* az) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t a = 0; a < ns; ++a) {
+        int64_t i = sink[a];
+        double sx = 0, sy = 0, sz = 0;
+        for (int64_t b = 0; b < nsrc; ++b) {
+            int64_t j = src[b];
+            if (j == i) continue;
+            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (soft2 > 0.0) r2 = r2 + soft2;
+            double r = sqrt(r2);
+            double mr3 = m[j] / (r2 * r);
+            sx += mr3 * dx; sy += mr3 * dy; sz += mr3 * dz;
+        }
+        ax[a] = G * sx; ay[a] = G * sy; az[a] = G * sz;
+    }
+}
+
+typedef struct {
+    double *x, *y, *z, *vx, *vy, *vz;
+    const double* m;
+    double G, soft2, eta, dt_min;
+    int sym;
+    int64_t n, kicks, force_evals, max_depth;
+} hold_sys;
+
+/* Kick of the slow system H_S = T_S + V_SS + V_FS over time h: slow bodies
+ * feel all of P = S + F, fast bodies feel the slow ones only. */
+static void hold_kick(hold_sys* s, int64_t ns, const int64_t* S, int64_t nf, const int64_t* F, const int64_t* P,
+                      double h) {
+    int64_t np = ns + nf;
+    double* a = (double*)malloc(sizeof(double) * 3 * (size_t)(np > 0 ? np : 1));
+    hold_accel(ns, S, np, P, s->x, s->y, s->z, s->m, s->G, s->soft2, a, a + ns, a + 2 * ns);
+    for (int64_t q = 0; q < ns; ++q) {
+        int64_t i = S[q];
+        s->vx[i] += h * a[q]; s->vy[i] += h * a[ns + q]; s->vz[i] += h * a[2 * ns + q];
+    }
+    if (nf > 0) {
+        hold_accel(nf, F, ns, S, s->x, s->y, s->z, s->m, s->G, s->soft2, a, a + nf, a + 2 * nf);
+        for (int64_t q = 0; q < nf; ++q) {
+            int64_t i = F[q];
+            s->vx[i] += h * a[q]; s->vy[i] += h * a[nf + q]; s->vz[i] += h * a[2 * nf + q];
+        }
+    }
+    s->kicks += 1;
+    s->force_evals += ns * np + nf * ns;
+    free(a);
+}
+
+/* Evolve the subsystem P = idx[0..k) under H_P = T_P + V_PP for time dt
+ * (Appendix A, after Pelupessy et al. 2012): split P into fast bodies
+ * (tau_i < dt, tau over pairs within P) and slow ones; evolve the fast
+ * system for dt/2, kick-drift-kick the slow system (H_S, the slow bodies'
+ * kinetic term, V_SS and V_FS), evolve the fast system for dt/2. Below
+ * dt_min nothing is split further (a plain leapfrog step of P). */
+static void hold_evolve(hold_sys* s, int64_t k, const int64_t* idx, double dt, int64_t depth) {
+    if (k == 0) return;
+    if (depth > s->max_depth) s->max_depth = depth;
+    int64_t* S = (int64_t*)malloc(sizeof(int64_t) * (size_t)k);
+    int64_t* F = (int64_t*)malloc(sizeof(int64_t) * (size_t)k);
+    int64_t* P = (int64_t*)malloc(sizeof(int64_t) * (size_t)k);
+    int64_t ns = 0, nf = 0;
+    if (k > 1 && dt > s->dt_min) {
+        double* tau = (double*)malloc(sizeof(double) * (size_t)k);
+        hold_taus(k, idx, s->x, s->y, s->z, s->vx, s->vy, s->vz, s->m, s->G, s->eta, s->sym, tau);
+        for (int64_t a = 0; a < k; ++a) {
+            if (tau[a] < dt) F[nf++] = idx[a];
+            else S[ns++] = idx[a];
+        }
+        free(tau);
+    } else {
+        for (int64_t a = 0; a < k; ++a) S[ns++] = idx[a];
+    }
+    for (int64_t a = 0; a < ns; ++a) P[a] = S[a];
+    for (int64_t a = 0; a < nf; ++a) P[ns + a] = F[a];
+    if (nf > 0) hold_evolve(s, nf, F, 0.5 * dt, depth + 1);
+    if (ns > 0) {
+        hold_kick(s, ns, S, nf, F, P, 0.5 * dt);
+        for (int64_t a = 0; a < ns; ++a) {
+            int64_t i = S[a];
+            s->x[i] += dt * s->vx[i]; s->y[i] += dt * s->vy[i]; s->z[i] += dt * s->vz[i];
+        }
+        hold_kick(s, ns, S, nf, F, P, 0.5 * dt);
+    }
+    if (nf > 0) hold_evolve(s, nf, F, 0.5 * dt, depth + 1);
+    free(S); free(F); free(P);
+}
+
+/* nsteps HOLD steps of size dt on all n bodies, in place. stats (may be
+ * NULL): {slow-system kicks, pair force evaluations, deepest level}. */
+void orc_hold(int64_t n, double* x, double* y, double* z, double* vx, double* vy, double* vz, const double* m,
+              double G, double soft, double eta, int sym, double dt, int64_t nsteps, double dt_min,
+              int64_t* stats) {
+    hold_sys s = {x, y, z, vx, vy, vz, m, G, soft * soft, eta, dt_min, sym, n, 0, 0, 0};
+    int64_t* all = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) all[i] = i;
+    for (int64_t t = 0; t < nsteps; ++t) hold_evolve(&s, n, all, dt, 0);
+    free(all);
+    if (stats) { stats[0] = s.kicks; stats[1] = s.force_evals; stats[2] = s.max_depth; }
+}
+
+/* Total energy sum m v^2 / 2 - G sum_{i<j} m_i m_j / |x_i - x_j| (softened
+ * like orc_direct). */
+double orc_energy(int64_t n, const double* x, const double* y, const double* z, const double* vx, const double* vy,
+                  const double* vz, const double* m, double G, double soft) {
+    double soft2 = soft * soft, ek = 0.0, ep = 0.0;
+    for (int64_t i = 0; i < n; ++i) ek += 0.5 * m[i] * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]);
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : ep)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t j = i + 1; j < n; ++j) {
+            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (soft2 > 0.0) r2 = r2 + soft2;
+            s += m[j] / sqrt(r2);
+        }
+        ep += m[i] * s;
+    }
+    return ek - G * ep;
+}
+
 /* ------------------------------------------------------------- the solve */
 
 typedef struct {

@@ -669,3 +669,105 @@ def test_jerk_meets_a_tolerance_like_the_acceleration():
     j = run.jerk(vel)
     d = np.linalg.norm(j - jd, axis=1) / np.linalg.norm(jd, axis=1)
     assert np.median(d) < 1e-6 and np.sqrt(np.mean(d * d)) < 1e-4, (np.median(d), np.sqrt(np.mean(d * d)))
+
+
+# ---------------------------------------------------------- HOLD (App. A)
+
+def test_pair_step_sizes_and_their_time_derivatives():
+    """Free-fall time eta sqrt(r^3 / (G m)) and fly-by time eta r / v; the
+    symmetrized step tau / (1 - tau'/2) with tau' checked against central
+    differences of tau along the two-body motion."""
+    G, mij, eta = 1.3, 0.7, 0.05
+    # slow relative motion: the free-fall time is the smaller one
+    r, v = np.array([0.3, -0.1, 0.2]), np.array([0.02, 0.05, -0.01])
+    rn = np.linalg.norm(r)
+    tff = eta * np.sqrt(rn ** 3 / (G * mij))
+    assert np.isclose(oracle.tau_pair(r, v, mij, G, eta), tff, rtol=1e-15)
+    # fast fly-by: the fly-by time is the smaller one
+    vf = np.array([3.0, -2.0, 1.0])
+    assert np.isclose(oracle.tau_pair(r, vf, mij, G, eta), eta * rn / np.linalg.norm(vf), rtol=1e-15)
+    # circular-like motion (r . v = 0, no radial speed) leaves the free-fall time unchanged
+    vc = np.cross(r, [0.0, 0.0, 1.0]) * 0.01
+    assert np.isclose(oracle.tau_pair(r, vc, mij, G, eta, sym=True), oracle.tau_pair(r, vc, mij, G, eta), rtol=1e-15)
+
+    def moved(r, v, h):
+        a = -G * mij * r / np.linalg.norm(r) ** 3
+        return r + h * v + 0.5 * h * h * a, v + h * a
+
+    h = 1e-6
+    for rr, vv in ((r, v), (r, vf)):
+        t = oracle.tau_pair(rr, vv, mij, G, eta)
+        rp, vp = moved(rr, vv, h)
+        rm, vm = moved(rr, vv, -h)
+        dt = (oracle.tau_pair(rp, vp, mij, G, eta) - oracle.tau_pair(rm, vm, mij, G, eta)) / (2 * h)
+        assert np.isclose(oracle.tau_pair(rr, vv, mij, G, eta, sym=True), t / (1 - 0.5 * dt), rtol=1e-7)
+
+
+def _leapfrog(pos, vel, m, dt, steps):
+    pos, vel = pos.copy(), vel.copy()
+    for _ in range(steps):
+        a, _ = oracle.direct(pos, m)
+        vel += 0.5 * dt * a
+        pos += dt * vel
+        a, _ = oracle.direct(pos, m)
+        vel += 0.5 * dt * a
+    return pos, vel
+
+
+def test_hold_is_the_leapfrog_when_no_body_is_fast():
+    pos, vel, m = ics.plummer(64, 51)
+    p, v, st = oracle.hold(pos, vel, m, dt=1 / 128, nsteps=20, eta=1e6, sym=False)
+    lp, lv = _leapfrog(pos, vel, m, 1 / 128, 20)
+    assert st["max_depth"] == 0
+    assert np.abs(p - lp).max() < 1e-14 and np.abs(v - lv).max() < 1e-13
+
+
+def test_hold_conserves_momentum_and_angular_momentum():
+    """Every kick of V_FS acts on both sets with the same step, drifts are
+    straight: both are conserved to round-off across the levels."""
+    pos, vel, m = ics.plummer(80, 52)
+    m = ics.kroupa_masses(80, 53)
+    p, v, st = oracle.hold(pos, vel, m, dt=1 / 32, nsteps=32, eta=0.05, sym=True, dt_min=1e-9)
+    assert st["max_depth"] >= 3
+    P0, P1 = (m[:, None] * vel).sum(0), (m[:, None] * v).sum(0)
+    L0, L1 = (m[:, None] * np.cross(pos, vel)).sum(0), (m[:, None] * np.cross(p, v)).sum(0)
+    scale = (m[:, None] * np.abs(v)).sum()
+    assert np.abs(P1 - P0).max() < 1e-13 * scale
+    assert np.abs(L1 - L0).max() < 1e-12 * (m[:, None] * np.abs(np.cross(p, v))).sum()
+
+
+@pytest.mark.parametrize("sym", [False, True])
+def test_hold_is_second_order(sym):
+    """Appendix A: the splitting is second order. Over a quarter time unit the
+    positions converge to a small-eta reference with errors falling ~4x per
+    halving of eta (the step sizes scale with eta)."""
+    pos, vel, m = ics.plummer(100, 7)
+    ref, _, _ = oracle.hold(pos, vel, m, dt=1 / 64, nsteps=16, eta=0.0025, sym=sym, dt_min=1e-12)
+    err = []
+    for eta in (0.04, 0.02, 0.01):
+        p, _, _ = oracle.hold(pos, vel, m, dt=1 / 64, nsteps=16, eta=eta, sym=sym, dt_min=1e-12)
+        err.append(np.abs(p - ref).max())
+    for a, b in zip(err, err[1:]):
+        assert 3.0 < a / b < 5.5, err
+
+
+def test_symmetrized_steps_reduce_the_energy_drift():
+    """Appendix A: individual time steps break the leapfrog's time symmetry
+    and make the energy drift; the time-symmetrized step removes most of it."""
+    errs = {False: [], True: []}
+    for seed in (7, 8, 9):
+        pos, vel, m = ics.plummer(100, seed)
+        E0 = oracle.energy(pos, vel, m)
+        for sym in (False, True):
+            p, v, _ = oracle.hold(pos, vel, m, dt=1 / 64, nsteps=320, eta=0.05, sym=sym, dt_min=1e-9)
+            errs[sym].append(abs(oracle.energy(p, v, m) / E0 - 1))
+    assert np.mean(errs[True]) < 0.3 * np.mean(errs[False]), errs
+
+
+def test_step_sizes_of_a_set_are_the_minimum_over_pairs():
+    pos, vel, m = ics.plummer(40, 54)
+    t = oracle.taus(pos, vel, m, eta=0.04, sym=True)
+    for i in (0, 17, 39):
+        ref = min(oracle.tau_pair(pos[j] - pos[i], vel[j] - vel[i], m[i] + m[j], 1.0, 0.04, True)
+                  for j in range(40) if j != i)
+        assert t[i] == ref
