@@ -180,6 +180,34 @@ int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const 
                const double* m, int64_t ntargets, const int64_t* targets, double* ax, double* ay,
                double* az, double* pot, void* cuda_stream);
 
+/* Step sizes of the HOLD integrator (Appendix A) for n bodies (device FP64
+ * arrays): tau_i = min over j != i of min(eta sqrt(r^3 / (G (m_i + m_j))),
+ * eta r / v), r and v the pair's separation and relative speed (the
+ * free-fall and fly-by times). symmetrize != 0: each time is divided by
+ * (1 - tau'/2) (Eq. step_symm), tau' its time derivative along the two-body
+ * motion, capped at 1. O(n^2), FP64, reproducible bit for bit. A single body
+ * gets +infinity. Errors: FMM_ERR_ARG for n out of range, eta <= 0 or NULL
+ * pointers. */
+int fmm_timesteps(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z, const double* vx,
+                  const double* vy, const double* vz, const double* m, double eta, int32_t symmetrize, double* tau,
+                  void* cuda_stream);
+
+/* nsteps steps of the HOLD integrator (Appendix A, after Pelupessy et al.
+ * 2012) on n bodies, positions and velocities updated in place (device FP64
+ * arrays; masses m). evolve(P, dt): split the set P into fast bodies (their
+ * fmm_timesteps step size within P below dt) and slow ones; evolve the fast
+ * system for dt/2; kick (dt/2), drift (dt) and kick (dt/2) the slow system
+ * H_S = T_S + V_SS + V_FS (slow bodies feel all of P, fast ones the slow
+ * ones); evolve the fast system for dt/2. Below dt_min (or 60 levels) a set
+ * is not split further. Forces: FP64 direct sum for sets of fewer than
+ * direct_below bodies, else the context's FMM solve; G and the softening
+ * from the context. stats (host, may be NULL): {slow-system kicks, FMM
+ * solves, direct solves, deepest level, splits}. Errors as fmm_solve, and
+ * FMM_ERR_ARG for dt <= 0, eta <= 0, dt_min < 0 or nsteps < 0. */
+int fmm_hold(fmm_ctx* ctx, int64_t n, double* x, double* y, double* z, double* vx, double* vy, double* vz,
+             const double* m, double dt, int64_t nsteps, double eta, int32_t symmetrize, double dt_min,
+             int64_t direct_below, int64_t* stats, void* cuda_stream);
+
 /* Statistics of the last solve. */
 int fmm_get_stats(const fmm_ctx* ctx, fmm_stats* out);
 

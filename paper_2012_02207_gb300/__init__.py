@@ -75,6 +75,9 @@ def lib():
             L.fmm_solve_graph.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), i64] + [dp] * 8 + [vp]
             L.fmm_solve_jerk.argtypes = [vp, i64] + [dp] * 14 + [vp]
             L.fmm_direct.argtypes = [vp, i64, dp, dp, dp, dp, i64, dp, dp, dp, dp, dp, vp]
+            L.fmm_timesteps.argtypes = [vp, i64] + [dp] * 7 + [ctypes.c_double, ctypes.c_int32, dp, vp]
+            L.fmm_hold.argtypes = [vp, i64] + [dp] * 7 + [ctypes.c_double, i64, ctypes.c_double, ctypes.c_int32,
+                                                          ctypes.c_double, i64, ctypes.POINTER(ctypes.c_int64), vp]
             L.fmm_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
             L.fmm_export_tree.argtypes = [vp] + [dp] * 8
             L.fmm_export_geometry.argtypes = [vp] + [dp] * 6
@@ -227,6 +230,30 @@ class FMM:
         self._check(lib().fmm_solve_jerk(self._h, n, *(_ptr(t) for t in (x, y, z, vx, vy, vz, m)),
                                          *(_ptr(o) for o in out), _stream_handle(stream)))
         return out
+
+    def hold(self, x, y, z, vx, vy, vz, m, dt, nsteps, eta=0.025, symmetrize=True, dt_min=1e-9,
+             direct_below=4096, stream=None):
+        """nsteps HOLD steps (fmm_hold) on device FP64 tensors, positions and
+        velocities updated in place; returns the run's counters."""
+        import torch  # noqa: PLC0415
+        n = x.numel()
+        for t in (x, y, z, vx, vy, vz, m):
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("positions, velocities and masses must be contiguous CUDA float64 tensors "
+                                 "of equal length")
+        st = (ctypes.c_int64 * 5)()
+        self._check(lib().fmm_hold(self._h, n, *(_ptr(t) for t in (x, y, z, vx, vy, vz, m)), float(dt), int(nsteps),
+                                   float(eta), int(bool(symmetrize)), float(dt_min), int(direct_below), st,
+                                   _stream_handle(stream)))
+        return dict(zip(("kicks", "fmm_solves", "direct_solves", "max_depth", "splits"), list(st)))
+
+    def timesteps(self, x, y, z, vx, vy, vz, m, eta, symmetrize=True, stream=None):
+        """Per-body HOLD step sizes (see fmm_timesteps) of device FP64 tensors."""
+        import torch  # noqa: PLC0415
+        tau = torch.empty(x.numel(), dtype=torch.float64, device=x.device)
+        self._check(lib().fmm_timesteps(self._h, x.numel(), *(_ptr(t) for t in (x, y, z, vx, vy, vz, m)),
+                                        float(eta), int(bool(symmetrize)), _ptr(tau), _stream_handle(stream)))
+        return tau
 
     def direct(self, x, y, z, m, targets=None, stream=None):
         """FP64 direct sum at device int64 target indices (all bodies if None)."""

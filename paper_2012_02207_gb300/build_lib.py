@@ -20,13 +20,14 @@ LIBDIR = os.path.join(HERE, "_lib")
 GEN = os.path.join(LIBDIR, "gen")
 LIB = os.path.join(LIBDIR, "libgbfmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NO_FMA = {"tree.cu", "walk.cu", "noalloc.cu"}
+NO_FMA = {"tree.cu", "walk.cu", "noalloc.cu", "timestep.cu", "hold.cu"}
 # FP32 kernels flush denormals: the hat scale floor keeps every coefficient
 # that matters far above the denormal range
 FTZ = {"p2p.cu", "m2l.cu"}
 M2L32_ORDERS = [4, 6, 8, 10, 12, 14]  # orders of the FP32 register M2L kernel
 EXTRA_FLAGS = os.environ.get("GBFMM_NVCC_FLAGS", "").split()  # extra nvcc flags for experiments
-SOURCES = ["api.cu", "sort.cu", "tree.cu", "walk.cu", "expansions.cu", "m2l.cu", "translate.cu", "p2p.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "sort.cu", "tree.cu", "walk.cu", "expansions.cu", "m2l.cu", "translate.cu", "p2p.cu", "noalloc.cu",
+           "timestep.cu", "hold.cu"]
 
 
 def nvcc() -> str:

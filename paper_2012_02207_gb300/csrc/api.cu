@@ -93,6 +93,10 @@ struct fmm_ctx {
     // jerks: sorted velocities (FP64, FP32), dipole weights, order p-1 moments,
     // dipole multipoles and locals (FP64 and FP32)
     Buf jv, jv32, jw, jmom, jmult, jmult32, jloc, jloc32;
+    // HOLD integrator: all-body list, compact gathers, accelerations, step
+    // sizes, split flags and scan, the fast count; per-depth slow/fast lists
+    Buf h_all, h_gat, h_acc, h_acc2, h_tau, h_flag, h_scan, h_scr, h_nf;
+    std::vector<Buf> h_S, h_F;
     // walk and lists
     // per list: sorted directed keys, the sort's second buffer (its own, so a
     // buffer never moves to a list of another size), CSR offsets
@@ -675,6 +679,115 @@ int jerk_pass(fmm_ctx* ctx, const double* vx, const double* vy, const double* vz
     return FMM_OK;
 }
 
+// ---------------------------------------------------------------- HOLD
+// The HOLD integrator of Appendix A (after Pelupessy et al. 2012), driven
+// from the host: evolve(P, dt) splits the set P by the step sizes of its
+// pairs into fast bodies (tau < dt) and slow ones, evolves the fast system
+// for dt/2, kicks, drifts and kicks the slow system (H_S = T_S + V_SS +
+// V_FS: slow bodies feel all of P, fast bodies the slow ones), and evolves
+// the fast system for dt/2 again. Sets of fewer than direct_below bodies use
+// the FP64 direct sum (the fast-from-slow force then with the fast masses
+// zeroed), larger ones the FMM solve (fast from slow as the difference of the
+// solves over P and over F).
+constexpr int kHoldMaxDepth = 60;
+struct HoldRun {
+    fmm_ctx* ctx;
+    cudaStream_t st;
+    double *x, *y, *z, *vx, *vy, *vz;
+    const double* m;
+    double eta, dt_min;
+    bool sym;
+    int64_t direct_below;
+    int64_t kicks = 0, fmm_solves = 0, direct_solves = 0, max_depth = 0, splits = 0;
+};
+
+// accelerations of the first ntgt of k compact bodies (columns of g, stride k)
+// from all k, into acc (3 columns of stride k; a 4th column is scratch)
+int hold_force(HoldRun& R, int k, const double* g, int ntgt, double* acc, bool force_direct) {
+    fmm_ctx* ctx = R.ctx;
+    const size_t K = (size_t)k;
+    if (force_direct || k < R.direct_below) {
+        direct_sum_f64(k, g, g + K, g + 2 * K, g + 6 * K, ctx->cfg.G, ctx->cfg.soft, ntgt, nullptr, acc, acc + K,
+                       acc + 2 * K, acc + 3 * K, R.st);
+        CK(cudaGetLastError());
+        R.direct_solves++;
+        return FMM_OK;
+    }
+    R.fmm_solves++;
+    return solve_device(ctx, k, 1, nullptr, g, g + K, g + 2 * K, g + 6 * K, acc, acc + K, acc + 2 * K, acc + 3 * K,
+                        R.st);
+}
+
+int hold_kick_sets(HoldRun& R, const int* S, int ns, const int* F, int nf, double h) {
+    fmm_ctx* ctx = R.ctx;
+    const int k = ns + nf;
+    double* g = as<double>(ctx->h_gat);
+    double* acc = as<double>(ctx->h_acc);
+    double* acc2 = as<double>(ctx->h_acc2);
+    hold_gather(ns, S, R.x, R.y, R.z, R.vx, R.vy, R.vz, R.m, g, k, -1, R.st);
+    hold_gather(nf, F, R.x, R.y, R.z, R.vx, R.vy, R.vz, R.m, g + ns, k, -1, R.st);
+    int rc;
+    if ((rc = hold_force(R, k, g, k, acc, false)) != FMM_OK) return rc;
+    hold_kick(ns, S, acc, nullptr, k, 0, h, R.vx, R.vy, R.vz, R.st);
+    if (nf > 0) {
+        if (k < R.direct_below) {
+            // fast bodies first, their masses zeroed: the force of the slow ones alone
+            hold_gather(nf, F, R.x, R.y, R.z, R.vx, R.vy, R.vz, R.m, g, k, 0, R.st);
+            hold_gather(ns, S, R.x, R.y, R.z, R.vx, R.vy, R.vz, R.m, g + nf, k, -1, R.st);
+            if ((rc = hold_force(R, k, g, nf, acc2, true)) != FMM_OK) return rc;
+            hold_kick(nf, F, acc2, nullptr, k, 0, h, R.vx, R.vy, R.vz, R.st);
+        } else {
+            hold_gather(nf, F, R.x, R.y, R.z, R.vx, R.vy, R.vz, R.m, g, nf, -1, R.st);
+            if ((rc = hold_force(R, nf, g, nf, acc2, false)) != FMM_OK) return rc;
+            hold_kick(nf, F, acc + ns, acc2, k, nf, h, R.vx, R.vy, R.vz, R.st);
+        }
+    }
+    CK(cudaGetLastError());
+    R.kicks++;
+    return FMM_OK;
+}
+
+int hold_evolve(HoldRun& R, const int* P, int k, double dt, int depth) {
+    if (k == 0) return FMM_OK;
+    fmm_ctx* ctx = R.ctx;
+    if (depth > R.max_depth) R.max_depth = depth;
+    const int* S = P;
+    const int* F = nullptr;
+    int ns = k, nf = 0, rc;
+    if (k > 1 && dt > R.dt_min && depth < kHoldMaxDepth) {
+        if ((int)ctx->h_S.size() <= depth) {
+            ctx->h_S.resize(depth + 1);
+            ctx->h_F.resize(depth + 1);
+        }
+        if ((rc = ensure(ctx, ctx->h_S[depth], 4 * (size_t)k)) || (rc = ensure(ctx, ctx->h_F[depth], 4 * (size_t)k)))
+            return rc;
+        double* g = as<double>(ctx->h_gat);
+        hold_gather(k, P, R.x, R.y, R.z, R.vx, R.vy, R.vz, R.m, g, k, -1, R.st);
+        const size_t K = (size_t)k;
+        timesteps_f64(k, g, g + K, g + 2 * K, g + 3 * K, g + 4 * K, g + 5 * K, g + 6 * K, ctx->cfg.G, R.eta, R.sym,
+                      as<double>(ctx->h_tau), R.st);
+        hold_split(k, P, as<double>(ctx->h_tau), dt, as<uint32_t>(ctx->h_flag), as<uint32_t>(ctx->h_scan),
+                   as<int>(ctx->h_S[depth]), as<int>(ctx->h_F[depth]), as<uint32_t>(ctx->h_nf),
+                   as<uint32_t>(ctx->h_scr), R.st);
+        uint32_t hnf = 0;
+        CK(cudaMemcpyAsync(&hnf, ctx->h_nf.ptr, 4, cudaMemcpyDeviceToHost, R.st));
+        CK(cudaStreamSynchronize(R.st));
+        nf = (int)hnf;
+        ns = k - nf;
+        S = as<int>(ctx->h_S[depth]);
+        F = as<int>(ctx->h_F[depth]);
+        R.splits++;
+    }
+    if (nf > 0 && (rc = hold_evolve(R, F, nf, 0.5 * dt, depth + 1)) != FMM_OK) return rc;
+    if (ns > 0) {
+        if ((rc = hold_kick_sets(R, S, ns, F, nf, 0.5 * dt)) != FMM_OK) return rc;
+        hold_drift(ns, S, dt, R.x, R.y, R.z, R.vx, R.vy, R.vz, R.st);
+        if ((rc = hold_kick_sets(R, S, ns, F, nf, 0.5 * dt)) != FMM_OK) return rc;
+    }
+    if (nf > 0 && (rc = hold_evolve(R, F, nf, 0.5 * dt, depth + 1)) != FMM_OK) return rc;
+    return FMM_OK;
+}
+
 int check_cfg(const fmm_config* c, std::string& why) {
     if (!c) { why = "cfg is NULL"; return FMM_ERR_ARG; }
     if (c->p < 1 || c->p > kMaxP) { why = "p must be in [1, 30]"; return FMM_ERR_ARG; }
@@ -804,8 +917,11 @@ void fmm_destroy(fmm_ctx* ctx) {
                   &ctx->item_first, &ctx->slot_first, &ctx->item_leaf, &ctx->leaf_of, &ctx->part_hi,
                   &ctx->part_lo, &ctx->work, &ctx->coff, &ctx->box, &ctx->ck0, &ctx->ck1, &ctx->cv0,
                   &ctx->cv1, &ctx->cid, &ctx->jv, &ctx->jv32, &ctx->jw, &ctx->jmom, &ctx->jmult,
-                  &ctx->jmult32, &ctx->jloc, &ctx->jloc32};
+                  &ctx->jmult32, &ctx->jloc, &ctx->jloc32, &ctx->h_all, &ctx->h_gat, &ctx->h_acc, &ctx->h_acc2,
+                  &ctx->h_tau, &ctx->h_flag, &ctx->h_scan, &ctx->h_scr, &ctx->h_nf};
     for (Buf* b : all) release(*b);
+    for (Buf& b : ctx->h_S) release(b);
+    for (Buf& b : ctx->h_F) release(b);
     drop_plan(ctx->plan);
     if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
     if (ctx->gev[0]) cudaEventDestroy(ctx->gev[0]);
@@ -1029,6 +1145,55 @@ int fmm_solve_batch(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, con
         return fail(ctx, FMM_ERR_ARG, "NULL input or output pointer");
     cudaSetDevice(ctx->device);
     return solve_device(ctx, n, nclusters, offsets, x, y, z, m, ax, ay, az, pot, (cudaStream_t)cuda_stream);
+}
+
+int fmm_hold(fmm_ctx* ctx, int64_t n, double* x, double* y, double* z, double* vx, double* vy, double* vz,
+             const double* m, double dt, int64_t nsteps, double eta, int32_t symmetrize, double dt_min,
+             int64_t direct_below, int64_t* stats, void* cuda_stream) {
+    if (!ctx) return FMM_ERR_ARG;
+    if (n < 0 || n > (int64_t)1 << 30) return fail(ctx, FMM_ERR_ARG, "n must be in [0, 2^30]");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FMM_ERR_ARG, "dt must be finite and > 0");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ctx, FMM_ERR_ARG, "eta must be finite and > 0");
+    if (!(dt_min >= 0.0) || nsteps < 0) return fail(ctx, FMM_ERR_ARG, "dt_min >= 0 and nsteps >= 0 required");
+    if (n > 0 && (!x || !y || !z || !vx || !vy || !vz || !m)) return fail(ctx, FMM_ERR_ARG, "NULL pointer");
+    cudaSetDevice(ctx->device);
+    HoldRun R{ctx, (cudaStream_t)cuda_stream, x, y, z, vx, vy, vz, m, eta, dt_min, symmetrize != 0, direct_below};
+    const size_t N = (size_t)(n > 0 ? n : 1);
+    int rc;
+    if ((rc = ensure(ctx, ctx->h_all, 4 * N)) || (rc = ensure(ctx, ctx->h_gat, 56 * N)) ||
+        (rc = ensure(ctx, ctx->h_acc, 32 * N)) || (rc = ensure(ctx, ctx->h_acc2, 32 * N)) ||
+        (rc = ensure(ctx, ctx->h_tau, 8 * N)) || (rc = ensure(ctx, ctx->h_flag, 4 * N)) ||
+        (rc = ensure(ctx, ctx->h_scan, 4 * N)) || (rc = ensure(ctx, ctx->h_scr, 4 * scan_scratch_words((int64_t)N))) ||
+        (rc = ensure(ctx, ctx->h_nf, 64)))
+        return rc;
+    hold_iota((int)n, as<int>(ctx->h_all), R.st);
+    for (int64_t s = 0; s < nsteps && n > 0; ++s)
+        if ((rc = hold_evolve(R, as<int>(ctx->h_all), (int)n, dt, 0)) != FMM_OK) return rc;
+    CK(cudaStreamSynchronize(R.st));
+    if (stats) {
+        stats[0] = R.kicks;
+        stats[1] = R.fmm_solves;
+        stats[2] = R.direct_solves;
+        stats[3] = R.max_depth;
+        stats[4] = R.splits;
+    }
+    return FMM_OK;
+}
+
+int fmm_timesteps(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z, const double* vx,
+                  const double* vy, const double* vz, const double* m, double eta, int32_t symmetrize, double* tau,
+                  void* cuda_stream) {
+    if (!ctx) return FMM_ERR_ARG;
+    if (n < 0 || n > INT32_MAX) return fail(ctx, FMM_ERR_ARG, "n must be in [0, 2^31)");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ctx, FMM_ERR_ARG, "eta must be finite and > 0");
+    if (n == 0) return FMM_OK;
+    if (!x || !y || !z || !vx || !vy || !vz || !m || !tau) return fail(ctx, FMM_ERR_ARG, "NULL pointer");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    timesteps_f64((int)n, x, y, z, vx, vy, vz, m, ctx->cfg.G, eta, symmetrize != 0, tau, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return FMM_OK;
 }
 
 int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* y, const double* z, const double* m,

@@ -319,6 +319,26 @@ void jerk_inputs(int n, const uint32_t* perm, const double* ms, const double* vx
 void jerk_leaves(const LeafArgs& a, bool fp32, const void* locj, const double* vs, const float4* v32,
                  const int* item_leaf, const uint32_t* item_first, const uint32_t* slot_first, const uint32_t* nitems,
                  unsigned* work, const int* leaf_of, double* jx, double* jy, double* jz, cudaStream_t st);
+// ------------------------------------------------------------- timestep.cu
+// HOLD step sizes: tau_i = min over j != i of the pair step (Appendix A)
+void timesteps_f64(int n, const double* x, const double* y, const double* z, const double* vx, const double* vy,
+                   const double* vz, const double* m, double G, double eta, bool sym, double* tau, cudaStream_t st);
+// ----------------------------------------------------------------- hold.cu
+// set operations of the HOLD integrator (index lists of bodies)
+void hold_iota(int n, int* idx, cudaStream_t st);
+// out[c * stride + a] = field c of body idx[a] (x, y, z, vx, vy, vz, m);
+// masses of a >= zero_from are zeroed (zero_from < 0: none)
+void hold_gather(int k, const int* idx, const double* x, const double* y, const double* z, const double* vx,
+                 const double* vy, const double* vz, const double* m, double* out, int stride, int zero_from,
+                 cudaStream_t st);
+// stable split of idx by tau < dt into S (slow) and F (fast); *nfast (device) <- |F|
+void hold_split(int k, const int* idx, const double* tau, double dt, uint32_t* flag, uint32_t* scan, int* S, int* F,
+                uint32_t* nfast, uint32_t* scratch, cudaStream_t st);
+// v[idx[a]] += h (acc[c * stride + a] - sub[c * sub_stride + a]) (sub may be NULL)
+void hold_kick(int k, const int* idx, const double* acc, const double* sub, int stride, int sub_stride, double h,
+               double* vx, double* vy, double* vz, cudaStream_t st);
+void hold_drift(int k, const int* idx, double dt, double* x, double* y, double* z, const double* vx,
+                const double* vy, const double* vz, cudaStream_t st);
 // soft: Plummer softening length (0: Newtonian)
 void direct_sum_f64(int64_t n, const double* x, const double* y, const double* z, const double* m,
                     double G, double soft, int64_t ntgt, const int64_t* tgt, double* ax, double* ay, double* az,
