@@ -189,6 +189,12 @@ def replica_throughput(ms_local, n, world, dist=None, device=None):
     return n * world / (ms * 1e-3), ms
 
 
+def arm_config(p, eps, world):
+    """The workload both arms report: the 2^20-body Plummer/Kroupa solve."""
+    return {"workload": "plummer_kroupa_n1048576_mixed", "n": 1 << 20, "p": p, "eps": eps, "leaf_size": LEAF,
+            "precision": "mixed", "l2": "flushed (512 MB write) before each step", "parallelism": f"replicas{world}"}
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -204,13 +210,14 @@ def run_reference(args):
         vals.append(v)
         times.append(dt)
     value = SAMPLE_N * len(times) / sum(times)
-    sample = f"oracle FMM (FP64, OpenMP) on a Plummer/Kroupa sample of N={SAMPLE_N}, p={p}, eps={eps}, per step"
+    sample = (f"oracle FMM (FP64, OpenMP) per step on a Plummer sphere of N={SAMPLE_N} drawn like the workload "
+              f"(positions seed 2, Kroupa masses seed 3), p={p}, eps={eps}")
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": f"plummer_kroupa_n{SAMPLE_N}_sample", "p": p, "eps": eps,
-                                         "leaf_size": LEAF},
+        "data": "synthetic", "config": arm_config(p, eps, world),
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -359,9 +366,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "plummer_kroupa_n1048576_mixed", "n": n, "p": p, "eps": args.eps,
-                       "leaf_size": LEAF, "precision": "mixed", "l2": "flushed (512 MB write) before each step",
-                       "parallelism": f"replicas{world}"},
+            "config": arm_config(p, args.eps, world),
             "fp64": {"value": value64, "ms_per_step": ms64, "steps": args.fp64_steps, "rms_err": err64,
                      "median_err": med64, "p": args.p64, "eps": args.eps64,
                      "phases_ms": {k: s64[-1][k] for k in ("ms_tree", "ms_upward", "ms_estimate", "ms_walk",

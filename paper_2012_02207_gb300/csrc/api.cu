@@ -611,7 +611,8 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
 // Jerks on the tree, lists and locals of the solve that just ran (see
 // jerk_leaves): the dipole field chi of the weights m_i v_i goes through an
 // order p - 1 P2M of each component, the dipole moments, M2M, M2L over the
-// same directed list and L2L, in the solve's precision.
+// same directed list and L2L, in the solve's precision (P2M and M2M in
+// double-word FP32 in mixed precision, as for the mass multipoles).
 int jerk_pass(fmm_ctx* ctx, const double* vx, const double* vy, const double* vz, double* jx, double* jy,
               double* jz, cudaStream_t st) {
     const int p = ctx->cfg.p;
@@ -635,10 +636,11 @@ int jerk_pass(fmm_ctx* ctx, const double* vx, const double* vy, const double* vz
     double* mom = as<double>(ctx->jmom);
     CK(cudaEventRecord(ctx->ev[8], st));
     jerk_inputs((int)N, perm, as<double>(ctx->ms), vx, vy, vz, as<double>(ctx->jv), w, as<float4>(ctx->jv32), st);
-    for (int c = 0; c < 3; ++c) p2m_weights(t, p - 1, xs, ys, zs, w + c * N, zc, hs, mom + c * K * nq, ctx->tb, st);
+    for (int c = 0; c < 3; ++c)
+        p2m_weights(t, p - 1, xs, ys, zs, w + c * N, zc, hs, mom + c * K * nq, ctx->tb, mixed, st);
     dipole_moments(t, p, mom, mom + K * nq, mom + 2 * K * nq, hs, as<double>(ctx->jmult), st);
     for (int L = t.nlevels - 2; L >= 0; --L)
-        m2m_level(t, L, p, zc, hs, as<double>(ctx->jmult), as<double>(ctx->contrib), ctx->tb, false, st);
+        m2m_level(t, L, p, zc, hs, as<double>(ctx->jmult), as<double>(ctx->contrib), ctx->tb, mixed, st);
     const uint64_t* mk = as<uint64_t>(ctx->dkeys[2]);
     const uint32_t* mo = as<uint32_t>(ctx->doff[2]);
     if (m2l32) {

@@ -477,9 +477,13 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
 }
 
 void p2m_weights(const TreeView& t, int p, const double* xs, const double* ys, const double* zs, const double* w,
-                 const double* zc, const double* hs, double* mult, const DevTables& tbl, cudaStream_t st) {
+                 const double* zc, const double* hs, double* mult, const DevTables& tbl, bool dword, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
-    if (p <= 16)
+    if (dword && p <= 16)
+        (k_p2m_dw<16, 4><<<152 * 8, 128, 0, st>>>(t, p, xs, ys, zs, w, zc, hs, mult), note_launch());
+    else if (dword)
+        (k_p2m_dw<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, xs, ys, zs, w, zc, hs, mult), note_launch());
+    else if (p <= 16)
         (k_p2m<16, 4><<<152 * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, w, zc, hs, mult), note_launch());
     else
         (k_p2m<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, tb, xs, ys, zs, w, zc, hs, mult), note_launch());

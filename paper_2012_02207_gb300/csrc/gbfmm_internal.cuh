@@ -225,9 +225,10 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
                  const double* ys, const double* zs, const double* ms, const double* zc,
                  const double* r, const double* hs, double* mult, double* Pk, float* Phat, float* r32,
                  double* contrib, const DevTables& tb, bool dword, cudaStream_t st);
-// FP64 hat P2M of the leaves with per-body weights w (in place of masses)
+// hat P2M of the leaves with per-body weights w (in place of masses); dword:
+// double-word FP32 arithmetic (mixed precision) instead of FP64
 void p2m_weights(const TreeView& t, int p, const double* xs, const double* ys, const double* zs, const double* w,
-                 const double* zc, const double* hs, double* mult, const DevTables& tb, cudaStream_t st);
+                 const double* zc, const double* hs, double* mult, const DevTables& tb, bool dword, cudaStream_t st);
 // hat multipoles (order p) of the point dipoles of each leaf from the order
 // p - 1 hat moments X, Y, Z of their x, y, z components (the jerk's chi field)
 void dipole_moments(const TreeView& t, int p, const double* X, const double* Y, const double* Z, const double* hs,
