@@ -1,12 +1,19 @@
 // Leaf evaluation: far field by L2P, near field by P2P (Sec. 2.1), plus the
 // plain FP64 direct sum used to measure force errors (Sec. 3.1.1).
 //
-// One warp per target leaf; lane l owns target body l of each 32-body chunk
-// of the leaf. The leaf's local expansion is evaluated at the body (L2P),
-// then the sources of every leaf in the target's P2P list (sorted by index)
-// are summed directly, all lanes reading the same source at a time. The
-// result times G is written to the caller's order through the sort
-// permutation.
+// P2P runs over work items: a target leaf and at most kLeavesPerItem of the
+// source leaves in its (sorted) P2P list, taken by warps from a counter.
+// A warp stages the item's source bodies in shared memory and takes the
+// target bodies 32 at a time, giving each of the nt targets of a chunk
+// G = 32 / nt lanes that split the sources between them (G = 1, 2, 4 run
+// unrolled). Each item writes one partial per target body. k_leaf_reduce
+// then evaluates the leaf's local expansion at the body (L2P), adds the
+// body's partials in item order, and writes the result times G to the
+// caller's order through the sort permutation. Every sum runs in a fixed
+// order. (Balanced rounds that keep more lanes busy, e.g. 2 x 10 targets with
+// 3 lanes each for a leaf of 20, ran the leaf phase at 11.9 ms against 7.0 ms:
+// the odd lane counts take the generic loop and every round stages the
+// sources again.)
 //
 // Mixed precision: bodies are stored relative to their own leaf centre in
 // FP32; a source leaf A is moved into the target leaf B's frame by the
