@@ -31,10 +31,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_BODIES = 1 << 20
-# fastest tuned configurations (paper_2012_02207_gb300/tuned_eps.json: RMS <= 8e-7 on the
-# tuning sample, 6.6e-7 (mixed) and 3.4e-7 (FP64) over all 2^20 bodies)
+# fastest tuned configurations (paper_2012_02207_gb300/tuned_eps.json): mixed p = 10 with the
+# largest eps whose RMS over all 2^20 bodies is <= 9e-7 (8.3e-7); FP64 p = 12 (3.4e-7 over all bodies)
 P_DEFAULT = 10
-EPS_DEFAULT = 2e-8
+EPS_DEFAULT = 2.8e-8
 P_FP64 = 12
 EPS_FP64 = 2e-8
 LEAF = 64
