@@ -96,3 +96,26 @@ def test_swap_is_an_involution_with_parity_zeros(n):
         for j in range(1, n + 1):
             if (j + m + n) % 2 == 0:
                 assert B[m - 1, j - 1] == 0.0
+
+
+def test_every_context_call_rejects_a_null_context_without_a_gpu():
+    """FMM_ERR_ARG (-1), before any device call, for a NULL context."""
+    L = gb.lib()
+    calls = {
+        "fmm_solve": (None, 10) + (None,) * 8 + (None,),
+        "fmm_solve_host": (None, 10) + (None,) * 8 + (None,),
+        "fmm_solve_batch": (None, 1, None) + (None,) * 8 + (None,),
+        "fmm_solve_graph": (None, 1, None, 10) + (None,) * 8 + (None,),
+        "fmm_solve_jerk": (None, 10) + (None,) * 14 + (None,),
+        "fmm_direct": (None, 10, None, None, None, None, 10, None, None, None, None, None, None),
+        "fmm_timesteps": (None, 10) + (None,) * 7 + (0.03, 1, None, None),
+        "fmm_hold": (None, 10) + (None,) * 7 + (0.01, 1, 0.03, 1, 1e-9, 4096, None, None),
+        "fmm_get_stats": (None, None),
+        "fmm_export_tree": (None,) + (None,) * 8,
+        "fmm_export_geometry": (None,) + (None,) * 6,
+        "fmm_export_pairs": (None, 0, None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == -1, name
+    L.fmm_destroy(None)  # allowed, does nothing
+    assert isinstance(L.fmm_last_error(None), bytes)
