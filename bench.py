@@ -210,6 +210,11 @@ def run_reference(args):
         vals.append(v)
         times.append(dt)
     value = SAMPLE_N * len(times) / sum(times)
+    # the same solve once on a single core, beside the all-core figure
+    import oracle  # noqa: PLC0415
+    oracle.set_num_threads(1)
+    v1, dt1, _ = cpu_sample(p, eps)
+    oracle.set_num_threads(cores)
     sample = (f"oracle FMM (FP64, OpenMP) per step on a Plummer sphere of N={SAMPLE_N} drawn like the workload "
               f"(positions seed 2, Kroupa masses seed 3), p={p}, eps={eps}")
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
@@ -219,7 +224,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": arm_config(p, eps, world),
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "value_1_core": v1, "ms_1_core": 1e3 * dt1},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 

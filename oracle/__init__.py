@@ -92,6 +92,7 @@ def lib():
             L.orc_energy.argtypes = [ctypes.c_int64] + [dp] * 7 + [ctypes.c_double] * 2
             L.orc_energy.restype = ctypes.c_double
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_num_threads.argtypes = [ctypes.c_int]
             L.orc_mac_values.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, dp]
             _lib = L
     return _lib
@@ -107,6 +108,11 @@ def _c(a):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on."""
+    lib().orc_set_num_threads(int(k))
 
 
 # --------------------------------------------------------------- harmonics

@@ -1348,6 +1348,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the oracle's parallel loops (for timing it on one core). */
+void orc_set_num_threads(int k) {
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
 /* The two sides of the MAC for a pair of cells: out = {E_{A->B} M_A/r^2,
  * E_{B->A} M_B/r^2, eps f_B, eps f_A, theta-test passed, softening bound
  * A->B, softening bound B->A} (the bounds are 0 without softening or when

@@ -70,3 +70,5 @@ def test_reference_arm_line():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+    # the same oracle solve on one core, beside the all-core figure
+    assert 0 < line["cpu_baseline"]["value_1_core"] <= line["value"] * 1.5
