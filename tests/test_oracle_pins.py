@@ -771,3 +771,17 @@ def test_step_sizes_of_a_set_are_the_minimum_over_pairs():
         ref = min(oracle.tau_pair(pos[j] - pos[i], vel[j] - vel[i], m[i] + m[j], 1.0, 0.04, True)
                   for j in range(40) if j != i)
         assert t[i] == ref
+
+
+def test_total_energy_two_body_and_against_the_direct_potential():
+    """E = sum m v^2 / 2 - G sum_{i<j} m_i m_j / r_ij: the two-body closed form,
+    and half the direct sum's potential energy sum m_i phi_i for many bodies."""
+    pos = np.array([[0.0, 0.0, 0.0], [0.3, 0.4, 0.0]])
+    vel = np.array([[0.1, 0.0, 0.0], [0.0, -0.2, 0.3]])
+    m = np.array([2.0, 3.0])
+    e = 0.5 * 2.0 * 0.01 + 0.5 * 3.0 * 0.13 - 1.7 * 6.0 / 0.5
+    assert np.isclose(oracle.energy(pos, vel, m, G=1.7), e, rtol=1e-15)
+    pos, vel, m = ics.plummer(500, 95)
+    _, pot = oracle.direct(pos, m, soft=0.01)
+    ref = 0.5 * (m * (vel * vel).sum(1)).sum() + 0.5 * (m * pot).sum()
+    assert np.isclose(oracle.energy(pos, vel, m, soft=0.01), ref, rtol=1e-12)
