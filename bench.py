@@ -40,8 +40,10 @@ EPS_FP64 = 4e-8
 LEAF = 64
 SAMPLE_N = 1 << 16          # bounded CPU sample for the oracle timings
 METRIC = "particles/s per FMM force solve at N=1e6: mixed vs FP64 at RMS err<=1e-6"
-N_SM = 152
-FP32_LANES_PER_SM = 128
+# config 3's orders, each at its tuned eps (paper_2012_02207_gb300/tuned_eps.json, mixed precision)
+CONFIG3_ORDERS = (6, 10, 14)
+# config 4 (the ensemble of 256 clusters): the autotuner's pick over all clusters
+ENSEMBLE_PICK = {"leaf": 128, "p": 12, "eps": 3e-8}
 
 
 def load_peaks():
@@ -52,9 +54,29 @@ def load_peaks():
         return {}
 
 
-def fp32_peak_tflops(sm_mhz):
-    """FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
-    return N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+def tuned_eps(p, precision="mixed"):
+    with open(os.path.join(ROOT, "paper_2012_02207_gb300", "tuned_eps.json")) as fh:
+        return json.load(fh)[precision][str(p)]["eps"]
+
+
+def measured_fma_peaks(gb, local):
+    """FP32 and FP64 FMA throughput of this GPU (fmm_fma_peak: independent FMA
+    chains on every lane, about 200 ms per launch), with the SM clock sampled
+    while they run."""
+    import ctypes  # noqa: PLC0415
+
+    import torch  # noqa: PLC0415
+    L = gb.lib()
+    out = {}
+    with ClockSampler(local) as clk:
+        for name, prec in (("fp32", gb.FMM_PRECISION_MIXED), ("fp64", gb.FMM_PRECISION_FP64)):
+            v = ctypes.c_double()
+            rc = L.fmm_fma_peak(prec, 200.0, ctypes.byref(v), torch.cuda.current_stream().cuda_stream)
+            if rc != 0:
+                raise gb.FmmError(rc, L.fmm_last_error(None).decode())
+            out[name] = v.value
+    out["clocks"] = clk.summary()
+    return out
 
 
 def m2l_flops(p):
@@ -190,9 +212,18 @@ def replica_throughput(ms_local, n, world, dist=None, device=None):
 
 
 def arm_config(p, eps, world):
-    """The workload both arms report: the 2^20-body Plummer/Kroupa solve."""
+    """The GPU arm's workload: the 2^20-body Plummer/Kroupa solve."""
     return {"workload": "plummer_kroupa_n1048576_mixed", "n": 1 << 20, "p": p, "eps": eps, "leaf_size": LEAF,
             "precision": "mixed", "l2": "flushed (512 MB write) before each step", "parallelism": f"replicas{world}"}
+
+
+def reference_config(p, eps, world):
+    """The reference arm's workload as it runs: the oracle (about 23 s per
+    2^20-body solve on 16 cores) times a 65536-body Plummer/Kroupa sphere drawn
+    like the GPU arm's, so that --steps K --warmup W ends within minutes."""
+    return {"workload": f"plummer_kroupa_n{SAMPLE_N}_oracle_sample", "n": SAMPLE_N, "p": p, "eps": eps,
+            "leaf_size": LEAF, "precision": "fp64", "sample_of": "plummer_kroupa_n1048576_mixed",
+            "parallelism": f"replicas{world}"}
 
 
 def run_reference(args):
@@ -222,11 +253,57 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": arm_config(p, eps, world),
+        "data": "synthetic", "config": reference_config(p, eps, world),
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
                          "sample": sample, "value_1_core": v1, "ms_1_core": 1e3 * dt1},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def cpu_table():
+    """Oracle timings on this host at configs 1-3 (all cores, and one core for
+    configs 1 and 3), plus the FP64 direct sum's rate at N = 2^20 from 2048
+    sampled targets (N^2 pair interactions would take about an hour)."""
+    import platform  # noqa: PLC0415
+
+    import ics  # noqa: PLC0415
+    import oracle  # noqa: PLC0415
+    cores = oracle.num_threads()
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        model = next((ln.split(":", 1)[1].strip() for ln in out.splitlines() if ln.startswith("Model name")), "")
+    except OSError:
+        pass
+    rows = []
+
+    def time_fmm(name, pos, m, p, eps, threads):
+        oracle.set_num_threads(threads)
+        t0 = time.perf_counter()
+        oracle.fmm(pos, m, p=p, eps=eps, leaf_size=LEAF)
+        dt = time.perf_counter() - t0
+        rows.append({"row": name, "n": len(m), "p": p, "eps": eps, "threads": threads, "s": dt,
+                     "particles_per_s": len(m) / dt})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+
+    pos1, m1 = ics.config_inputs("plummer4k")
+    time_fmm("config1 oracle FMM", pos1, m1, 8, 1e-7, cores)
+    time_fmm("config1 oracle FMM", pos1, m1, 8, 1e-7, 1)
+    pos2, m2 = ics.config_inputs("plummer1m")
+    time_fmm("config2 oracle FMM (equal masses)", pos2, m2, P_FP64, EPS_FP64, cores)
+    pos3, m3 = ics.config_inputs("kroupa1m")
+    time_fmm("config3 oracle FMM (Kroupa masses)", pos3, m3, P_DEFAULT, EPS_DEFAULT, cores)
+    time_fmm("config3 oracle FMM (Kroupa masses)", pos3, m3, P_DEFAULT, EPS_DEFAULT, 1)
+    oracle.set_num_threads(cores)
+    tg = np.sort(np.random.default_rng(0).choice(len(m3), 2048, replace=False))
+    t0 = time.perf_counter()
+    oracle.direct(pos3, m3, targets=tg)
+    dt = time.perf_counter() - t0
+    pairs_per_s = len(tg) * (len(m3) - 1) / dt
+    rows.append({"row": "FP64 direct sum, N = 2^20", "threads": cores, "sampled_targets": len(tg), "s": dt,
+                 "pair_interactions_per_s": pairs_per_s,
+                 "full_solve_s_extrapolated": len(m3) * (len(m3) - 1) / pairs_per_s})
+    print(json.dumps({"cpu_model": model, "machine": platform.machine(), "cores": cores, "rows": rows}), flush=True)
 
 
 def main():
@@ -241,9 +318,16 @@ def main():
     ap.add_argument("--p64", type=int, default=P_FP64)
     ap.add_argument("--eps64", type=float, default=EPS_FP64)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the config-3 orders, the ensemble and the FMA peaks (profiling runs)")
     ap.add_argument("--err-sample", type=int, default=0,
                     help="bodies in the force-error check (0: all bodies)")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="only time the oracle at configs 1-3 on this host and print one JSON line")
     args = ap.parse_args()
+    if args.cpu_table:
+        cpu_table()
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -315,19 +399,21 @@ def main():
         dax, day, daz, _ = mixed.direct(*cols, mt, targets=sample[sl])
         dref[sl] = torch.stack([dax, day, daz], 1)
 
-    def rms_err(ax, ay, az):
+    def err_stats(ax, ay, az):
         a = torch.stack([ax, ay, az], 1)[sample]
         d = torch.linalg.norm(a - dref, dim=1) / torch.linalg.norm(dref, dim=1)
-        return float(torch.sqrt((d * d).mean()).item()), float(d.median().item())
+        q = torch.quantile(d.float(), torch.tensor([0.99, 0.9999], device=dev)).tolist() if len(d) <= 1 << 24 else [None, None]
+        return {"rms": float(torch.sqrt((d * d).mean()).item()), "median": float(d.median().item()),
+                "p99": q[0], "p9999": q[1], "max": float(d.max().item())}
 
     mixed.solve(*cols, mt, out=outs)
-    err_mixed, med_mixed = rms_err(*outs[:3])
+    e_mixed = err_stats(*outs[:3])
 
     # FP64 mode on the same inputs (slow; a few steps)
     fp64 = gb.FMM(p=args.p64, eps=args.eps64, leaf_size=LEAF, precision="fp64")
     t64, s64 = timed_solves(fp64, args.fp64_steps, 1)
     ms64 = sum(t64) / len(t64)
-    err64, med64 = rms_err(*outs[:3])
+    e64 = err_stats(*outs[:3])
     value64 = n / (ms64 * 1e-3)
 
     # end to end through the host entry point (pinned host buffers)
@@ -349,35 +435,70 @@ def main():
             e2e_times.append(t1 - t0)
     e2e_value = n * world / (sum(e2e_times) / len(e2e_times))
 
-    # roofline of the dominant phase (FP32 ALU bound in mixed mode)
+    extras = {}
+    if not args.no_extras:
+        # config 3 at its three orders, each at its tuned eps: time and error over all bodies
+        c3 = {}
+        for p3 in CONFIG3_ORDERS:
+            eps3 = tuned_eps(p3)
+            f3 = gb.FMM(p=p3, eps=eps3, leaf_size=LEAF, precision="mixed")
+            t3, s3 = timed_solves(f3, 3, 1)
+            c3[str(p3)] = {"eps": eps3, "ms_per_solve": statistics.median(t3),
+                           "particles_per_s": n / (statistics.median(t3) * 1e-3), **err_stats(*outs[:3])}
+            del f3
+        extras["config3_orders"] = c3
+        # config 4: the 256-cluster ensemble as one forest at the autotuner's pick
+        from paper_2012_02207_gb300.ensemble import Ensemble  # noqa: PLC0415
+        import ics  # noqa: PLC0415
+        offsets, epos, emass, _, _ = ics.ensemble(256, 4)
+        ens = Ensemble(offsets, epos, emass, sample=512)
+        fe = gb.FMM(p=ENSEMBLE_PICK["p"], eps=ENSEMBLE_PICK["eps"], leaf_size=ENSEMBLE_PICK["leaf"], precision="mixed")
+        eout, ems = ens.time_batch(fe, steps=5)
+        erms = ens.errors(eout)
+        ge = gb.FMM(p=ENSEMBLE_PICK["p"], eps=ENSEMBLE_PICK["eps"], leaf_size=ENSEMBLE_PICK["leaf"], precision="mixed")
+        _, ems_graph, replayed = ens.time_graph(ge)
+        extras["config4_ensemble"] = {
+            "clusters": 256, "n_bodies": ens.n, **ENSEMBLE_PICK, "forest_ms": ems,
+            "forest_particles_per_s": ens.n / (ems * 1e-3), "graph_replay_ms_host": ems_graph,
+            "graph_replayed": replayed, "kernel_launches": fe.stats()["kernel_launches"],
+            "worst_cluster_rms": float(erms.max()), "median_cluster_rms": float(np.median(erms)),
+            "error_sample": "512 bodies per cluster (all bodies of smaller clusters) against the FP64 direct sum"}
+        del ens, fe, ge, eout
+        torch.cuda.empty_cache()
+
+    # roofline of the dominant phase: the FP32 pipe in mixed precision, against
+    # the FP32 FMA throughput measured on this GPU in this run
     st = stats[-1]
     p = args.p
     phase_ms = {"m2l": statistics.median(s["ms_m2l"] for s in stats),
                 "leaf_p2p_l2p": statistics.median(s["ms_leaf"] for s in stats)}
     flops = {"m2l": 2 * st["n_m2l"] * m2l_flops(p), "leaf_p2p_l2p": P2P_FLOPS * st["p2p_interactions"]}
     dom = max(phase_ms, key=phase_ms.get)
-    sm_for_peak = load_peaks().get("sm_max_mhz", 2070.0)
-    peak = fp32_peak_tflops(sm_for_peak)
+    peaks = measured_fma_peaks(gb, local)
+    peak = peaks["fp32"]
     achieved = flops[dom] / (phase_ms[dom] * 1e-3) / 1e12
+    # P2P by the method's count: mutual pair interactions (Newton's third law, Sec. 2.3)
+    p2p_mutual = P2P_FLOPS * st["p2p_interactions"] / 2 / (phase_ms["leaf_p2p_l2p"] * 1e-3) / 1e12
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, dt, cores = cpu_sample(p, args.eps)
         cpu = {"value": v, "unit": "particles/s", "cores": cores, "kind": "oracle",
-               "sample": f"oracle FMM (FP64, OpenMP) on one Plummer/Kroupa solve of N={SAMPLE_N}, "
-                         f"p={p}, eps={args.eps}: {dt:.2f} s"}
+               "sample": f"oracle FMM (FP64, OpenMP) on one Plummer/Kroupa solve of N={SAMPLE_N} drawn like the "
+                         f"workload (positions seed 2, masses seed 3), p={p}, eps={args.eps}: {dt:.2f} s"}
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": arm_config(p, args.eps, world),
-            "fp64": {"value": value64, "ms_per_step": ms64, "steps": args.fp64_steps, "rms_err": err64,
-                     "median_err": med64, "p": args.p64, "eps": args.eps64,
+            "fp64": {"value": value64, "ms_per_step": ms64, "steps": args.fp64_steps, "rms_err": e64["rms"],
+                     "median_err": e64["median"], "p": args.p64, "eps": args.eps64,
                      "phases_ms": {k: s64[-1][k] for k in ("ms_tree", "ms_upward", "ms_estimate", "ms_walk",
                                                           "ms_m2l", "ms_downward", "ms_leaf", "ms_total")}},
             "speedup_vs_fp64": value / value64,
-            "rms_err": err_mixed, "median_err": med_mixed, "err_bodies": int(len(sample)),
+            "rms_err": e_mixed["rms"], "median_err": e_mixed["median"], "err_stats": e_mixed,
+            "err_bodies": int(len(sample)),
             "phases_ms": {k: statistics.median(s[k] for s in stats) for k in
                           ("ms_tree", "ms_upward", "ms_estimate", "ms_walk", "ms_m2l", "ms_downward", "ms_leaf",
                            "ms_total")},
@@ -385,12 +506,18 @@ def main():
                                           "p2p_interactions", "walk_iters")},
             "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": kernel_traffic(dom),
-                         "peak_note": f"FP32 lanes x 2 x {sm_for_peak:.0f} MHz (sm_max_mhz of measured peaks)"},
+                         "peak_note": "FP32 FMA throughput measured in this run (fmm_fma_peak) at SM clock "
+                                      f"{peaks['clocks'].get('sm_mhz')} MHz"},
+            "roofline_p2p_mutual": {"achieved": p2p_mutual, "peak": peak, "unit": "TFLOP/s",
+                                    "frac": p2p_mutual / peak,
+                                    "note": "leaf phase (P2P + L2P) by the method's count: 20 flops per mutual pair"},
+            "measured_peaks": {"fp32_tflops": peaks["fp32"], "fp64_tflops": peaks["fp64"],
+                               "clocks": peaks["clocks"]},
             "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": 32 * n,
                     "d2h_bytes_per_step": 32 * n},
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
             "clocks": clocks, "wall_s_timed": wall,
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, **extras,
         }), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -48,7 +48,8 @@ typedef enum {
     FMM_ERR_NONFINITE = -4,  /* a position or mass is NaN or infinite, or a mass is <= 0 */
     FMM_ERR_COINCIDENT = -5, /* two bodies share exactly the same position */
     FMM_ERR_CAPACITY = -6,   /* an internal list outgrew its capacity after one regrow */
-    FMM_ERR_TIMEOUT = -7     /* a bounded device-side wait ran out */
+    FMM_ERR_TIMEOUT = -7     /* a bounded device-side wait ran out (reserved: no call of this
+                                version spins on the device, so none returns it) */
 } fmm_status;
 
 typedef enum {
@@ -241,7 +242,9 @@ int fmm_export_swap(int64_t* ncos, int64_t* nsin, double* cos_blocks, double* si
  * callers that cannot call cudaMalloc, e.g. under a device-memory budget owned
  * by another allocator, or in a loop where an allocation's latency or failure
  * is not acceptable).
- * x, y, z: n device FP64 positions. Outputs (device): keys[n] sorted Morton
+ * x, y, z: n device FP64 positions. The inputs, the outputs and the stream
+ * must belong to the current CUDA device: the call takes its scratch and
+ * launches its kernels there. Outputs (device): keys[n] sorted Morton
  * keys, perm[n] the caller index of each sorted body (ties keep input order),
  * box[4] (may be NULL) the cube centre and half-size. These are exactly the
  * keys and permutation fmm_solve builds its octree from.
@@ -256,6 +259,18 @@ int fmm_export_swap(int64_t* ncos, int64_t* nsin, double* cos_blocks, double* si
  * is fmm_last_error(NULL). */
 int fmm_morton_sort_noalloc(int64_t n, const double* x, const double* y, const double* z,
                             uint64_t* keys, int64_t* perm, double* box, void* cuda_stream);
+
+/* Measured FMA throughput of the current device, the denominator of the
+ * arithmetic rooflines of the solve's kernels (M2L and P2P run on the FP32
+ * pipe in mixed precision and on the FP64 pipe in FP64 mode). The paper has
+ * no counterpart: it is a measurement utility. precision: FMM_PRECISION_MIXED
+ * times FP32 FMAs, FMM_PRECISION_FP64 FP64 FMAs; independent FMA chains on
+ * every lane of a full grid, one launch grown to last about target_ms
+ * (0 < target_ms <= 10000), the best of three such launches timed with CUDA
+ * events on cuda_stream. *tflops receives 2 x FMAs / s / 1e12. Allocates and
+ * frees a small device buffer; synchronises the stream. Errors: FMM_ERR_ARG,
+ * FMM_ERR_OOM, FMM_ERR_CUDA (message in fmm_last_error(NULL)). */
+int fmm_fma_peak(int precision, double target_ms, double* tflops, void* cuda_stream);
 
 /* Message of the last error on this context (or of the last failed
  * fmm_create when ctx is NULL). Never NULL. */

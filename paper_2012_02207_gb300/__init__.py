@@ -84,6 +84,7 @@ def lib():
             L.fmm_export_pairs.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), dp]
             L.fmm_export_swap.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), dp, dp]
             L.fmm_morton_sort_noalloc.argtypes = [i64, dp, dp, dp, dp, dp, dp, vp]
+            L.fmm_fma_peak.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp]
             L.fmm_last_error.argtypes = [vp]
             L.fmm_last_error.restype = ctypes.c_char_p
             _lib = L
@@ -319,11 +320,16 @@ def morton_sort_noalloc(x, y, z, stream=None):
     float64[4] = cube centre and half-size)."""
     import torch  # noqa: PLC0415
     n = x.numel()
-    keys = torch.empty(n, dtype=torch.int64, device=x.device)
-    perm = torch.empty(n, dtype=torch.int64, device=x.device)
-    box = torch.empty(4, dtype=torch.float64, device=x.device)
-    rc = lib().fmm_morton_sort_noalloc(n, _ptr(x), _ptr(y), _ptr(z), _ptr(keys), _ptr(perm), _ptr(box),
-                                       _stream_handle(stream))
+    for t in (x, y, z):
+        if (t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n
+                or t.device != x.device):
+            raise ValueError("x, y, z must be contiguous CUDA float64 tensors of equal length on one device")
+    with torch.cuda.device(x.device):  # the library uses the current device's scratch and launches there
+        keys = torch.empty(n, dtype=torch.int64, device=x.device)
+        perm = torch.empty(n, dtype=torch.int64, device=x.device)
+        box = torch.empty(4, dtype=torch.float64, device=x.device)
+        rc = lib().fmm_morton_sort_noalloc(n, _ptr(x), _ptr(y), _ptr(z), _ptr(keys), _ptr(perm), _ptr(box),
+                                           _stream_handle(stream))
     if rc != 0:
         raise FmmError(rc, lib().fmm_last_error(None).decode())
     return keys, perm, box

@@ -27,7 +27,7 @@ FTZ = {"p2p.cu", "m2l.cu"}
 M2L32_ORDERS = [4, 6, 8, 10, 12, 14]  # orders of the FP32 register M2L kernel
 EXTRA_FLAGS = os.environ.get("GBFMM_NVCC_FLAGS", "").split()  # extra nvcc flags for experiments
 SOURCES = ["api.cu", "sort.cu", "tree.cu", "walk.cu", "expansions.cu", "m2l.cu", "translate.cu", "p2p.cu", "noalloc.cu",
-           "timestep.cu", "hold.cu"]
+           "timestep.cu", "hold.cu", "peaks.cu"]
 
 
 def nvcc() -> str:

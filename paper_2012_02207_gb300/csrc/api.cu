@@ -12,7 +12,9 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "gbfmm_internal.cuh"
@@ -21,8 +23,49 @@
 namespace gbfmm {
 namespace {
 thread_local int64_t g_launches = 0;
+constexpr int kMaxDevices = 64;
+std::mutex g_dev_mu;
+int g_sm_count[kMaxDevices] = {};
+std::vector<std::pair<const void*, int>> g_smem_set[kMaxDevices];  // (function, bytes) set per device
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return 0;
+    }
+    return dev;
 }
+}  // namespace
 void note_launch() { ++g_launches; }
+
+int device_sm_count() {
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    if (g_sm_count[dev] == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+            cudaGetLastError();
+            sms = 1;  // a launch then still covers the work (grid-stride loops), only slower
+        }
+        g_sm_count[dev] = sms;
+    }
+    return g_sm_count[dev];
+}
+
+cudaError_t ensure_dyn_smem(const void* func, int bytes) {
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    for (auto& e : g_smem_set[dev])
+        if (e.first == func) {
+            if (e.second >= bytes) return cudaSuccess;
+            const cudaError_t rc = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (rc == cudaSuccess) e.second = bytes;
+            return rc;
+        }
+    const cudaError_t rc = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (rc == cudaSuccess) g_smem_set[dev].emplace_back(func, bytes);
+    return rc;
+}
 bool m2l32_supported(int p);
 void tree_build_count(TreeBuffers& b, int* sorted_in_1, cudaStream_t st);
 void tree_build_emit(TreeBuffers& b, cudaStream_t st);

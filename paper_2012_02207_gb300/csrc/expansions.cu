@@ -462,13 +462,13 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
                  double* contrib, const DevTables& tbl, bool dword, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
     if (dword && p <= 16)
-        (k_p2m_dw<16, 4><<<152 * 8, 128, 0, st>>>(t, p, xs, ys, zs, ms, zc, hs, mult), note_launch());
+        (k_p2m_dw<16, 4><<<device_sm_count() * 8, 128, 0, st>>>(t, p, xs, ys, zs, ms, zc, hs, mult), note_launch());
     else if (dword)
-        (k_p2m_dw<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, xs, ys, zs, ms, zc, hs, mult), note_launch());
+        (k_p2m_dw<kMaxP, 2><<<device_sm_count() * 16, 64, 0, st>>>(t, p, xs, ys, zs, ms, zc, hs, mult), note_launch());
     else if (p <= 16)
-        (k_p2m<16, 4><<<152 * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, hs, mult), note_launch());
+        (k_p2m<16, 4><<<device_sm_count() * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, hs, mult), note_launch());
     else
-        (k_p2m<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, hs, mult), note_launch());
+        (k_p2m<kMaxP, 2><<<device_sm_count() * 16, 64, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, hs, mult), note_launch());
     const int nr = ncoef_real(p);
     (void)nr;
     (void)h_level_start;
@@ -480,13 +480,13 @@ void p2m_weights(const TreeView& t, int p, const double* xs, const double* ys, c
                  const double* zc, const double* hs, double* mult, const DevTables& tbl, bool dword, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
     if (dword && p <= 16)
-        (k_p2m_dw<16, 4><<<152 * 8, 128, 0, st>>>(t, p, xs, ys, zs, w, zc, hs, mult), note_launch());
+        (k_p2m_dw<16, 4><<<device_sm_count() * 8, 128, 0, st>>>(t, p, xs, ys, zs, w, zc, hs, mult), note_launch());
     else if (dword)
-        (k_p2m_dw<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, xs, ys, zs, w, zc, hs, mult), note_launch());
+        (k_p2m_dw<kMaxP, 2><<<device_sm_count() * 16, 64, 0, st>>>(t, p, xs, ys, zs, w, zc, hs, mult), note_launch());
     else if (p <= 16)
-        (k_p2m<16, 4><<<152 * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, w, zc, hs, mult), note_launch());
+        (k_p2m<16, 4><<<device_sm_count() * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, w, zc, hs, mult), note_launch());
     else
-        (k_p2m<kMaxP, 2><<<152 * 16, 64, 0, st>>>(t, p, tb, xs, ys, zs, w, zc, hs, mult), note_launch());
+        (k_p2m<kMaxP, 2><<<device_sm_count() * 16, 64, 0, st>>>(t, p, tb, xs, ys, zs, w, zc, hs, mult), note_launch());
 }
 
 void dipole_moments(const TreeView& t, int p, const double* X, const double* Y, const double* Z, const double* hs,
@@ -534,11 +534,7 @@ void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const
     const TabF64 tb = tab64(tbl);
     const int nc = tri(p + 1, 0), nr = ncoef_real(p);
     const size_t sh = (size_t)(2 * nc + nr + p + 1) * sizeof(double);
-    static bool attr_set = false;
-    if (GBFMM_L2L_DIRECT && !attr_set) {
-        cudaFuncSetAttribute(k_l2l<double, TabF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr_set = true;
-    }
+    if (GBFMM_L2L_DIRECT) ensure_dyn_smem((const void*)k_l2l<double, TabF64>, 100 * 1024);
     (void)h_level_start;
     for (int L = 1; L < t.nlevels; ++L) {
         if (t.lvl_cnt[L] <= 0) continue;

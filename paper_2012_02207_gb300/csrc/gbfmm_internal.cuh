@@ -109,6 +109,18 @@ struct TreeView {
 // reports the count of the last solve.
 void note_launch();
 
+// Streaming multiprocessors of the current device (queried once per device).
+// Persistent and grid-stride kernels size their grids as a multiple of it.
+int device_sm_count();
+
+// Raise func's dynamic shared-memory limit to `bytes` on the current device.
+// cudaFuncSetAttribute acts on the current device only, so this is done once
+// per (device, function) pair, under a lock, and remembered.
+cudaError_t ensure_dyn_smem(const void* func, int bytes);
+
+// Message returned by fmm_last_error(NULL) (entry points without a context).
+void set_global_error(const char* msg);
+
 // ---------------------------------------------------------------- sort.cu
 // Stable LSD radix sort of 64-bit keys (optionally with 32-bit values) on the
 // low `bits` bits. Ping-pongs between buffers; returns 1 if the sorted data

@@ -836,12 +836,12 @@ void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_
     cudaMemsetAsync(work, 0, sizeof(unsigned), st);
     const bool soft = a.soft2 > 0.0;
     if (fp32) {
-        if (soft) (k_p2p_items<float, true><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
-        else (k_p2p_items<float, false><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        if (soft) (k_p2p_items<float, true><<<device_sm_count() * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        else (k_p2p_items<float, false><<<device_sm_count() * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
         (k_leaf_reduce<float><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch());
     } else {
-        if (soft) (k_p2p_items<double, true><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
-        else (k_p2p_items<double, false><<<152 * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        if (soft) (k_p2p_items<double, true><<<device_sm_count() * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        else (k_p2p_items<double, false><<<device_sm_count() * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
         (k_leaf_reduce<double><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch());
     }
 }
@@ -857,12 +857,12 @@ void jerk_leaves(const LeafArgs& a, bool fp32, const void* locj, const double* v
     cudaMemsetAsync(work, 0, sizeof(unsigned), st);
     const bool soft = a.soft2 > 0.0;
     if (fp32) {
-        if (soft) (k_jerk_items<float, true><<<152 * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
-        else (k_jerk_items<float, false><<<152 * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        if (soft) (k_jerk_items<float, true><<<device_sm_count() * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        else (k_jerk_items<float, false><<<device_sm_count() * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
         (k_jerk_reduce<float><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, locj, vs, leaf_of, item_first, slot_first, jx, jy, jz), note_launch());
     } else {
-        if (soft) (k_jerk_items<double, true><<<152 * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
-        else (k_jerk_items<double, false><<<152 * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        if (soft) (k_jerk_items<double, true><<<device_sm_count() * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
+        else (k_jerk_items<double, false><<<device_sm_count() * 16, 128, 0, st>>>(a, vs, v32, item_leaf, item_first, slot_first, nitems, work), note_launch());
         (k_jerk_reduce<double><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, locj, vs, leaf_of, item_first, slot_first, jx, jy, jz), note_launch());
     }
 }

@@ -277,12 +277,7 @@ template <typename K, bool VAL>
 int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int bits, uint32_t* hist,
                     cudaStream_t st, const unsigned long long* dn) {
     if (n <= 1 || bits <= 0) return 0;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_scatter<K, VAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)scatter_smem<K, VAL>());
-        attr = true;
-    }
+    ensure_dyn_smem((const void*)k_scatter<K, VAL>, (int)scatter_smem<K, VAL>());
     const int nblocks = (int)((n + kTile - 1) / kTile);
     int cur = 0;
     for (int shift = 0; shift < bits; shift += 8) {

@@ -303,11 +303,7 @@ template <typename T>
 void launch_m2m(const TreeView& t, int Lc, int p, const double* zc, const double* hs,
                 const double* mult, double* contrib, const RotTables<T>& tb, cudaStream_t st) {
     const size_t sh = (size_t)4 * m2m_warp_values(p) * sizeof(T);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_m2m_rot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr = true;
-    }
+    ensure_dyn_smem((const void*)k_m2m_rot<T>, 100 * 1024);
     const int nblk = (t.lvl_cnt[Lc] + 3) / 4;
     (k_m2m_rot<T><<<nblk, 128, sh, st>>>(t, Lc, p, zc, hs, mult, contrib, tb), note_launch());
 }
@@ -316,11 +312,7 @@ template <typename T>
 void launch_l2l(const TreeView& t, int L, int p, const double* zc, const double* hs, T* loc,
                 const RotTables<T>& tb, cudaStream_t st) {
     const size_t sh = (size_t)4 * m2m_warp_values(p) * sizeof(T);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_l2l_rot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr = true;
-    }
+    ensure_dyn_smem((const void*)k_l2l_rot<T>, 100 * 1024);
     const int nblk = (t.lvl_cnt[L] + 3) / 4;
     (k_l2l_rot<T><<<nblk, 128, sh, st>>>(t, L, p, zc, hs, loc, tb), note_launch());
 }

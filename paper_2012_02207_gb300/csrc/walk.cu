@@ -421,7 +421,7 @@ int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* 
     const int64_t cap_leaf = wb.out_cap[mode == 0 ? 1 : 3];
     unsigned long long* cnt_acc = ds->list_cnt + (mode == 0 ? 0 : 2);
     unsigned long long* cnt_leaf = ds->list_cnt + (mode == 0 ? 1 : 3);
-    const int grid = 152 * 8;
+    const int grid = device_sm_count() * 8;
     if (fixed_iters > 0) {
         // a planned number of steps with no read-back (a captured solve): steps
         // past the end of the walk find an empty frontier and return at once;

@@ -183,12 +183,34 @@ def test_direct_kernel_matches_oracle_direct():
     assert np.allclose(pot.cpu().numpy(), opot, rtol=1e-13, atol=0)
 
 
+# the benchmark's settings: mixed precision p = 10, eps = 2.8e-8; FP64 mode p = 12, eps = 4e-8
+BENCH_MIXED = (10, 2.8e-8)
+BENCH_FP64 = (12, 4e-8)
+
+
+def _all_body_rms(f, cols, acc):
+    """RMS relative error of acc (device, n x 3) over all bodies against the
+    library's FP64 direct sum (pinned to the oracle's direct sum below)."""
+    n = cols[0].numel()
+    err2 = 0.0
+    for c0 in range(0, n, 1 << 17):
+        tg = torch.arange(c0, min(n, c0 + (1 << 17)), device=DEV)
+        dax, day, daz, _ = f.direct(*cols, targets=tg)
+        d = torch.stack([dax, day, daz], 1)
+        e = torch.linalg.norm(acc[tg] - d, dim=1) / torch.linalg.norm(d, dim=1)
+        err2 += float((e * e).sum().item())
+    return (err2 / n) ** 0.5
+
+
 @pytest.mark.slow
-def test_full_size_mixed_solve_tree_lists_and_sampled_forces():
-    """N = 2^20 Kroupa Plummer sphere in the benchmark's configuration: the
-    tree and the lists are bit-exact against the oracle, and forces on a
-    sample of bodies match the FP64 direct sum."""
-    n, p, eps = 1 << 20, 10, 1e-7
+def test_full_size_mixed_solve_at_the_benchmark_setting():
+    """N = 2^20 Kroupa Plummer sphere at the benchmark's own setting: the tree,
+    the estimate and the lists are bit-exact against the oracle; the
+    library's FP64 direct sum (the benchmark's error reference) equals the
+    oracle's direct sum at 2000 sampled bodies to 1e-13; the sampled forces
+    meet the target against the oracle's direct sum."""
+    n = 1 << 20
+    p, eps = BENCH_MIXED
     pos, m = ics.config_inputs("kroupa1m")
     f, acc, pot = solve(pos, m, p=p, eps=eps, precision="mixed")
     run = oracle.OracleRun(pos, m, p=p, eps=eps, stage=oracle.STAGE_LISTS)
@@ -197,9 +219,67 @@ def test_full_size_mixed_solve_tree_lists_and_sampled_forces():
         assert np.array_equal(gt[k], ot[k]), k
     og, gg = run.geometry(), f.export_geometry()
     assert np.array_equal(gg["f"], og["f"]) and np.array_equal(gg["fmin"], og["fmin"])
-    for which in ("m2l", "p2p"):
+    for which in ("far", "near", "m2l", "p2p"):
         assert np.array_equal(sorted_pairs(f.export_pairs(which)), sorted_pairs(run.pairs(which))), which
-    sample = np.random.default_rng(0).choice(n, 2000, replace=False)
+    sample = np.sort(np.random.default_rng(0).choice(n, 2000, replace=False))
     dacc, dpot = oracle.direct(pos, m, targets=sample)
+    cols = to_dev(pos, m)
+    gax, gay, gaz, gpot = f.direct(*cols, targets=torch.tensor(sample, device=DEV))
+    gacc = torch.stack([gax, gay, gaz], 1).cpu().numpy()
+    assert np.all(np.linalg.norm(gacc - dacc, axis=1) <= 1e-13 * np.linalg.norm(dacc, axis=1))
+    assert np.all(np.abs(gpot.cpu().numpy() - dpot) <= 1e-13 * np.abs(dpot))
     s = oracle.error_stats(acc[sample], dacc)
     assert s["rms"] < 1e-6 and s["median"] < 5e-7 and s["p99"] < 3e-6, s
+
+
+@pytest.mark.slow
+def test_full_size_mixed_rms_on_an_independent_draw():
+    """eps = 2.8e-8 was tuned on the benchmark's own draw (positions seed 2,
+    masses seed 3). Another draw of the same model (seeds 12 and 13) must meet
+    the RMS <= 1e-6 target over all 2^20 bodies too."""
+    n = 1 << 20
+    p, eps = BENCH_MIXED
+    pos, _, _ = ics.plummer(n, 12)
+    m = ics.kroupa_masses(n, 13)
+    cols = to_dev(pos, m)
+    f = gb.FMM(p=p, eps=eps, precision="mixed")
+    ax, ay, az, _ = f.solve(*cols)
+    rms = _all_body_rms(f, cols, torch.stack([ax, ay, az], 1))
+    assert rms <= 1e-6, rms
+
+
+@pytest.mark.slow
+def test_full_size_fp64_matches_oracle_fmm_on_every_body():
+    """FP64 mode at the benchmark's FP64 setting (N = 2^20, p = 12,
+    eps = 4e-8) against the oracle FMM, body by body on all bodies:
+    |a_gpu - a_oracle| <= 1e-12 f_i with f_i the scalar force estimate of
+    Sec. 2.3, and potentials to 1e-12."""
+    p, eps = BENCH_FP64
+    pos, m = ics.config_inputs("kroupa1m")
+    _, acc, pot = solve(pos, m, p=p, eps=eps, precision="fp64")
+    run = oracle.OracleRun(pos, m, p=p, eps=eps, stage=oracle.STAGE_FULL)
+    assert run.status == 0
+    oacc, opot = run.forces()
+    fi = np.empty(len(m))
+    fi[run.tree()["perm"]] = run.geometry()["f"]
+    d = np.linalg.norm(acc - oacc, axis=1)
+    assert np.max(d / fi) <= 1e-12, np.max(d / fi)
+    assert np.max(np.abs(pot - opot) / np.abs(opot)) <= 1e-12
+
+
+@pytest.mark.parametrize("n,p,eps", [(20000, 10, 2.8e-8), (20000, 6, 1e-6), (20000, 14, 1e-7)])
+def test_mixed_forces_track_the_oracle_fmm_body_by_body(n, p, eps):
+    """Mixed precision against the oracle FMM on the same lists, body by body.
+    The two differ only by FP32 rounding: P2P terms (relative 2^-24 each, each
+    leaf's sum compensated) and the FP32 M2L/L2L/L2P on hat-scaled
+    coefficients, whose rounding grows with p (the z-translation sums
+    alternating terms). Bound: 3e-6 f_i at p <= 10, 1e-5 f_i at p = 14."""
+    pos, _, _ = ics.plummer(n, 31 + p)
+    m = ics.kroupa_masses(n, 32 + p)
+    _, acc, _ = solve(pos, m, p=p, eps=eps, precision="mixed")
+    run = oracle.OracleRun(pos, m, p=p, eps=eps, stage=oracle.STAGE_FULL)
+    oacc, _ = run.forces()
+    fi = np.empty(n)
+    fi[run.tree()["perm"]] = run.geometry()["f"]
+    dev = np.linalg.norm(acc - oacc, axis=1) / fi
+    assert np.max(dev) <= (3e-6 if p <= 10 else 1e-5), (np.max(dev), np.median(dev))

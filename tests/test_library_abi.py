@@ -119,3 +119,10 @@ def test_every_context_call_rejects_a_null_context_without_a_gpu():
         assert getattr(L, name)(*args) == -1, name
     L.fmm_destroy(None)  # allowed, does nothing
     assert isinstance(L.fmm_last_error(None), bytes)
+
+
+def test_noalloc_wrapper_rejects_host_tensors_before_calling_the_library():
+    torch = pytest.importorskip("torch")
+    x = torch.zeros(8, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        gb.morton_sort_noalloc(x, x, x)

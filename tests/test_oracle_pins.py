@@ -323,6 +323,127 @@ def test_tree_definition(n, leaf):
     assert np.all(leafcount == 1)
 
 
+def _decode_morton(keys, bits):
+    """Per-axis integer coordinates (q_x, q_y, q_z) of `bits`-digit Morton
+    keys, read with the x bit highest in each 3-bit digit."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    q = np.zeros((len(keys), 3), dtype=np.int64)
+    for b in range(bits):
+        digit = ((keys >> np.uint64(3 * (bits - 1 - b))) & np.uint64(7)).astype(np.int64)
+        for d in range(3):
+            q[:, d] = (q[:, d] << 1) | ((digit >> (2 - d)) & 1)
+    return q
+
+
+def _key_cases():
+    g = np.random.default_rng(2024)
+    plummer = ics.plummer(3000, 91)[0]
+    # extents 10 : 1 : 0.1, so a per-axis (non-cubic) box would differ from the cube
+    elongated = g.uniform(0, 1, (2000, 3)) * np.array([10.0, 1.0, 0.1]) + np.array([-3.0, 2.0, 5.0])
+    # nearly all bodies inside one octant of the root cube, two at opposite corners
+    clustered = np.vstack([g.uniform(0.51, 0.52, (1500, 3)), [[0.0, 0.0, 0.0], [1.0, 1.0, 1.0]]])
+    # bodies on the faces and corners of the bounding box (the top edge is clamped)
+    edges = g.uniform(-1, 1, (600, 3))
+    edges[:100, 0] = 1.0
+    edges[100:200, 1] = -1.0
+    edges[200:300, 2] = 1.0
+    edges[300] = [1.0, 1.0, 1.0]
+    edges[301] = [-1.0, -1.0, -1.0]
+    planar = np.column_stack([g.uniform(-2, 2, 800), g.uniform(-1, 1, 800), np.full(800, 0.25)])
+    return {"plummer": plummer, "elongated": elongated, "clustered": clustered, "edges": edges,
+            "planar": planar}
+
+
+@pytest.mark.parametrize("case", ["plummer", "elongated", "clustered", "edges", "planar"])
+def test_keys_place_every_body_inside_its_cell(case):
+    """Reading R1 of the tree of Sec. 2.1 as geometry, not as a formula: the
+    root cube has centre (min+max)/2 and half-size max_axis (max-min)/2; a
+    body's 21-level key, read x bit first, names the cell of side 2h/2^21
+    that contains it (the top face belongs to the last cell); the level-L
+    prefix of every node names the cube of side 2h/2^L holding all of its
+    bodies. Round instead of floor, a swapped axis order, a per-axis box or
+    a missing clamp each put some body outside its cell."""
+    pos = _key_cases()[case]
+    n = len(pos)
+    run = oracle.OracleRun(pos, np.full(n, 1.0 / n), leaf_size=16, stage=oracle.STAGE_TREE)
+    assert run.status == 0
+    t = run.tree()
+    mn, mx = pos.min(0), pos.max(0)
+    c, h = 0.5 * (mn + mx), float((0.5 * (mx - mn)).max())
+    assert np.array_equal(t["box"][:3], c) and t["box"][3] == h
+    lo = c - h
+    ps = pos[t["perm"]]
+    q = _decode_morton(t["keys"], 21)
+    w = 2 * h / 2 ** 21
+    tol = 1e-6 * w
+    rel = ps - lo
+    assert np.all(q >= 0) and np.all(q < 2 ** 21)
+    assert np.all(rel >= q * w - tol)
+    top = q == 2 ** 21 - 1
+    assert np.all((rel < (q + 1) * w + tol) | top)
+    assert np.all(rel[top] <= 2 * h + tol)
+    # bodies on the top face of the cube are clamped into the last cell
+    on_top = np.abs(ps - (c + h)) == 0
+    assert np.all(q[on_top] == 2 ** 21 - 1)
+    for k in range(run.nnodes):
+        L = int(t["level"][k])
+        b, e = t["begin"][k], t["end"][k]
+        Q = _decode_morton(t["keys"][b:b + 1] >> np.uint64(3 * (21 - L)), L)[0] if L else np.zeros(3, int)
+        side = 2 * h / 2 ** L
+        r = rel[b:e]
+        assert np.all(r >= Q * side - tol) and np.all(r <= (Q + 1) * side + tol)
+
+
+def _multipole_closed_form(p, pos, m, center):
+    """M_n^m = sum_i m_i Upsilon_n^m(x_i - z) with Upsilon from scipy's
+    associated Legendre functions (Sec. 2.2, Dehnen's normalisation; scipy
+    includes the Condon-Shortley phase, hence the (-1)^m)."""
+    d = pos - center
+    r = np.linalg.norm(d, axis=1)
+    ct = np.where(r > 0, d[:, 2] / np.where(r > 0, r, 1), 1.0)
+    ph = np.arctan2(d[:, 1], d[:, 0])
+    M = np.zeros(oracle.NCOEF(p), complex)
+    for n in range(p + 1):
+        for mm in range(n + 1):
+            ups = r ** n * (-1) ** mm * lpmv(mm, n, ct) * np.exp(1j * mm * ph) / math.factorial(n + mm)
+            M[idx(n, mm)] = (m * ups).sum()
+    return M
+
+
+def test_solve_multipoles_and_degree_norms_follow_their_definitions():
+    """The multipoles a solve keeps for every node (P2M at the leaves, M2M
+    above) equal the moments sum_i m_i Upsilon_n^m(x_i - z_A) of the node's
+    bodies, and the exported degree norms are Sec. 2.3's
+    P_n^2 = sum_{m=-n..n} (n-m)!(n+m)! |M_n^m|^2 of those moments. A dropped
+    factor 2 on the m >= 1 terms, a wrong factorial or a missing degree
+    fails this."""
+    p = 8
+    pos, _, _ = ics.plummer(1500, 17)
+    m = ics.kroupa_masses(1500, 18)
+    run = oracle.OracleRun(pos, m, p=p, leaf_size=32, stage=oracle.STAGE_F)
+    t, g, mult = run.tree(), run.geometry(), run.multipoles()
+    ps, ms = pos[t["perm"]], m[t["perm"]]
+    leaves = np.flatnonzero(t["nchild"] == 0)
+    inner = np.flatnonzero(t["nchild"] > 0)
+    nodes = np.concatenate([[0], inner[:: max(1, len(inner) // 6)], leaves[:: max(1, len(leaves) // 8)]])
+    for k in nodes:
+        sl = slice(t["begin"][k], t["end"][k])
+        ref = _multipole_closed_form(p, ps[sl], ms[sl], g["z"][k])
+        scale = ms[sl].sum() * max(g["r"][k], 1e-300) ** np.array([n for n in range(p + 1) for _ in range(n + 1)])
+        assert np.all(np.abs(mult[k] - ref) <= 1e-11 * scale + 1e-300), k
+        Pn = np.array([math.sqrt(sum(math.factorial(n - mm) * math.factorial(n + mm) * abs(full(ref, n, mm)) ** 2
+                                     for mm in range(-n, n + 1))) for n in range(p + 1)])
+        assert np.allclose(g["P"][k], Pn, rtol=1e-10, atol=1e-12 * ms[sl].sum() * g["r"][k] ** np.arange(p + 1))
+        # P_0 is the mass; P_1 vanishes about the centre of mass (reading R3)
+        assert math.isclose(g["P"][k][0], ms[sl].sum(), rel_tol=1e-13)
+        assert g["P"][k][1] <= 1e-12 * ms[sl].sum() * max(g["r"][k], 1e-300)
+    # every node: the exported norms are those of the exported moments
+    for k in range(run.nnodes):
+        Pn = [math.sqrt(sum(math.factorial(n - mm) * math.factorial(n + mm) * abs(full(mult[k], n, mm)) ** 2
+                            for mm in range(-n, n + 1))) for n in range(p + 1)]
+        assert np.allclose(g["P"][k], Pn, rtol=1e-12, atol=0), k
+
+
 @pytest.mark.parametrize("n,eps,p", [(1200, 1e-4, 4), (1500, 1e-7, 8), (900, 1e30, 3)])
 def test_lists_cover_every_particle_pair_exactly_once(n, eps, p):
     """Every ordered pair (i, j), i != j, is handled exactly once: by one M2L
