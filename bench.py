@@ -82,21 +82,27 @@ def measured_fma_peaks(gb, local):
 def m2l_flops(p):
     """Algorithmic flops of one directed rotation-accelerated M2L at order p:
     four z-rotations (complex products on every m >= 1 coefficient), four
-    swaps (one FMA per non-zero of the cosine and sine blocks), the
-    z-translation (one FMA per (n, k, m) term and real/imag part) and the
-    accumulation of the (p+1)^2 result."""
+    swaps (one FMA per non-zero of the cosine and sine blocks; the swap right
+    after the z-translation only over its non-zero inputs, F'_n^m with
+    m <= p - n), the z-translation (one FMA per (n, k, m) term and real/imag
+    part) and the accumulation of the (p+1)^2 result."""
     rot = sum(6 + 6 * (p - m + 1) for m in range(1, p + 1))
-    swap = 0
-    for n in range(1, p + 1):
-        swap += sum(1 for m in range(n + 1) for j in range(n + 1) if (j + m + n) % 2 == 0)
-        swap += sum(1 for m in range(1, n + 1) for j in range(1, n + 1) if (j + m + n) % 2 == 1)
+
+    def swap_terms(after_z):
+        cnt = 0
+        for n in range(1, p + 1):
+            jmax = min(n, p - n) if after_z else n
+            cnt += sum(1 for m in range(n + 1) for j in range(jmax + 1) if (j + m + n) % 2 == 0)
+            cnt += sum(1 for m in range(1, n + 1) for j in range(1, jmax + 1) if (j + m + n) % 2 == 1)
+        return cnt
+    swap4 = 3 * swap_terms(False) + swap_terms(True)
     trans = 0
     for m in range(p + 1):
         parts = 2 if m else 1
         trans += parts * (p - m + 1)                     # signs and powers of u
         for n in range(m, p + 1):
             trans += parts * 2 * max(0, p - n - m + 1) + parts  # FMAs + final scale
-    return 4 * rot + 4 * 2 * swap + 2 * trans + (p + 1) ** 2
+    return 4 * rot + 2 * swap4 + 2 * trans + (p + 1) ** 2
 
 
 P2P_FLOPS = 20  # per directed body-body interaction (the usual gravity-kernel count)
@@ -447,6 +453,14 @@ def main():
                            "particles_per_s": n / (statistics.median(t3) * 1e-3), **err_stats(*outs[:3])}
             del f3
         extras["config3_orders"] = c3
+        # config 3 as written: FP64 coefficients (M2L, L2L, L2P in FP64) with the FP32 P2P, same p and eps
+        f64l = gb.FMM(p=args.p, eps=args.eps, leaf_size=LEAF, precision="mixed", fp64_locals=True)
+        tl, sl = timed_solves(f64l, 2, 1)
+        extras["config3_fp64_locals"] = {
+            "p": args.p, "eps": args.eps, "ms_per_solve": statistics.median(tl),
+            "particles_per_s": n / (statistics.median(tl) * 1e-3), **err_stats(*outs[:3]),
+            "phases_ms": {k: sl[-1][k] for k in ("ms_m2l", "ms_downward", "ms_leaf", "ms_total")}}
+        del f64l
         # config 4: the 256-cluster ensemble as one forest at the autotuner's pick
         from paper_2012_02207_gb300.ensemble import Ensemble  # noqa: PLC0415
         import ics  # noqa: PLC0415

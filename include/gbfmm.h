@@ -59,13 +59,18 @@ typedef enum {
                                 multipoles for the MAC and the walk in FP64 */
 } fmm_precision;
 
+/* fmm_config.flags bits */
+#define FMM_FLAG_FP64_LOCALS 1u /* mixed precision only: M2L, L2L and L2P run in FP64 on FP64
+                                   multipole and local coefficients, P2P stays FP32 (the split
+                                   "FP64 coefficients for the high orders"); slower, see DESIGN */
+
 typedef struct {
     int p;                 /* expansion order, 1..30 (swap matrices are tabulated to 30, Sec. 2.4) */
     double eps;            /* MAC tolerance epsilon of Sec. 2.3, >= 0 (0: never accept, all P2P) */
     int leaf_size;         /* split a cell while it holds more than leaf_size bodies, 1..256 */
     int precision;         /* fmm_precision */
     double G;              /* gravitational constant (Henon units: 1) */
-    unsigned flags;        /* reserved, 0 */
+    unsigned flags;        /* FMM_FLAG_* bits (0: none); unknown bits are rejected */
     unsigned fault_inject; /* test hook, 0 in production: bit 0 forces tiny list capacities
                               so the capacity-regrow path runs */
     double soft;           /* Plummer softening length eps_soft >= 0 (Appendix B; 0: Newtonian).

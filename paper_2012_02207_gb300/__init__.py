@@ -21,6 +21,7 @@ _lib = None
 
 FMM_PRECISION_FP64 = 0
 FMM_PRECISION_MIXED = 1
+FMM_FLAG_FP64_LOCALS = 1
 
 STATUS = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_CUDA", -3: "FMM_ERR_OOM", -4: "FMM_ERR_NONFINITE",
           -5: "FMM_ERR_COINCIDENT", -6: "FMM_ERR_CAPACITY", -7: "FMM_ERR_TIMEOUT"}
@@ -115,16 +116,21 @@ class Config:
     G: float = 1.0
     fault_inject: int = 0
     soft: float = 0.0
+    flags: int = 0
 
 
 class FMM:
     """One solver context (fmm_create/fmm_destroy) on the current CUDA device."""
 
-    def __init__(self, p=8, eps=1e-7, leaf_size=64, precision="mixed", G=1.0, fault_inject=0, soft=0.0):
+    def __init__(self, p=8, eps=1e-7, leaf_size=64, precision="mixed", G=1.0, fault_inject=0, soft=0.0,
+                 fp64_locals=False):
+        """fp64_locals: in mixed precision, run M2L, L2L and L2P in FP64 on FP64
+        coefficients (FMM_FLAG_FP64_LOCALS); P2P stays FP32."""
         if isinstance(precision, str):
             precision = {"fp64": FMM_PRECISION_FP64, "mixed": FMM_PRECISION_MIXED}[precision]
-        self.config = Config(p, eps, leaf_size, precision, G, fault_inject, soft)
-        cfg = _Config(p, eps, leaf_size, precision, G, 0, fault_inject, soft)
+        flags = FMM_FLAG_FP64_LOCALS if fp64_locals else 0
+        self.config = Config(p, eps, leaf_size, precision, G, fault_inject, soft, flags)
+        cfg = _Config(p, eps, leaf_size, precision, G, flags, fault_inject, soft)
         h = ctypes.c_void_p()
         rc = lib().fmm_create(ctypes.byref(h), ctypes.byref(cfg))
         if rc != 0:

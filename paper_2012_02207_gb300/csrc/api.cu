@@ -143,7 +143,7 @@ struct fmm_ctx {
     // walk and lists
     // per list: sorted directed keys, the sort's second buffer (its own, so a
     // buffer never moves to a list of another size), CSR offsets
-    Buf front0, front1, lists[4], dkeys[4], dalt[4], doff[4], dcount;
+    Buf front0, front1, lists[4], dkeys[4], dalt[4], dsrc[4], doff[4], dcount, geo;
     int64_t front_cap = 0, list_cap[4] = {0, 0, 0, 0};
     // host staging for fmm_solve_host
     Buf hin[4], hout[4];
@@ -287,6 +287,7 @@ int build_directed(fmm_ctx* ctx, int which, cudaStream_t st) {
     if ((rc = ensure(ctx, ctx->dkeys[which], keys_bytes)) != FMM_OK) return rc;
     if ((rc = ensure(ctx, ctx->dalt[which], keys_bytes)) != FMM_OK) return rc;
     if ((rc = ensure(ctx, ctx->doff[which], sizeof(uint32_t) * (size_t)(ctx->nnodes + 2))) != FMM_OK) return rc;
+    if ((rc = ensure(ctx, ctx->dsrc[which], sizeof(uint32_t) * (size_t)(2 * np + 1))) != FMM_OK) return rc;
     if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(2 * np + 1))) != FMM_OK) return rc;
     ctx->ndirected[which] = 2 * np;
     unsigned long long* nkeys = as<unsigned long long>(ctx->dcount) + 8 + which;
@@ -297,17 +298,16 @@ int build_directed(fmm_ctx* ctx, int which, cudaStream_t st) {
         pairs_to_directed32(as<int2>(ctx->lists[which]), ctx->ds->list_cnt + which, np, ctx->nb, ka,
                             as<unsigned long long>(ctx->dcount) + 2 + which, nkeys, st);
         const int in1 = radix_sort32(ka, kb, 2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st, nkeys);
-        directed_offsets_widen(in1 ? kb : ka, 2 * np, nkeys, ctx->nb, &ctx->ds->nnodes,
-                               as<uint64_t>(ctx->dkeys[which]), as<uint32_t>(ctx->doff[which]), st);
+        directed_offsets_src32(in1 ? kb : ka, 2 * np, nkeys, ctx->nb, &ctx->ds->nnodes,
+                               as<uint32_t>(ctx->dsrc[which]), as<uint32_t>(ctx->doff[which]), st);
         return FMM_OK;
     }
     pairs_to_directed(as<int2>(ctx->lists[which]), ctx->ds->list_cnt + which, np, ctx->nb,
                       as<uint64_t>(ctx->dkeys[which]), as<unsigned long long>(ctx->dcount) + 2 + which, nkeys, st);
     const int in1 = radix_sort(as<uint64_t>(ctx->dkeys[which]), nullptr, as<uint64_t>(ctx->dalt[which]), nullptr,
                                2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st, nkeys);
-    if (in1) std::swap(ctx->dkeys[which], ctx->dalt[which]);
-    directed_offsets(as<uint64_t>(ctx->dkeys[which]), 2 * np, nkeys, ctx->nb, &ctx->ds->nnodes,
-                     as<uint32_t>(ctx->doff[which]), st);
+    directed_offsets(as<uint64_t>(in1 ? ctx->dalt[which] : ctx->dkeys[which]), 2 * np, nkeys, ctx->nb,
+                     &ctx->ds->nnodes, as<uint32_t>(ctx->dsrc[which]), as<uint32_t>(ctx->doff[which]), st);
     return FMM_OK;
 }
 
@@ -407,6 +407,8 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
                  double* pot, cudaStream_t st) {
     const int p = ctx->cfg.p;
     const bool mixed = ctx->cfg.precision == FMM_PRECISION_MIXED;
+    // FP32 far field (M2L, L2L, L2P on hat FP32 coefficients) unless the flag asks for FP64 locals
+    const bool far32 = mixed && !(ctx->cfg.flags & FMM_FLAG_FP64_LOCALS);
     const GraphPlan* gp = ctx->gmode;  // non-null: the graph form (planned sizes, no read-back)
     // phase events; while capturing they become event-record nodes (the external
     // flag is only accepted then), so a replay times its phases too
@@ -490,11 +492,11 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
         (rc = ensure(ctx, ctx->fmin, 4 * K)) || (rc = ensure(ctx, ctx->fscratch, 4 * (2 * K + N))) ||
         (rc = ensure(ctx, ctx->zhi, 16 * K)) || (rc = ensure(ctx, ctx->zlo, 16 * K)) ||
         (rc = ensure(ctx, ctx->contrib, 8 * K * nr)) || (rc = ensure(ctx, ctx->Phat, 4 * K * (p + 1))) ||
-        (rc = ensure(ctx, ctx->r32, 4 * K)) ||
+        (rc = ensure(ctx, ctx->r32, 4 * K)) || (rc = ensure(ctx, ctx->geo, sizeof(double) * kShiftGeo * K)) ||
         (rc = ensure(ctx, ctx->item_first, 4 * (K + 2))) || (rc = ensure(ctx, ctx->slot_first, 4 * (K + 2))) ||
         (rc = ensure(ctx, ctx->leaf_of, 4 * N)) || (rc = ensure(ctx, ctx->work, 64)))
         return rc;
-    if (mixed) {
+    if (far32) {
         if ((rc = ensure(ctx, ctx->mult32, 4 * K * ((nr + 3) & ~(size_t)3))) || (rc = ensure(ctx, ctx->loc32, 4 * K * nr)))
             return rc;
         if (!m2l32_supported(p) && (rc = ensure(ctx, ctx->loc, 8 * K * nr))) return rc;
@@ -525,12 +527,13 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
                   ctx->h_level_start, as<double>(ctx->M), as<double>(ctx->S), as<double>(ctx->zc),
                   as<double>(ctx->r), st);
     hat_scales(t, as<int>(ctx->parent), as<double>(ctx->r), as<double>(ctx->hs), st);
+    shift_geometry(t, as<double>(ctx->zc), as<double>(ctx->hs), as<double>(ctx->geo), st);
     node_centres_f32(t, as<double>(ctx->zc), as<double>(ctx->hs), as<float4>(ctx->zhi), as<float4>(ctx->zlo), st);
     CK(rec(1));
     // ---- upward pass
     upward_pass(t, ctx->h_level_start, p, as<double>(ctx->xs), as<double>(ctx->ys), as<double>(ctx->zs),
                 as<double>(ctx->ms), as<double>(ctx->zc), as<double>(ctx->r), as<double>(ctx->hs),
-                as<double>(ctx->mult), as<double>(ctx->Pk), as<float>(ctx->Phat), as<float>(ctx->r32), as<double>(ctx->contrib), ctx->tb,
+                as<double>(ctx->geo), as<double>(ctx->mult), as<double>(ctx->Pk), as<float>(ctx->Phat), as<float>(ctx->r32), as<double>(ctx->contrib), ctx->tb,
                 mixed, st);
     CK(rec(2));
     // ---- scalar-force estimate
@@ -548,8 +551,8 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     CK(cudaMemsetAsync(ctx->dcount.ptr, 0, 128, st));
     if ((rc = run_walk(ctx, 0, st))) return rc;
     if ((rc = build_directed(ctx, 0, st)) || (rc = build_directed(ctx, 1, st))) return rc;
-    scalar_force(t, as<double>(ctx->zc), as<double>(ctx->M), as<float4>(ctx->xf), as<uint64_t>(ctx->dkeys[0]),
-                 as<uint32_t>(ctx->doff[0]), as<uint64_t>(ctx->dkeys[1]), as<uint32_t>(ctx->doff[1]), ctx->nb,
+    scalar_force(t, as<double>(ctx->zc), as<double>(ctx->M), as<float4>(ctx->xf), as<uint32_t>(ctx->dsrc[0]),
+                 as<uint32_t>(ctx->doff[0]), as<uint32_t>(ctx->dsrc[1]), as<uint32_t>(ctx->doff[1]),
                  ctx->h_level_start, ctx->cfg.soft, as<float>(ctx->fscratch), as<float>(ctx->f),
                  as<float>(ctx->fmin), st);
     CK(rec(3));
@@ -558,24 +561,26 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     if ((rc = build_directed(ctx, 2, st)) || (rc = build_directed(ctx, 3, st))) return rc;
     CK(rec(4));
     // ---- far field
-    const uint64_t* mk = as<uint64_t>(ctx->dkeys[2]);
+    const uint32_t* mk = as<uint32_t>(ctx->dsrc[2]);
     const uint32_t* mo = as<uint32_t>(ctx->doff[2]);
-    if (mixed && m2l32_supported(p)) {
+    if (far32 && m2l32_supported(p)) {
         multipoles_to_f32_padded(as<double>(ctx->mult), as<float>(ctx->mult32), t, (int)nr,
                                  (int)((nr + 3) & ~(size_t)3), st);
-        m2l_f32(t.dnn, p, mk, mo, ctx->nb, as<float>(ctx->mult32), as<float4>(ctx->zhi), as<float4>(ctx->zlo),
+        m2l_f32(t.dnn, p, mk, mo, as<float>(ctx->mult32), as<float4>(ctx->zhi), as<float4>(ctx->zlo),
                 as<float>(ctx->loc32), &ctx->ds->queue, st);
     } else {
-        m2l_f64(t.dnn, p, mk, mo, ctx->nb, as<double>(ctx->mult), as<double>(ctx->zc), as<double>(ctx->hs),
+        m2l_f64(t.dnn, p, mk, mo, as<double>(ctx->mult), as<double>(ctx->zc), as<double>(ctx->hs),
                 as<double>(ctx->loc), ctx->tb, &ctx->ds->queue, st);
-        if (mixed) multipoles_to_f32(as<double>(ctx->loc), as<float>(ctx->loc32), t, (int)nr, st);
+        if (far32) multipoles_to_f32(as<double>(ctx->loc), as<float>(ctx->loc32), t, (int)nr, st);
     }
     CK(rec(5));
-    if (mixed)
-        downward_pass_f32(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->hs), as<float>(ctx->loc32),
+    if (far32)
+        downward_pass_f32(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->hs), as<double>(ctx->geo),
+                          as<float>(ctx->loc32),
                           ctx->tb, st);
     else
-        downward_pass_f64(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->hs), as<double>(ctx->loc),
+        downward_pass_f64(t, ctx->h_level_start, p, as<double>(ctx->zc), as<double>(ctx->hs), as<double>(ctx->geo),
+                          as<double>(ctx->loc),
                           ctx->tb, st);
     CK(rec(6));
     // ---- leaves: P2P work items, then L2P + partials per body
@@ -606,7 +611,7 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     la.xs = as<double>(ctx->xs); la.ys = as<double>(ctx->ys); la.zs = as<double>(ctx->zs); la.ms = as<double>(ctx->ms);
     la.zc = as<double>(ctx->zc); la.hs = as<double>(ctx->hs);
     la.zhi = as<float4>(ctx->zhi); la.zlo = as<float4>(ctx->zlo);
-    la.p2p_keys = as<uint64_t>(ctx->dkeys[3]); la.p2p_off = as<uint32_t>(ctx->doff[3]); la.nb = ctx->nb;
+    la.p2p_src = as<uint32_t>(ctx->dsrc[3]); la.p2p_off = as<uint32_t>(ctx->doff[3]);
     la.perm = as<uint32_t>(in1 ? ctx->v1 : ctx->v0);
     la.ax = ax; la.ay = ay; la.az = az; la.pot = pot;
     la.part_hi = as<double2>(ctx->part_hi); la.part_lo = as<double2>(ctx->part_lo);
@@ -616,11 +621,9 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     if (mixed) {
         leaf_relative_f32(t, la.xs, la.ys, la.zs, la.ms, la.zc, as<float4>(ctx->prel), st);
         la.prel = as<float4>(ctx->prel);
-        la.loc = ctx->loc32.ptr;
-    } else {
-        la.loc = ctx->loc.ptr;
     }
-    leaf_eval(la, mixed, as<int>(ctx->item_leaf), item_first, slot_first, totals,
+    la.loc = far32 ? ctx->loc32.ptr : ctx->loc.ptr;
+    leaf_eval(la, mixed, far32, as<int>(ctx->item_leaf), item_first, slot_first, totals,
               as<unsigned>(ctx->work), as<int>(ctx->leaf_of), st);
     CK(rec(7));
     CK(cudaGetLastError());
@@ -663,6 +666,8 @@ int jerk_pass(fmm_ctx* ctx, const double* vx, const double* vy, const double* vz
     const bool m2l32 = mixed && m2l32_supported(p);
     const size_t N = (size_t)ctx->n, K = (size_t)ctx->nnodes;
     const size_t nr = ncoef_real(p), nq = ncoef_real(p - 1), pad = (nr + 3) & ~(size_t)3;
+    if (ctx->cfg.flags & FMM_FLAG_FP64_LOCALS)
+        return fail(ctx, FMM_ERR_ARG, "jerks are not available with FMM_FLAG_FP64_LOCALS");
     int rc;
     if ((rc = ensure(ctx, ctx->jv, 24 * N)) || (rc = ensure(ctx, ctx->jw, 24 * N)) ||
         (rc = ensure(ctx, ctx->jv32, 16 * N)) || (rc = ensure(ctx, ctx->jmom, 24 * K * nq)) ||
@@ -683,20 +688,20 @@ int jerk_pass(fmm_ctx* ctx, const double* vx, const double* vy, const double* vz
         p2m_weights(t, p - 1, xs, ys, zs, w + c * N, zc, hs, mom + c * K * nq, ctx->tb, mixed, st);
     dipole_moments(t, p, mom, mom + K * nq, mom + 2 * K * nq, hs, as<double>(ctx->jmult), st);
     for (int L = t.nlevels - 2; L >= 0; --L)
-        m2m_level(t, L, p, zc, hs, as<double>(ctx->jmult), as<double>(ctx->contrib), ctx->tb, mixed, st);
-    const uint64_t* mk = as<uint64_t>(ctx->dkeys[2]);
+        m2m_level(t, L, p, as<double>(ctx->geo), as<double>(ctx->jmult), as<double>(ctx->contrib), ctx->tb, mixed, st);
+    const uint32_t* mk = as<uint32_t>(ctx->dsrc[2]);
     const uint32_t* mo = as<uint32_t>(ctx->doff[2]);
     if (m2l32) {
         multipoles_to_f32_padded(as<double>(ctx->jmult), as<float>(ctx->jmult32), t, (int)nr, (int)pad, st);
-        m2l_f32(t.dnn, p, mk, mo, ctx->nb, as<float>(ctx->jmult32), as<float4>(ctx->zhi), as<float4>(ctx->zlo),
+        m2l_f32(t.dnn, p, mk, mo, as<float>(ctx->jmult32), as<float4>(ctx->zhi), as<float4>(ctx->zlo),
                 as<float>(ctx->jloc32), &ctx->ds->queue, st);
     } else {
-        m2l_f64(t.dnn, p, mk, mo, ctx->nb, as<double>(ctx->jmult), zc, hs, as<double>(ctx->jloc), ctx->tb,
+        m2l_f64(t.dnn, p, mk, mo, as<double>(ctx->jmult), zc, hs, as<double>(ctx->jloc), ctx->tb,
                 &ctx->ds->queue, st);
         if (mixed) multipoles_to_f32(as<double>(ctx->jloc), as<float>(ctx->jloc32), t, (int)nr, st);
     }
-    if (mixed) downward_pass_f32(t, ctx->h_level_start, p, zc, hs, as<float>(ctx->jloc32), ctx->tb, st);
-    else downward_pass_f64(t, ctx->h_level_start, p, zc, hs, as<double>(ctx->jloc), ctx->tb, st);
+    if (mixed) downward_pass_f32(t, ctx->h_level_start, p, zc, hs, as<double>(ctx->geo), as<float>(ctx->jloc32), ctx->tb, st);
+    else downward_pass_f64(t, ctx->h_level_start, p, zc, hs, as<double>(ctx->geo), as<double>(ctx->jloc), ctx->tb, st);
     LeafArgs la{};
     la.t = t; la.p = p; la.G = ctx->cfg.G;
     la.soft2 = ctx->cfg.soft * ctx->cfg.soft;
@@ -704,7 +709,7 @@ int jerk_pass(fmm_ctx* ctx, const double* vx, const double* vy, const double* vz
     la.xs = xs; la.ys = ys; la.zs = zs; la.ms = as<double>(ctx->ms);
     la.zc = zc; la.hs = hs;
     la.zhi = as<float4>(ctx->zhi); la.zlo = as<float4>(ctx->zlo);
-    la.p2p_keys = as<uint64_t>(ctx->dkeys[3]); la.p2p_off = as<uint32_t>(ctx->doff[3]); la.nb = ctx->nb;
+    la.p2p_src = as<uint32_t>(ctx->dsrc[3]); la.p2p_off = as<uint32_t>(ctx->doff[3]);
     la.perm = perm;
     la.tb = ctx->tb;
     la.prel = as<float4>(ctx->prel);
@@ -842,6 +847,11 @@ int check_cfg(const fmm_config* c, std::string& why) {
     if (c->precision == FMM_PRECISION_MIXED && c->p > kMaxPF32) { why = "mixed precision supports p <= 16"; return FMM_ERR_ARG; }
     if (!std::isfinite(c->G)) { why = "G must be finite"; return FMM_ERR_ARG; }
     if (!(c->soft >= 0.0) || !std::isfinite(c->soft)) { why = "soft must be finite and >= 0"; return FMM_ERR_ARG; }
+    if (c->flags & ~FMM_FLAG_FP64_LOCALS) { why = "unknown flag bits"; return FMM_ERR_ARG; }
+    if ((c->flags & FMM_FLAG_FP64_LOCALS) && c->precision != FMM_PRECISION_MIXED) {
+        why = "FMM_FLAG_FP64_LOCALS applies to mixed precision only";
+        return FMM_ERR_ARG;
+    }
     return FMM_OK;
 }
 
@@ -963,7 +973,7 @@ void fmm_destroy(fmm_ctx* ctx) {
                   &ctx->part_lo, &ctx->work, &ctx->coff, &ctx->box, &ctx->ck0, &ctx->ck1, &ctx->cv0,
                   &ctx->cv1, &ctx->cid, &ctx->jv, &ctx->jv32, &ctx->jw, &ctx->jmom, &ctx->jmult,
                   &ctx->jmult32, &ctx->jloc, &ctx->jloc32, &ctx->h_all, &ctx->h_gat, &ctx->h_acc, &ctx->h_acc2,
-                  &ctx->h_tau, &ctx->h_flag, &ctx->h_scan, &ctx->h_scr, &ctx->h_nf};
+                  &ctx->h_tau, &ctx->h_flag, &ctx->h_scan, &ctx->h_scr, &ctx->h_nf, &ctx->geo};
     for (Buf* b : all) release(*b);
     for (Buf& b : ctx->h_S) release(b);
     for (Buf& b : ctx->h_F) release(b);
@@ -975,6 +985,7 @@ void fmm_destroy(fmm_ctx* ctx) {
         release(ctx->lists[l]);
         release(ctx->dkeys[l]);
         release(ctx->dalt[l]);
+        release(ctx->dsrc[l]);
         release(ctx->doff[l]);
         release(ctx->hin[l]);
         release(ctx->hout[l]);

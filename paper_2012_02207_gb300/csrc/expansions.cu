@@ -458,8 +458,8 @@ void upload_expansion_tables(const HostTables& h) {
 
 void upward_pass(const TreeView& t, const int* h_level_start, int p, const double* xs,
                  const double* ys, const double* zs, const double* ms, const double* zc,
-                 const double* r, const double* hs, double* mult, double* Pk, float* Phat, float* r32,
-                 double* contrib, const DevTables& tbl, bool dword, cudaStream_t st) {
+                 const double* r, const double* hs, const double* geo, double* mult, double* Pk, float* Phat,
+                 float* r32, double* contrib, const DevTables& tbl, bool dword, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
     if (dword && p <= 16)
         (k_p2m_dw<16, 4><<<device_sm_count() * 8, 128, 0, st>>>(t, p, xs, ys, zs, ms, zc, hs, mult), note_launch());
@@ -472,7 +472,7 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
     const int nr = ncoef_real(p);
     (void)nr;
     (void)h_level_start;
-    for (int L = t.nlevels - 2; L >= 0; --L) m2m_level(t, L, p, zc, hs, mult, contrib, tbl, dword, st);
+    for (int L = t.nlevels - 2; L >= 0; --L) m2m_level(t, L, p, geo, mult, contrib, tbl, dword, st);
     (k_pnorm<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.dnn, p, mult, r, hs, Pk, Phat, r32), note_launch());
 }
 
@@ -530,7 +530,7 @@ void multipoles_to_f32(const double* mult, float* mult32, const TreeView& t, int
 #endif
 
 void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const double* zc,
-                       const double* hs, double* loc, const DevTables& tbl, cudaStream_t st) {
+                       const double* hs, const double* geo, double* loc, const DevTables& tbl, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
     const int nc = tri(p + 1, 0), nr = ncoef_real(p);
     const size_t sh = (size_t)(2 * nc + nr + p + 1) * sizeof(double);
@@ -539,19 +539,19 @@ void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const
     for (int L = 1; L < t.nlevels; ++L) {
         if (t.lvl_cnt[L] <= 0) continue;
         if (GBFMM_L2L_DIRECT) (k_l2l<double, TabF64><<<t.lvl_cnt[L], 64, sh, st>>>(t, L, p, tb, zc, hs, loc), note_launch());
-        else l2l_level(t, L, p, zc, hs, loc, tbl, false, st);
+        else l2l_level(t, L, p, geo, loc, tbl, false, st);
     }
 }
 
 void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const double* zc,
-                       const double* hs, float* loc, const DevTables& tbl, cudaStream_t st) {
+                       const double* hs, const double* geo, float* loc, const DevTables& tbl, cudaStream_t st) {
     const int nc = tri(p + 1, 0), nr = ncoef_real(p);
     const size_t sh = (size_t)(2 * nc + nr + p + 1) * sizeof(float);
     (void)h_level_start;
     for (int L = 1; L < t.nlevels; ++L) {
         if (t.lvl_cnt[L] <= 0) continue;
         if (GBFMM_L2L_DIRECT) (k_l2l<float, TabF32><<<t.lvl_cnt[L], 64, sh, st>>>(t, L, p, TabF32{}, zc, hs, loc), note_launch());
-        else l2l_level(t, L, p, zc, hs, loc, tbl, true, st);
+        else l2l_level(t, L, p, geo, loc, tbl, true, st);
     }
 }
 

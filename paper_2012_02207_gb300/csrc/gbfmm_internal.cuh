@@ -202,26 +202,27 @@ int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* 
 // (else kErrCapacity)
 void walk_check_finished(DevScalars* ds, int nit, cudaStream_t st);
 // Scalar-force estimate f (Sec. 2.3) from the theta-walk lists given as
-// per-target CSR (sorted directed keys target<<nb | source).
+// per-target CSR (source cell of every entry, sources ascending per target).
 void scalar_force(const TreeView& t, const double* zc, const double* M, const float4* xf,
-                  const uint64_t* far_keys, const uint32_t* far_off, const uint64_t* near_keys,
-                  const uint32_t* near_off, int nb, const int* h_level_start, double soft, float* farf,
+                  const uint32_t* far_src, const uint32_t* far_off, const uint32_t* near_src,
+                  const uint32_t* near_off, const int* h_level_start, double soft, float* farf,
                   float* f, float* fmin, cudaStream_t st);
 // directed entries of a pair list: (B<-A) and (A<-B), a self pair once and a
 // marker that sorts last; np: the device count of pairs, npcap >= *np the
 // pairs the grid covers; *nkeys (device) <- 2 min(*np, npcap), the keys written.
 void pairs_to_directed(const int2* pairs, const unsigned long long* np, int64_t npcap, int nb, uint64_t* keys,
                        unsigned long long* count, unsigned long long* nkeys, cudaStream_t st);
-// 32-bit keys (when 2 nb <= 32); the sorted keys are widened to 64 bits by
-// directed_offsets_widen, which also writes the CSR offsets.
+// 32-bit keys (when 2 nb <= 32); directed_offsets_src32 turns the sorted keys
+// into source indices and CSR offsets.
 void pairs_to_directed32(const int2* pairs, const unsigned long long* np, int64_t npcap, int nb, uint32_t* keys,
                          unsigned long long* count, unsigned long long* nkeys, cudaStream_t st);
-// dnk (device): the keys present, of the nkeys the grid covers
-void directed_offsets_widen(const uint32_t* k32, int64_t nkeys, const unsigned long long* dnk, int nb,
-                            const int* dnn, uint64_t* keys, uint32_t* off, cudaStream_t st);
-// CSR offsets (nnodes + 1, nnodes = *dnn) of sorted directed keys.
+// Sorted directed keys -> src (the source cell of every entry; 0xffffffff for
+// the markers past the end) and the CSR offsets per target (nnodes + 1,
+// nnodes = *dnn). dnk (device): the keys present, of the nkeys the grid covers.
+void directed_offsets_src32(const uint32_t* k32, int64_t nkeys, const unsigned long long* dnk, int nb,
+                            const int* dnn, uint32_t* src, uint32_t* off, cudaStream_t st);
 void directed_offsets(const uint64_t* keys, int64_t nkeys, const unsigned long long* dnk, int nb, const int* dnn,
-                      uint32_t* off, cudaStream_t st);
+                      uint32_t* src, uint32_t* off, cudaStream_t st);
 
 // ---------------------------------------------------------- expansions.cu
 void upload_expansion_tables(const HostTables& h);
@@ -235,8 +236,8 @@ void hat_scales(const TreeView& t, const int* parent, const double* r, double* h
 // r: node sizes (the walk's FP32 copy r32 is written from them); hs: hat scales.
 void upward_pass(const TreeView& t, const int* h_level_start, int p, const double* xs,
                  const double* ys, const double* zs, const double* ms, const double* zc,
-                 const double* r, const double* hs, double* mult, double* Pk, float* Phat, float* r32,
-                 double* contrib, const DevTables& tb, bool dword, cudaStream_t st);
+                 const double* r, const double* hs, const double* geo, double* mult, double* Pk, float* Phat,
+                 float* r32, double* contrib, const DevTables& tb, bool dword, cudaStream_t st);
 // hat P2M of the leaves with per-body weights w (in place of masses); dword:
 // double-word FP32 arithmetic (mixed precision) instead of FP64
 void p2m_weights(const TreeView& t, int p, const double* xs, const double* ys, const double* zs, const double* w,
@@ -245,15 +246,20 @@ void p2m_weights(const TreeView& t, int p, const double* xs, const double* ys, c
 // p - 1 hat moments X, Y, Z of their x, y, z components (the jerk's chi field)
 void dipole_moments(const TreeView& t, int p, const double* X, const double* Y, const double* Z, const double* hs,
                     double* mult, cudaStream_t st);
+// The geometry of every node's shift to its parent, kShiftGeo doubles per
+// node: cos phi, sin phi, cos theta, sin theta of b = z_C - z_P, |b| / s_P and
+// s_C / s_P (FP64, one thread per node); read by the M2M and L2L kernels.
+constexpr int kShiftGeo = 6;
+void shift_geometry(const TreeView& t, const double* zc, const double* hs, double* geo, cudaStream_t st);
 // rotation-accelerated M2M of one level: the children (level L + 1) into their
 // parents (level L); contrib: (p+1)^2 doubles per node (scratch); dword:
 // double-word FP32 arithmetic instead of FP64
-void m2m_level(const TreeView& t, int L, int p, const double* zc, const double* hs, double* mult,
-               double* contrib, const DevTables& tb, bool dword, cudaStream_t st);
+void m2m_level(const TreeView& t, int L, int p, const double* geo, double* mult, double* contrib,
+               const DevTables& tb, bool dword, cudaStream_t st);
 // rotation-accelerated L2L of one level: the locals of the nodes of level L
 // gain their parents' shifted locals; loc: FP32 (fp32) or FP64 (p+1)^2 per node
-void l2l_level(const TreeView& t, int L, int p, const double* zc, const double* hs, void* loc,
-               const DevTables& tb, bool fp32, cudaStream_t st);
+void l2l_level(const TreeView& t, int L, int p, const double* geo, void* loc, const DevTables& tb, bool fp32,
+               cudaStream_t st);
 void multipoles_to_f32(const double* mult, float* mult32, const TreeView& t, int nr, cudaStream_t st);
 // FP32 copy with each node's vector padded to `stride` floats (zeros after nr)
 void multipoles_to_f32_padded(const double* mult, float* mult32, const TreeView& t, int nr, int stride,
@@ -265,18 +271,18 @@ void node_centres_f32(const TreeView& t, const double* zc, const double* hs, flo
 
 // L2L level by level (FP64 or FP32 locals).
 void downward_pass_f64(const TreeView& t, const int* h_level_start, int p, const double* zc,
-                       const double* hs, double* loc, const DevTables& tb, cudaStream_t st);
+                       const double* hs, const double* geo, double* loc, const DevTables& tb, cudaStream_t st);
 void downward_pass_f32(const TreeView& t, const int* h_level_start, int p, const double* zc,
-                       const double* hs, float* loc, const DevTables& tb, cudaStream_t st);
+                       const double* hs, const double* geo, float* loc, const DevTables& tb, cudaStream_t st);
 
 // ----------------------------------------------------------------- m2l.cu
 // Rotation-accelerated M2L (Sec. 2.4), gathered per target over the sorted
 // directed list; writes the locals of every node (zero without sources).
 // queue: a device counter, zeroed here; warps take target cells (below *dnn) from it.
-void m2l_f64(const int* dnn, int p, const uint64_t* keys, const uint32_t* off, int nb,
+void m2l_f64(const int* dnn, int p, const uint32_t* src, const uint32_t* off,
              const double* mult, const double* zc, const double* hs, double* loc,
              const DevTables& tb, unsigned* queue, cudaStream_t st);
-void m2l_f32(const int* dnn, int p, const uint64_t* keys, const uint32_t* off, int nb,
+void m2l_f32(const int* dnn, int p, const uint32_t* src, const uint32_t* off,
              const float* mult, const float4* zhi, const float4* zlo, float* loc, unsigned* queue,
              cudaStream_t st);
 bool m2l32_supported(int p);
@@ -295,9 +301,8 @@ struct LeafArgs {
     const double *xs, *ys, *zs, *ms;
     const double *zc, *hs;  // node centres and hat scales
     const float4 *zhi, *zlo;  // double-float node centres; zhi.w = hat scale
-    const uint64_t* p2p_keys;
+    const uint32_t* p2p_src;  // source leaf of every directed P2P entry, ascending per target
     const uint32_t* p2p_off;
-    int nb;
     const uint32_t* perm;
     double *ax, *ay, *az, *pot;
     const void* loc;   // FP64 or FP32 locals
@@ -315,8 +320,9 @@ void leaf_items_plan(const TreeView& t, const uint32_t* p2p_off, uint32_t* item_
 void leaf_items_check(uint32_t* totals, uint32_t items_cap, uint32_t slots_cap, unsigned* err, cudaStream_t st);
 void leaf_items_fill(const TreeView& t, const uint32_t* item_first, int* item_leaf, uint32_t items_cap,
                      int* leaf_of, cudaStream_t st);
-// nitems: device count of work items
-void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_t* item_first,
+// nitems: device count of work items; p2p32: FP32 P2P on leaf-relative
+// bodies (else FP64); l2p32: FP32 L2P on FP32 hat locals (else FP64)
+void leaf_eval(const LeafArgs& a, bool p2p32, bool l2p32, const int* item_leaf, const uint32_t* item_first,
                const uint32_t* slot_first, const uint32_t* nitems, unsigned* work, const int* leaf_of,
                cudaStream_t st);
 void leaf_relative_f32(const TreeView& t, const double* xs, const double* ys, const double* zs,

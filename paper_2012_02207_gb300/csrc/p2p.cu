@@ -54,12 +54,15 @@ struct TabL32 {
 //   phi = -sum_{n,m} conj(Shat_n^m(dhat)) Fhat_n^m
 //   F_1^m(x) = (1/s) sum_{k,l} conj(Shat_k^l) w_{1+k}^{m+l}/w_k^l Fhat_{1+k}^{m+l}, m = 0, 1
 //   a = (Re F_1^1, Im F_1^1, F_1^0)        (all without G)
-template <typename T, typename Tab>
-__device__ void l2p_hat(int p, const T* __restrict__ F, T x, T y, T z, T inv_s, const Tab& tb,
-                        T& phi, T& ax, T& ay, T& az) {
+// PC > 0: the order is the compile-time PC (loops unrolled); PC = 0: p.
+template <typename T, typename Tab, int PC = 0>
+__device__ __forceinline__ void l2p_hat(int p_rt, const T* __restrict__ F, T x, T y, T z, T inv_s, const Tab& tb,
+                                        T& phi, T& ax, T& ay, T& az) {
+    const int p = PC > 0 ? PC : p_rt;
     const T r2 = x * x + y * y + z * z;
     T pot = T(0), g0 = T(0), g1r = T(0), g1i = T(0);
     T dre = T(1), dim = T(0);  // Shat_l^l
+#pragma unroll
     for (int l = 0; l <= p; ++l) {
         if (l > 0) {
             const T t = dre * x - dim * y;
@@ -69,6 +72,7 @@ __device__ void l2p_hat(int p, const T* __restrict__ F, T x, T y, T z, T inv_s, 
             dim *= tb.D(l);
         }
         T s1r = dre, s1i = dim, s2r = T(0), s2i = T(0);  // Shat_k^l, Shat_{k-1}^l
+#pragma unroll
         for (int k = l; k <= p; ++k) {
             T sr, si;
             if (k == l) { sr = dre; si = dim; }
@@ -128,8 +132,10 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float b) {
     lo += err;
 }
 
+// a body (position, mass) as one 16-byte (FP32) or 32-byte (FP64) aligned record,
+// so that shared-memory reads and writes take one vector access
 template <typename T>
-struct Body4 { T x, y, z, w; };
+struct alignas(4 * sizeof(T)) Body4 { T x, y, z, w; };
 
 constexpr int kStageCap = 256;  // bodies staged per pack (source leaves packed back to back)
 
@@ -167,6 +173,313 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
     return y;
 }
 
+// ---------------------------------------------------------------------------
+// P2P force over work items, sources across lanes and targets in registers.
+//
+// A warp stages the item's source bodies (moved into the target leaf B's
+// frame) in shared memory, up to TileCfg::kCap at a time. The targets of B
+// are taken in groups of TG (8 in FP32, 4 in FP64; a last group of TG/2 when
+// at most TG/2 remain). For a group, lane l runs over the staged sources
+// l, l + 32, l + 64, ... and keeps TG four-component partial sums (ax, ay,
+// az, sum m/r) in registers: one shared-memory load serves TG interactions
+// and every lane is busy whatever the leaf sizes. The 32 lanes' partials of
+// the group are then summed by a transpose reduction across the warp (a
+// fixed tree: lane l ends with component l % 4 of target l / 4), and added
+// in FP64 to the group's totals in shared memory. So the order of every sum
+// is fixed and the result does not depend on scheduling.
+//
+// FP32 terms are summed per lane over at most kCap / 32 = 16 sources of a
+// staged pack, the cross-lane tree adds five levels, and each pack's total is
+// accumulated in FP64.
+//
+// SOFT: Plummer softening (Appendix B), 1/r -> 1/sqrt(r^2 + s2); the body
+// itself (r2 = 0; coincident bodies are rejected) still contributes nothing.
+
+template <typename T>
+struct TileCfg;
+template <>
+struct TileCfg<float> {
+    static constexpr int TG = 8;      // targets per group
+    static constexpr int kCap = 512;  // staged source bodies per warp (8 KB): at most 16 per lane
+    static constexpr int kRun = 1 << 30;  // so a lane's run is at most 16 terms: no fold
+};
+template <>
+struct TileCfg<double> {
+    static constexpr int TG = 4;
+    static constexpr int kCap = 256;          // 8 KB per warp
+    static constexpr int kRun = 1 << 30;      // FP64: no fold
+};
+constexpr int kTargetChunk = 64;  // targets whose totals a warp keeps in shared memory per pass
+
+// per warp: staged sources, the target chunk's positions, its FP64 totals
+template <typename T>
+constexpr size_t p2p_tile_smem_per_warp() {
+    return sizeof(Body4<T>) * TileCfg<T>::kCap + sizeof(Body4<T>) * kTargetChunk + sizeof(double) * 4 * kTargetChunk;
+}
+
+// Stage whole source leaves src[q], src[q+1], ... (below q1) of target leaf
+// B into sm, moved into B's frame, as many as fit in kCap bodies; returns the
+// body count, advances q and sets selfin if B itself is among them. The lanes
+// read 32 leaves' ranges and centres at once and copy their bodies with
+// independent loads, so the latency of the index, range and body loads is paid
+// once per 32 leaves rather than once per leaf. A leaf larger than kCap (a
+// level-21 leaf can exceed the leaf size) goes in pieces of kCap bodies, soff
+// being the next body of it.
+template <typename T, int kCap>
+__device__ __forceinline__ int stage_leaves(const LeafArgs& a, int B, float4 bh, float4 bl, uint32_t& q,
+                                            uint32_t q1, int& soff, Body4<T>* __restrict__ sm, bool& selfin,
+                                            int lane) {
+    int cnt = 0;
+    selfin = false;
+    {
+        // the next leaf does not fit in an empty stage, or a piece of it is already staged
+        const int A = (int)a.p2p_src[q];
+        const int a0 = a.t.begin[A], nA = a.t.end[A] - a0;
+        if (soff > 0 || nA > kCap) {
+            const int take = nA - soff < kCap ? nA - soff : kCap;
+            float ox = 0.f, oy = 0.f, oz = 0.f;
+            if (sizeof(T) == 4) {
+                const float4 ah = a.zhi[A], al = a.zlo[A];
+                ox = (ah.x - bh.x) + (al.x - bl.x);
+                oy = (ah.y - bh.y) + (al.y - bl.y);
+                oz = (ah.z - bh.z) + (al.z - bl.z);
+            }
+            for (int l = lane; l < take; l += 32) {
+                const int jj = a0 + soff + l;
+                Body4<T> v;
+                if (sizeof(T) == 4) {
+                    const float4 u = a.prel[jj];
+                    v = {(T)(u.x + ox), (T)(u.y + oy), (T)(u.z + oz), (T)u.w};
+                } else {
+                    v = {(T)a.xs[jj], (T)a.ys[jj], (T)a.zs[jj], (T)a.ms[jj]};
+                }
+                sm[l] = v;
+            }
+            selfin = A == B;
+            soff += take;
+            if (soff >= nA) {
+                soff = 0;
+                ++q;
+            }
+            return take;
+        }
+    }
+    while (q < q1) {
+        const int nl = q1 - q < 32u ? (int)(q1 - q) : 32;
+        int A = -1, a0 = 0, nA = 0;
+        float ox = 0.f, oy = 0.f, oz = 0.f;
+        if (lane < nl) {
+            A = (int)a.p2p_src[q + lane];
+            a0 = a.t.begin[A];
+            nA = a.t.end[A] - a0;
+            if (sizeof(T) == 4) {
+                const float4 ah = a.zhi[A], al = a.zlo[A];
+                ox = (ah.x - bh.x) + (al.x - bl.x);
+                oy = (ah.y - bh.y) + (al.y - bl.y);
+                oz = (ah.z - bh.z) + (al.z - bl.z);
+            }
+        }
+        int incl = nA;  // inclusive prefix sum of the leaf sizes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const unsigned fits = __ballot_sync(0xffffffffu, lane < nl && cnt + incl <= kCap);
+        // (an empty stage always takes the first leaf: one larger than kCap went the piecewise way above,
+        // and this loop stops before such a leaf once anything is staged)
+        const int fit = __popc(fits);  // a prefix of the leaves, since incl grows
+        selfin |= __any_sync(0xffffffffu, lane < fit && A == B) != 0;
+#pragma unroll 4
+        for (int j = 0; j < fit; ++j) {
+            const int aj = __shfl_sync(0xffffffffu, a0, j), nj = __shfl_sync(0xffffffffu, nA, j);
+            const int dst = cnt + __shfl_sync(0xffffffffu, incl, j) - nj;
+            const float oxj = __shfl_sync(0xffffffffu, ox, j), oyj = __shfl_sync(0xffffffffu, oy, j),
+                        ozj = __shfl_sync(0xffffffffu, oz, j);
+            for (int l = lane; l < nj; l += 32) {
+                Body4<T> v;
+                if (sizeof(T) == 4) {
+                    const float4 u = a.prel[aj + l];
+                    v = {(T)(u.x + oxj), (T)(u.y + oyj), (T)(u.z + ozj), (T)u.w};
+                } else {
+                    v = {(T)a.xs[aj + l], (T)a.ys[aj + l], (T)a.zs[aj + l], (T)a.ms[aj + l]};
+                }
+                sm[dst + l] = v;
+            }
+        }
+        if (fit > 0) cnt += __shfl_sync(0xffffffffu, incl, fit - 1);
+        q += (uint32_t)fit;
+        if (fit < nl) break;  // the stage is full
+    }
+    return cnt;
+}
+
+// Halving step of the transpose reduction: C values per lane become C/2;
+// a lane with bit o set keeps the upper half and receives its partner's.
+template <int C, typename T>
+__device__ __forceinline__ void halve(T* v, int lane, int o) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < C / 2; ++i) {
+        const T send = up ? v[i] : v[i + C / 2];
+        const T keep = up ? v[i + C / 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+}
+
+// v[0..V-1] on every lane (V = 32, 16 or 8). On return v[0] of lane l holds
+// the sum over the 32 lanes of value l % V.
+template <int V, typename T>
+__device__ __forceinline__ T transpose_reduce(T* v, int lane) {
+    static_assert(V == 32 || V == 16 || V == 8, "V");
+    if constexpr (V <= 16) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 16);
+    }
+    if constexpr (V == 8) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 8);
+    }
+    if constexpr (V == 32) halve<32>(v, lane, 16);
+    if constexpr (V >= 16) halve<16>(v, lane, 8);
+    halve<8>(v, lane, 4);
+    halve<4>(v, lane, 2);
+    halve<2>(v, lane, 1);
+    return v[0];
+}
+
+// One group of NT targets (b0 + t0 .. b0 + t0 + NT - 1, clamped to the last
+// target; clamped duplicates are computed and discarded) against the cnt
+// staged sources; adds the group's totals to tot[4 * (t0 + t) + c].
+template <typename T, int NT, bool GUARD, bool SOFT>
+__device__ __forceinline__ void p2p_group(const Body4<T>* __restrict__ sm, int cnt, const Body4<T>* __restrict__ tg,
+                                          int t0, int nt, T s2, double* tot, int lane) {
+    constexpr int kRun = TileCfg<T>::kRun;
+    T tx[NT], ty[NT], tz[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const Body4<T> v = tg[t0 + t < nt ? t0 + t : nt - 1];
+        tx[t] = v.x; ty[t] = v.y; tz[t] = v.z;
+    }
+    T run[NT * 4], acc[NT * 4];
+#pragma unroll
+    for (int e = 0; e < NT * 4; ++e) { run[e] = T(0); acc[e] = T(0); }
+    static_assert(kRun >= (1 << 30) || sizeof(T) == 4, "fold only in FP32");
+    const int per_lane = (cnt + 31) >> 5;
+    for (int u = 0; u < per_lane; ++u) {
+        const int k = lane + 32 * u;
+        const Body4<T> s = sm[k < cnt ? k : cnt - 1];
+        const T mj = k < cnt ? s.w : T(0);  // padding sources carry no mass
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const T dx = s.x - tx[t], dy = s.y - ty[t], dz = s.z - tz[t];
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            T rinv;
+            if constexpr (sizeof(T) == 4) rinv = rsqrtf(SOFT ? r2 + s2 : r2);
+            else rinv = (T)rsqrt_nr((double)(SOFT ? r2 + s2 : r2));
+            if (GUARD && !(r2 > T(0))) rinv = T(0);  // the body itself
+            const T mr = mj * rinv;
+            const T mr3 = mr * rinv * rinv;
+            run[4 * t] += mr3 * dx;
+            run[4 * t + 1] += mr3 * dy;
+            run[4 * t + 2] += mr3 * dz;
+            run[4 * t + 3] += mr;
+        }
+        if (kRun < (1 << 30) && (u % kRun) == kRun - 1) {
+#pragma unroll
+            for (int e = 0; e < NT * 4; ++e) { acc[e] += run[e]; run[e] = T(0); }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < NT * 4; ++e) acc[e] += run[e];
+    const T v = transpose_reduce<NT * 4>(acc, lane);
+    if (lane < NT * 4 && 4 * t0 + lane < 4 * nt) tot[4 * t0 + lane] += (double)v;
+}
+
+template <typename T, bool GUARD, bool SOFT>
+__device__ __forceinline__ void p2p_groups(const Body4<T>* __restrict__ sm, int cnt, const Body4<T>* __restrict__ tg,
+                                           int nt, T s2, double* tot, int lane) {
+    constexpr int TG = TileCfg<T>::TG;
+    int t0 = 0;
+    for (; nt - t0 > TG / 2; t0 += TG) p2p_group<T, TG, GUARD, SOFT>(sm, cnt, tg, t0, nt, s2, tot, lane);
+    if (t0 < nt) p2p_group<T, TG / 2, GUARD, SOFT>(sm, cnt, tg, t0, nt, s2, tot, lane);
+}
+
+template <typename T, bool SOFT>
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 5) k_p2p_tiles(LeafArgs a, const int* __restrict__ item_leaf,
+                                                    const uint32_t* __restrict__ item_first,
+                                                    const uint32_t* __restrict__ slot_first,
+                                                    const uint32_t* __restrict__ nitems_p, unsigned* __restrict__ work) {
+    constexpr int kCap = TileCfg<T>::kCap;
+    extern __shared__ __align__(16) unsigned char p2p_smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char* wbase = p2p_smem + (size_t)wib * p2p_tile_smem_per_warp<T>();
+    Body4<T>* sm = reinterpret_cast<Body4<T>*>(wbase);
+    Body4<T>* tg = sm + kCap;
+    double* tot = reinterpret_cast<double*>(tg + kTargetChunk);
+    const int nitems = (int)*nitems_p;
+    const T s2 = SOFT ? (sizeof(T) == 4 ? (T)a.soft2f : (T)a.soft2) : T(0);
+    for (;;) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(work, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if ((int)it >= nitems) break;
+        const int B = item_leaf[it];
+        const int j = (int)(it - item_first[B]);
+        const uint32_t q0 = a.p2p_off[B] + (uint32_t)j * kLeavesPerItem;
+        const uint32_t qe = a.p2p_off[B + 1];
+        const uint32_t q1 = q0 + kLeavesPerItem < qe ? q0 + kLeavesPerItem : qe;
+        const int b0 = a.t.begin[B], nB = a.t.end[B] - b0;
+        const uint32_t slot0 = slot_first[B] + (uint32_t)j * (uint32_t)nB;
+        const float4 bh = a.zhi[B], bl = a.zlo[B];
+        unsigned long long nsrc = 0;  // source bodies of this item (for the interaction count)
+        bool self_item = false;
+        for (int tc = 0; tc < nB; tc += kTargetChunk) {
+            const int nt = nB - tc < kTargetChunk ? nB - tc : kTargetChunk;
+            __syncwarp();
+            for (int e = lane; e < 4 * nt; e += 32) tot[e] = 0.0;
+            for (int t = lane; t < nt; t += 32) {
+                const int i = b0 + tc + t;
+                if (sizeof(T) == 4) {
+                    const float4 v = a.prel[i];
+                    tg[t] = {(T)v.x, (T)v.y, (T)v.z, (T)v.w};
+                } else {
+                    tg[t] = {(T)a.xs[i], (T)a.ys[i], (T)a.zs[i], (T)a.ms[i]};
+                }
+            }
+            uint32_t q = q0;
+            int soff = 0;
+            while (q < q1) {
+                __syncwarp();
+                bool selfin = false;
+                const int cnt = stage_leaves<T, kCap>(a, B, bh, bl, q, q1, soff, sm, selfin, lane);
+                __syncwarp();
+                if (tc == 0) { nsrc += (unsigned long long)cnt; self_item |= selfin; }
+                if (selfin) p2p_groups<T, true, SOFT>(sm, cnt, tg, nt, s2, tot, lane);
+                else p2p_groups<T, false, SOFT>(sm, cnt, tg, nt, s2, tot, lane);
+            }
+            __syncwarp();
+            // totals to the item's partial slots: (ax, ay) in part_hi, (az, sum m/r) in part_lo
+            double* hi = reinterpret_cast<double*>(a.part_hi);
+            double* lo = reinterpret_cast<double*>(a.part_lo);
+            for (int e = lane; e < 4 * nt; e += 32) {
+                const size_t slot = (size_t)slot0 + (size_t)(tc + (e >> 2));
+                const int c = e & 3;
+                (c < 2 ? hi : lo)[2 * slot + (c & 1)] = tot[e];
+            }
+        }
+        // directed body-body interactions of the item (a body never acts on itself)
+        if (lane == 0)
+            atomicAdd(a.interactions, (unsigned long long)nB * nsrc - (self_item ? (unsigned long long)nB : 0ull));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// P2P force over work items, targets across lanes (the alternative layout,
+// selected by GBFMM_P2P_TILES = 0): a warp stages the item's sources in
+// shared memory 256 at a time and gives each of the nt targets of a chunk of
+// 32 G = 32 / nt lanes that split the sources between them; FP32 runs of
+// kRun terms are folded into two-sum pairs; one partial per target body.
 // SOFT: Plummer softening (Appendix B), 1/r -> 1/sqrt(r^2 + s2); the body
 // itself (r2 = 0; coincident bodies are rejected) still contributes nothing.
 template <typename T, bool GUARD, int GC, bool SOFT>
@@ -221,14 +534,13 @@ __device__ __forceinline__ void p2p_pack(const Body4<T>* __restrict__ sm, int cn
 }
 
 template <typename T, bool SOFT>
-__global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __restrict__ item_leaf,
+__global__ void __launch_bounds__(128) k_p2p_lanes(LeafArgs a, const int* __restrict__ item_leaf,
                                                     const uint32_t* __restrict__ item_first,
                                                     const uint32_t* __restrict__ slot_first,
                                                     const uint32_t* __restrict__ nitems_p, unsigned* __restrict__ work) {
     __shared__ Body4<T> stage[4][kStageCap];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Body4<T>* sm = stage[wib];
-    const uint64_t mask = (1ull << a.nb) - 1ull;
     const int nitems = (int)*nitems_p;
     for (;;) {
         unsigned it = 0;
@@ -268,7 +580,7 @@ __global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __rest
                 int cnt = 0;
                 bool selfin = false;
                 while (q < q1) {
-                    const int A = (int)(a.p2p_keys[q] & mask);
+                    const int A = (int)a.p2p_src[q];
                     const int a0 = a.t.begin[A], nA = a.t.end[A] - a0;
                     const int rem = nA - soff;
                     int take = rem;
@@ -350,7 +662,7 @@ __global__ void __launch_bounds__(128) k_p2p_items(LeafArgs a, const int* __rest
 
 // One thread per body: L2P of its leaf's local expansion plus the P2P
 // partials of its leaf's items in item order; G-scaled, to the caller's order.
-template <typename T>
+template <typename T, int PC>
 __global__ void __launch_bounds__(128) k_leaf_reduce(LeafArgs a, const int* __restrict__ leaf_of,
                                                       const uint32_t* __restrict__ item_first,
                                                       const uint32_t* __restrict__ slot_first) {
@@ -366,8 +678,8 @@ __global__ void __launch_bounds__(128) k_leaf_reduce(LeafArgs a, const int* __re
         const float inv_s = 1.0f / bh.w;
         const float4 v = a.prel[i];
         float phi, fx, fy, fz;
-        l2p_hat<float>(a.p, reinterpret_cast<const float*>(a.loc) + (size_t)nr * B, v.x * inv_s, v.y * inv_s,
-                       v.z * inv_s, inv_s, tb, phi, fx, fy, fz);
+        l2p_hat<float, TabL32, PC>(a.p, reinterpret_cast<const float*>(a.loc) + (size_t)nr * B, v.x * inv_s,
+                                   v.y * inv_s, v.z * inv_s, inv_s, tb, phi, fx, fy, fz);
         sx = fx; sy = fy; sz = fz; sp = phi;
     } else {
         const TabL64 tb{a.tb.w, a.tb.iw, a.tb.rec_a, a.tb.rec_b, a.tb.diag, a.tb.sub};
@@ -628,7 +940,6 @@ __global__ void __launch_bounds__(128) k_jerk_items(LeafArgs a, const double* __
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Body4<T>* sm = stage[wib];
     Body4<T>* su = vstage[wib];
-    const uint64_t mask = (1ull << a.nb) - 1ull;
     const int nitems = (int)*nitems_p;
     const size_t n = (size_t)a.t.n;
     const T s2 = sizeof(T) == 4 ? (T)a.soft2f : (T)a.soft2;
@@ -669,7 +980,7 @@ __global__ void __launch_bounds__(128) k_jerk_items(LeafArgs a, const double* __
                 __syncwarp();
                 int cnt = 0;
                 while (q < q1) {
-                    const int A = (int)(a.p2p_keys[q] & mask);
+                    const int A = (int)a.p2p_src[q];
                     const int a0 = a.t.begin[A], nA = a.t.end[A] - a0;
                     const int rem = nA - soff;
                     int take = rem;
@@ -830,19 +1141,60 @@ void leaf_items_fill(const TreeView& t, const uint32_t* item_first, int* item_le
     (k_leaf_of_bodies<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, leaf_of), note_launch());
 }
 
-void leaf_eval(const LeafArgs& a, bool fp32, const int* item_leaf, const uint32_t* item_first,
+#ifndef GBFMM_P2P_TILES
+#define GBFMM_P2P_TILES 1
+#endif
+
+namespace {
+// persistent grid: as many blocks as fit on every SM (warps take items from a counter)
+template <typename T, bool SOFT>
+void launch_p2p_tiles(const LeafArgs& a, const int* item_leaf, const uint32_t* item_first, const uint32_t* slot_first,
+                      const uint32_t* nitems, unsigned* work, cudaStream_t st) {
+    if (!GBFMM_P2P_TILES) {
+        (k_p2p_lanes<T, SOFT><<<device_sm_count() * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems,
+                                                                     work),
+         note_launch());
+        return;
+    }
+    const int sh = (int)(4 * p2p_tile_smem_per_warp<T>());
+    ensure_dyn_smem((const void*)k_p2p_tiles<T, SOFT>, sh);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p_tiles<T, SOFT>, 128, sh) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    (k_p2p_tiles<T, SOFT><<<device_sm_count() * per_sm, 128, sh, st>>>(a, item_leaf, item_first, slot_first, nitems,
+                                                                       work),
+     note_launch());
+}
+}  // namespace
+
+void leaf_eval(const LeafArgs& a, bool p2p32, bool l2p32, const int* item_leaf, const uint32_t* item_first,
                const uint32_t* slot_first, const uint32_t* nitems, unsigned* work, const int* leaf_of,
                cudaStream_t st) {
     cudaMemsetAsync(work, 0, sizeof(unsigned), st);
     const bool soft = a.soft2 > 0.0;
-    if (fp32) {
-        if (soft) (k_p2p_items<float, true><<<device_sm_count() * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
-        else (k_p2p_items<float, false><<<device_sm_count() * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
-        (k_leaf_reduce<float><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch());
+    if (p2p32) {
+        if (soft) launch_p2p_tiles<float, true>(a, item_leaf, item_first, slot_first, nitems, work, st);
+        else launch_p2p_tiles<float, false>(a, item_leaf, item_first, slot_first, nitems, work, st);
     } else {
-        if (soft) (k_p2p_items<double, true><<<device_sm_count() * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
-        else (k_p2p_items<double, false><<<device_sm_count() * 16, 128, 0, st>>>(a, item_leaf, item_first, slot_first, nitems, work), note_launch());
-        (k_leaf_reduce<double><<<blocks_for(a.t.n, 128), 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch());
+        if (soft) launch_p2p_tiles<double, true>(a, item_leaf, item_first, slot_first, nitems, work, st);
+        else launch_p2p_tiles<double, false>(a, item_leaf, item_first, slot_first, nitems, work, st);
+    }
+    const int nb = blocks_for(a.t.n, 128);
+    if (l2p32) {
+        switch (a.p) {
+            case 4: (k_leaf_reduce<float, 4><<<nb, 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch()); break;
+            case 6: (k_leaf_reduce<float, 6><<<nb, 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch()); break;
+            case 8: (k_leaf_reduce<float, 8><<<nb, 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch()); break;
+            case 10: (k_leaf_reduce<float, 10><<<nb, 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch()); break;
+            case 12: (k_leaf_reduce<float, 12><<<nb, 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch()); break;
+            case 14: (k_leaf_reduce<float, 14><<<nb, 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch()); break;
+            default: (k_leaf_reduce<float, 0><<<nb, 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch()); break;
+        }
+    } else {
+        (k_leaf_reduce<double, 0><<<nb, 128, 0, st>>>(a, leaf_of, item_first, slot_first), note_launch());
     }
 }
 

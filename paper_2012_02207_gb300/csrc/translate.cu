@@ -146,10 +146,35 @@ __device__ void wswap(WarpVec<T>& w, int p, const RotTables<T>& tb, int lane) {
 // shared values per warp: vector, scratch, two power tables, u^k and (s_C/s_P)^k
 __host__ __device__ inline int m2m_warp_values(int p) { return 2 * ncoef_real(p) + 6 * (p + 1); }
 
+// The geometry of the shift from node C's centre to its parent P's, one
+// thread per node: with b = z_C - z_P, the angles of b (cos and sin of phi
+// and theta), u = |b| / s_P and s_C / s_P. The warps of the M2M and L2L
+// kernels read these instead of each evaluating the FP64 square roots and
+// divisions on all of their lanes (a warp's FP64 instruction occupies the
+// FP64 pipe about as long whether one lane or 32 need the value).
+__global__ void k_shift_geometry(TreeView t, const double* __restrict__ zc, const double* __restrict__ hs,
+                                 double* __restrict__ geo) {
+    const int C = blockIdx.x * blockDim.x + threadIdx.x;
+    if (C >= *t.dnn) return;
+    const int P = t.parent[C];
+    if (P < 0) return;  // a root shifts nowhere
+    const double bx = zc[3 * C] - zc[3 * P], by = zc[3 * C + 1] - zc[3 * P + 1], bz = zc[3 * C + 2] - zc[3 * P + 2];
+    const double rxy2 = bx * bx + by * by;
+    const double rho = sqrt(rxy2 + bz * bz);
+    const double rxy = sqrt(rxy2);
+    double cp = 1.0, sp = 0.0, ct = 1.0, st = 0.0;
+    if (rxy > 0.0) { cp = bx / rxy; sp = by / rxy; }
+    if (rho > 0.0) { ct = bz / rho; st = rxy / rho; }
+    const double sP = hs[P];
+    double* g = geo + kShiftGeo * (size_t)C;
+    g[0] = cp; g[1] = sp; g[2] = ct; g[3] = st;
+    g[4] = rho / sP;
+    g[5] = hs[C] / sP;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int Lc, int p,
-                                                  const double* __restrict__ zc,
-                                                  const double* __restrict__ hs,
+                                                  const double* __restrict__ geo,
                                                   const double* __restrict__ mult,
                                                   double* __restrict__ contrib, RotTables<T> tb) {
     extern __shared__ __align__(16) unsigned char sh_m2m_raw[];
@@ -167,16 +192,9 @@ __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int Lc, int p,
     const int P = t.parent[C];
     const double* src = mult + (size_t)nr * C;
     for (int q = lane; q < nr; q += 32) wv.v[q] = ar_from<T>(src[q]);
-    // the geometry of the shift in FP64 (a few instructions per child)
-    const double bx = zc[3 * C] - zc[3 * P], by = zc[3 * C + 1] - zc[3 * P + 1], bz = zc[3 * C + 2] - zc[3 * P + 2];
-    const double rxy2 = bx * bx + by * by;
-    const double rho = sqrt(rxy2 + bz * bz);
-    const double rxy = sqrt(rxy2);
-    double cp = 1.0, sp = 0.0, ct = 1.0, st = 0.0;
-    if (rxy > 0.0) { cp = bx / rxy; sp = by / rxy; }
-    if (rho > 0.0) { ct = bz / rho; st = rxy / rho; }
-    const double sP = hs[P];
-    const double u = rho / sP, sg = hs[C] / sP;
+    (void)P;
+    const double* gc = geo + kShiftGeo * (size_t)C;  // the shift's geometry (k_shift_geometry)
+    const double cp = gc[0], sp = gc[1], ct = gc[2], st = gc[3], u = gc[4], sg = gc[5];
     wpowers<T>(pwa, p, ar_from<T>(sp), ar_from<T>(cp), lane);
     wpowers<T>(pwb, p, ar_from<T>(ct), ar_from<T>(-st), lane);
     // u^k and (s_C/s_P)^k, lane k by binary powering
@@ -224,8 +242,7 @@ __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int Lc, int p,
 // (T = float or double) are added to the child's, which the M2L wrote.
 template <typename T>
 __global__ void __launch_bounds__(128) k_l2l_rot(TreeView t, int L, int p,
-                                                  const double* __restrict__ zc,
-                                                  const double* __restrict__ hs,
+                                                  const double* __restrict__ geo,
                                                   T* __restrict__ loc, RotTables<T> tb) {
     extern __shared__ __align__(16) unsigned char sh_l2l_raw[];
     T* sh = reinterpret_cast<T*>(sh_l2l_raw);
@@ -242,15 +259,8 @@ __global__ void __launch_bounds__(128) k_l2l_rot(TreeView t, int L, int p,
     const int P = t.parent[C];
     const T* src = loc + (size_t)nr * P;
     for (int q = lane; q < nr; q += 32) wv.v[q] = src[q];
-    const double bx = zc[3 * C] - zc[3 * P], by = zc[3 * C + 1] - zc[3 * P + 1], bz = zc[3 * C + 2] - zc[3 * P + 2];
-    const double rxy2 = bx * bx + by * by;
-    const double rho = sqrt(rxy2 + bz * bz);
-    const double rxy = sqrt(rxy2);
-    double cp = 1.0, sp = 0.0, ct = 1.0, st = 0.0;
-    if (rxy > 0.0) { cp = bx / rxy; sp = by / rxy; }
-    if (rho > 0.0) { ct = bz / rho; st = rxy / rho; }
-    const double sP = hs[P];
-    const double u = rho / sP, sg = hs[C] / sP;
+    const double* gc = geo + kShiftGeo * (size_t)C;  // the shift's geometry (k_shift_geometry)
+    const double cp = gc[0], sp = gc[1], ct = gc[2], st = gc[3], u = gc[4], sg = gc[5];
     wpowers<T>(pwa, p, ar_from<T>(sp), ar_from<T>(cp), lane);
     wpowers<T>(pwb, p, ar_from<T>(ct), ar_from<T>(-st), lane);
     if (lane <= p) {
@@ -300,45 +310,50 @@ __global__ void k_m2m_sum(TreeView t, int L, int nr, const double* __restrict__ 
 }
 
 template <typename T>
-void launch_m2m(const TreeView& t, int Lc, int p, const double* zc, const double* hs,
+void launch_m2m(const TreeView& t, int Lc, int p, const double* geo,
                 const double* mult, double* contrib, const RotTables<T>& tb, cudaStream_t st) {
     const size_t sh = (size_t)4 * m2m_warp_values(p) * sizeof(T);
     ensure_dyn_smem((const void*)k_m2m_rot<T>, 100 * 1024);
     const int nblk = (t.lvl_cnt[Lc] + 3) / 4;
-    (k_m2m_rot<T><<<nblk, 128, sh, st>>>(t, Lc, p, zc, hs, mult, contrib, tb), note_launch());
+    (k_m2m_rot<T><<<nblk, 128, sh, st>>>(t, Lc, p, geo, mult, contrib, tb), note_launch());
 }
 
 template <typename T>
-void launch_l2l(const TreeView& t, int L, int p, const double* zc, const double* hs, T* loc,
+void launch_l2l(const TreeView& t, int L, int p, const double* geo, T* loc,
                 const RotTables<T>& tb, cudaStream_t st) {
     const size_t sh = (size_t)4 * m2m_warp_values(p) * sizeof(T);
     ensure_dyn_smem((const void*)k_l2l_rot<T>, 100 * 1024);
     const int nblk = (t.lvl_cnt[L] + 3) / 4;
-    (k_l2l_rot<T><<<nblk, 128, sh, st>>>(t, L, p, zc, hs, loc, tb), note_launch());
+    (k_l2l_rot<T><<<nblk, 128, sh, st>>>(t, L, p, geo, loc, tb), note_launch());
 }
 
 }  // namespace
 
-void l2l_level(const TreeView& t, int L, int p, const double* zc, const double* hs, void* loc,
-               const DevTables& tb, bool fp32, cudaStream_t st) {
+void shift_geometry(const TreeView& t, const double* zc, const double* hs, double* geo, cudaStream_t st) {
+    if (t.nnodes > 0)
+        (k_shift_geometry<<<(t.nnodes + 127) / 128, 128, 0, st>>>(t, zc, hs, geo), note_launch());
+}
+
+void l2l_level(const TreeView& t, int L, int p, const double* geo, void* loc, const DevTables& tb, bool fp32,
+               cudaStream_t st) {
     if (t.lvl_cnt[L] <= 0) return;
     if (fp32)
-        launch_l2l<float>(t, L, p, zc, hs, static_cast<float*>(loc),
+        launch_l2l<float>(t, L, p, geo, static_cast<float*>(loc),
                           RotTables<float>{tb.swap_cos_dw, tb.swap_sin_dw, tb.zshift_dw}, st);
     else
-        launch_l2l<double>(t, L, p, zc, hs, static_cast<double*>(loc),
+        launch_l2l<double>(t, L, p, geo, static_cast<double*>(loc),
                            RotTables<double>{tb.swap_cos, tb.swap_sin, tb.zshift}, st);
 }
 
-void m2m_level(const TreeView& t, int L, int p, const double* zc, const double* hs, double* mult,
-               double* contrib, const DevTables& tb, bool dword, cudaStream_t st) {
+void m2m_level(const TreeView& t, int L, int p, const double* geo, double* mult, double* contrib,
+               const DevTables& tb, bool dword, cudaStream_t st) {
     if (t.lvl_cnt[L + 1] <= 0) return;
     const int nr = ncoef_real(p);
     if (dword)
-        launch_m2m<dw>(t, L + 1, p, zc, hs, mult, contrib,
+        launch_m2m<dw>(t, L + 1, p, geo, mult, contrib,
                        RotTables<dw>{tb.swap_cos_dw, tb.swap_sin_dw, tb.zshift_dw}, st);
     else
-        launch_m2m<double>(t, L + 1, p, zc, hs, mult, contrib,
+        launch_m2m<double>(t, L + 1, p, geo, mult, contrib,
                            RotTables<double>{tb.swap_cos, tb.swap_sin, tb.zshift}, st);
     const int64_t work = (int64_t)t.lvl_cnt[L] * nr;
     (k_m2m_sum<<<(int)((work + 127) / 128), 128, 0, st>>>(t, L, nr, contrib, mult), note_launch());

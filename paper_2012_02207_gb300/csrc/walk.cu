@@ -282,16 +282,17 @@ __global__ void k_directed32(const int2* __restrict__ pairs, const unsigned long
     if (pr.x == pr.y) atomicAdd(count, 1ull);
 }
 
-// sorted 32-bit keys -> the 64-bit keys the consumers read, and the CSR offsets
-__global__ void k_offsets_widen(const uint32_t* __restrict__ k32, int64_t nk,
+// sorted 32-bit keys -> the source index of every entry (what the consumers
+// read) and the CSR offsets per target
+__global__ void k_offsets_src32(const uint32_t* __restrict__ k32, int64_t nk,
                                 const unsigned long long* __restrict__ dnk, int nb, const int* __restrict__ dnn,
-                                uint64_t* __restrict__ keys, uint32_t* __restrict__ off) {
+                                uint32_t* __restrict__ src, uint32_t* __restrict__ off) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if ((int64_t)*dnk < nk) nk = (int64_t)*dnk;
     if (i > nk) return;
     const int nnodes = *dnn;
     const uint32_t k = i < nk ? k32[i] : 0xffffffffu;
-    if (i < nk) keys[i] = k == 0xffffffffu ? ~0ull : (uint64_t)k;
+    if (i < nk) src[i] = k == 0xffffffffu ? 0xffffffffu : (k & ((1u << nb) - 1u));
     int64_t t = (i < nk) ? (int64_t)(k >> nb) : (int64_t)nnodes;
     int64_t tp = (i > 0) ? (int64_t)(k32[i - 1] >> nb) : -1;
     t = t < nnodes ? t : nnodes;
@@ -300,11 +301,12 @@ __global__ void k_offsets_widen(const uint32_t* __restrict__ k32, int64_t nk,
 }
 
 __global__ void k_offsets(const uint64_t* __restrict__ keys, int64_t nk, const unsigned long long* __restrict__ dnk,
-                          int nb, const int* __restrict__ dnn, uint32_t* __restrict__ off) {
+                          int nb, const int* __restrict__ dnn, uint32_t* __restrict__ src, uint32_t* __restrict__ off) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if ((int64_t)*dnk < nk) nk = (int64_t)*dnk;
     if (i > nk) return;
     const int nnodes = *dnn;
+    if (i < nk) src[i] = keys[i] == ~0ull ? 0xffffffffu : (uint32_t)(keys[i] & ((1ull << nb) - 1ull));
     // marker keys (all ones, from self pairs) sort last and count as "past the end"
     int64_t t = (i < nk) ? (int64_t)(keys[i] >> nb) : (int64_t)nnodes;
     int64_t tp = (i > 0) ? (int64_t)(keys[i - 1] >> nb) : -1;
@@ -314,23 +316,33 @@ __global__ void k_offsets(const uint64_t* __restrict__ keys, int64_t nk, const u
 }
 
 // far part of the estimate: per cell, M_A / r^2 summed over theta-partners in
-// ascending order, r^2 from the FP32-rounded centre offsets.
+// ascending order, r^2 from the FP32-rounded centre offsets. One warp per
+// cell: the lanes form the terms of 32 partners at a time, then the terms are
+// added one after the other in partner order (the same sequence of FP32
+// additions as a single thread walking the list).
 __global__ void k_far_f(const int* __restrict__ dnn, const double* __restrict__ zc, const double* __restrict__ M,
-                        const uint64_t* __restrict__ keys, const uint32_t* __restrict__ off, int nb,
+                        const uint32_t* __restrict__ src, const uint32_t* __restrict__ off,
                         float* __restrict__ farf) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (b >= *dnn) return;
-    const uint64_t mask = (1ull << nb) - 1ull;
     const double bx = zc[3 * b], by = zc[3 * b + 1], bz = zc[3 * b + 2];
     float acc = 0.0f;
-    for (uint32_t q = off[b]; q < off[b + 1]; ++q) {
-        const int a = (int)(keys[q] & mask);
-        const float dx = (float)(zc[3 * a] - bx), dy = (float)(zc[3 * a + 1] - by),
-                    dz = (float)(zc[3 * a + 2] - bz);
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        acc = acc + (float)M[a] / r2;
+    const uint32_t q0 = off[b], q1 = off[b + 1];
+    for (uint32_t qb = q0; qb < q1; qb += 32) {
+        const uint32_t q = qb + lane;
+        float term = 0.0f;
+        if (q < q1) {
+            const int a = (int)src[q];
+            const float dx = (float)(zc[3 * a] - bx), dy = (float)(zc[3 * a + 1] - by),
+                        dz = (float)(zc[3 * a + 2] - bz);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            term = (float)M[a] / r2;
+        }
+        const int cnt = q1 - qb < 32u ? (int)(q1 - qb) : 32;
+        for (int k = 0; k < cnt; ++k) acc = acc + __shfl_sync(0xffffffffu, term, k);
     }
-    farf[b] = acc;
+    if (lane == 0) farf[b] = acc;
 }
 
 // g(k) = g(parent) + far(k), accumulated from the root down the ancestor chain
@@ -345,41 +357,65 @@ __global__ void k_push_down(TreeView t, const float* __restrict__ farf, float* _
     g[k] = acc;
 }
 
-// near part per body: partner leaves ascending, their bodies in order, j != i
-__global__ void k_near_f(TreeView t, const float4* __restrict__ xf, const uint64_t* __restrict__ keys,
-                         const uint32_t* __restrict__ off, int nb, const int* __restrict__ leaf_of,
-                         const float* __restrict__ g, float soft2f, float* __restrict__ f) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= t.n) return;
-    const int b = leaf_of[i];
-    const uint64_t mask = (1ull << nb) - 1ull;
-    const float4 pi = xf[i];
-    float acc = 0.0f;
-    for (uint32_t q = off[b]; q < off[b + 1]; ++q) {
-        const int a = (int)(keys[q] & mask);
-        const int j0 = t.begin[a], j1 = t.end[a];
-        for (int j = j0; j < j1; ++j) {
-            if (j == i) continue;
-            const float4 pj = xf[j];
-            const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            if (!(r2 > 0.0f)) continue;
-            if (soft2f > 0.0f) {
-                // softened magnitude m r / (r^2 + soft^2)^{3/2}
-                const float s2 = r2 + soft2f;
-                acc = acc + pj.w * sqrtf(r2) / (s2 * sqrtf(s2));
-            } else {
-                acc = acc + pj.w / r2;
-            }
-        }
+// near part per body: partner leaves ascending, their bodies in order, j != i.
+// One warp per leaf, lane t for its bodies t and t + 32 (the leaf size is at
+// most 64 here; larger leaves take more passes): every lane walks the same
+// partner bodies, so the loads are broadcasts and no lane diverges, and each
+// body's sum is the same sequence of FP32 additions as before.
+template <bool SOFT>
+__device__ __forceinline__ float near_term(float4 pi, float4 pj, float soft2f, bool& use) {
+    const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    use = r2 > 0.0f;
+    if (SOFT) {
+        // softened magnitude m r / (r^2 + soft^2)^{3/2}
+        const float s2 = r2 + soft2f;
+        return pj.w * sqrtf(r2) / (s2 * sqrtf(s2));
     }
-    f[i] = g[b] + acc;
+    return pj.w / r2;
 }
 
-__global__ void k_leaf_of(TreeView t, int* __restrict__ leaf_of) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= *t.dnn || t.nchild[k] != 0) return;
-    for (int i = t.begin[k]; i < t.end[k]; ++i) leaf_of[i] = k;
+template <bool SOFT>
+__global__ void k_near_f(TreeView t, const float4* __restrict__ xf, const uint32_t* __restrict__ src,
+                         const uint32_t* __restrict__ off, const float* __restrict__ g, float soft2f,
+                         float* __restrict__ f) {
+    const int b = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= *t.dnn || t.nchild[b] != 0) return;
+    const int b0 = t.begin[b], nB = t.end[b] - b0;
+    const uint32_t q0 = off[b], q1 = off[b + 1];
+    for (int t0 = 0; t0 < nB; t0 += 64) {
+        const int i0 = b0 + t0 + lane, i1 = i0 + 32;
+        const bool act0 = t0 + lane < nB, act1 = t0 + lane + 32 < nB;
+        const float4 p0 = xf[act0 ? i0 : b0], p1 = xf[act1 ? i1 : b0];
+        float acc0 = 0.0f, acc1 = 0.0f;
+        if (nB - t0 > 32) {  // two bodies per lane
+            for (uint32_t q = q0; q < q1; ++q) {
+                const int a = (int)src[q];
+                const int j0 = t.begin[a], j1 = t.end[a];
+                for (int j = j0; j < j1; ++j) {
+                    const float4 pj = xf[j];
+                    bool u0, u1;
+                    const float v0 = near_term<SOFT>(p0, pj, soft2f, u0);
+                    const float v1 = near_term<SOFT>(p1, pj, soft2f, u1);
+                    if (u0 && j != i0) acc0 = acc0 + v0;
+                    if (u1 && j != i1) acc1 = acc1 + v1;
+                }
+            }
+        } else {
+            for (uint32_t q = q0; q < q1; ++q) {
+                const int a = (int)src[q];
+                const int j0 = t.begin[a], j1 = t.end[a];
+                for (int j = j0; j < j1; ++j) {
+                    bool u0;
+                    const float v0 = near_term<SOFT>(p0, xf[j], soft2f, u0);
+                    if (u0 && j != i0) acc0 = acc0 + v0;
+                }
+            }
+        }
+        if (act0) f[i0] = g[b] + acc0;
+        if (act1) f[i1] = g[b] + acc1;
+    }
 }
 
 // fmin of a leaf over its bodies; of an internal cell over its children
@@ -492,29 +528,33 @@ void pairs_to_directed32(const int2* pairs, const unsigned long long* np, int64_
      note_launch());
 }
 
-void directed_offsets_widen(const uint32_t* k32, int64_t nkeys, const unsigned long long* dnk, int nb,
-                            const int* dnn, uint64_t* keys, uint32_t* off, cudaStream_t st) {
-    (k_offsets_widen<<<blocks_for(nkeys + 1, 256), 256, 0, st>>>(k32, nkeys, dnk, nb, dnn, keys, off), note_launch());
+void directed_offsets_src32(const uint32_t* k32, int64_t nkeys, const unsigned long long* dnk, int nb,
+                            const int* dnn, uint32_t* src, uint32_t* off, cudaStream_t st) {
+    (k_offsets_src32<<<blocks_for(nkeys + 1, 256), 256, 0, st>>>(k32, nkeys, dnk, nb, dnn, src, off), note_launch());
 }
 
 void directed_offsets(const uint64_t* keys, int64_t nkeys, const unsigned long long* dnk, int nb, const int* dnn,
-                      uint32_t* off, cudaStream_t st) {
-    (k_offsets<<<blocks_for(nkeys + 1, 256), 256, 0, st>>>(keys, nkeys, dnk, nb, dnn, off), note_launch());
+                      uint32_t* src, uint32_t* off, cudaStream_t st) {
+    (k_offsets<<<blocks_for(nkeys + 1, 256), 256, 0, st>>>(keys, nkeys, dnk, nb, dnn, src, off), note_launch());
 }
 
 void scalar_force(const TreeView& t, const double* zc, const double* M, const float4* xf,
-                  const uint64_t* far_keys, const uint32_t* far_off, const uint64_t* near_keys,
-                  const uint32_t* near_off, int nb, const int* h_level_start, double soft, float* farf,
+                  const uint32_t* far_src, const uint32_t* far_off, const uint32_t* near_src,
+                  const uint32_t* near_off, const int* h_level_start, double soft, float* farf,
                   float* f, float* fmin, cudaStream_t st) {
-    // farf doubles as scratch: [0, nnodes) far sums, [nnodes, 2 nnodes) pushed-down g,
-    // and the leaf index of every body after that.
+    // farf doubles as scratch: [0, nnodes) far sums, [nnodes, 2 nnodes) pushed-down g
     float* g = farf + t.nnodes;
-    int* leaf_of = reinterpret_cast<int*>(farf + 2 * (size_t)t.nnodes);
-    (k_far_f<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t.dnn, zc, M, far_keys, far_off, nb, farf), note_launch());
+    (k_far_f<<<blocks_for(32 * (int64_t)t.nnodes, 128), 128, 0, st>>>(t.dnn, zc, M, far_src, far_off, farf),
+     note_launch());
     (k_push_down<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, farf, g), note_launch());
-    (k_leaf_of<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, leaf_of), note_launch());
-    (k_near_f<<<blocks_for(t.n, 128), 128, 0, st>>>(t, xf, near_keys, near_off, nb, leaf_of, g,
-                                                    (float)(soft * soft), f), note_launch());
+    if ((float)(soft * soft) > 0.0f)
+        (k_near_f<true><<<blocks_for(32 * (int64_t)t.nnodes, 128), 128, 0, st>>>(t, xf, near_src, near_off, g,
+                                                                                 (float)(soft * soft), f),
+         note_launch());
+    else
+        (k_near_f<false><<<blocks_for(32 * (int64_t)t.nnodes, 128), 128, 0, st>>>(t, xf, near_src, near_off, g,
+                                                                                  0.0f, f),
+         note_launch());
     (k_fmin_leaves<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, f, fmin), note_launch());
     (void)h_level_start;
     for (int L = t.nlevels - 2; L >= 0; --L)
