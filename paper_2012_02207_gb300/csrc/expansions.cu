@@ -194,6 +194,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m(TreeView t, int p, TabF64 tb
 // pipes in the same order as k_p2m. The result is stored in FP64; its
 // relative error is of order 1e-13 instead of 1e-16, far below what the
 // FP32 translations downstream add.
+// Shared memory per warp: the tile of one chunk's harmonics, 2(p+1) rows of
+// 33 (one per body, padded), and the sums, p+1 columns of 2(p+1) entries.
+__host__ __device__ inline int p2m_dw_warp_values(int p) { return 2 * (p + 1) * 33 + (p + 1) * 2 * (p + 1); }
+
 template <int PM, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
                                                  const double* __restrict__ xs,
@@ -203,12 +207,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
                                                  const double* __restrict__ zc,
                                                  const double* __restrict__ hs,
                                                  double* __restrict__ mult) {
-    __shared__ dw sh_tile[WARPS][2 * (PM + 1)][33];
-    // lane-private sums: entry e of column m at sh_acc[warp][m][e] (e = lane, lane + 32)
-    __shared__ dw sh_acc[WARPS][PM + 1][64];
+    extern __shared__ __align__(16) unsigned char sh_p2m_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    dw (*tile)[33] = sh_tile[wib];
-    dw (*acc)[64] = sh_acc[wib];
+    const int np1 = p + 1, ne = 2 * (p + 1);
+    dw* tile_base = reinterpret_cast<dw*>(sh_p2m_raw) + (size_t)wib * p2m_dw_warp_values(p);
+    dw* acc_base = tile_base + ne * 33;
+    // tile[row][body], acc[column m][entry]
+    auto tile = [&](int r) { return tile_base + r * 33; };
+    auto acc = [&](int m) { return acc_base + m * ne; };
+    (void)np1;
     const int nr = ncoef_real(p);
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     const dw zero = dw_make(0.f, 0.f);
@@ -216,7 +223,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
         if (t.nchild[k] != 0) continue;
         const double is = 1.0 / hs[k];
         const double cx = zc[3 * k], cy = zc[3 * k + 1], cz = zc[3 * k + 2];
-        for (int m = 0; m <= p; ++m) { acc[m][lane] = zero; acc[m][lane + 32] = zero; }
+        for (int e = lane; e < np1 * ne; e += 32) acc_base[e] = zero;
         for (int i0 = t.begin[k]; i0 < t.end[k]; i0 += 32) {
             const int i = i0 + lane;
             const bool act = i < t.end[k];
@@ -234,8 +241,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
                     dre = dw_mul(tq, c_dw_d[m]);
                 }
                 dw s1r = dre, s1i = dim, s2r = zero, s2i = zero;
-                tile[0][lane] = dre;
-                tile[1][lane] = dim;
+                tile(0)[lane] = dre;
+                tile(1)[lane] = dim;
                 for (int n = m + 1; n <= p; ++n) {
                     dw vr, vi;
                     if (n == m + 1) {
@@ -247,15 +254,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
                         vr = dw_sub(dw_mul(a, s1r), dw_mul(b, s2r));
                         vi = dw_sub(dw_mul(a, s1i), dw_mul(b, s2i));
                     }
-                    tile[2 * (n - m)][lane] = vr;
-                    tile[2 * (n - m) + 1][lane] = vi;
+                    tile(2 * (n - m))[lane] = vr;
+                    tile(2 * (n - m) + 1)[lane] = vi;
                     s2r = s1r; s2i = s1i; s1r = vr; s1i = vi;
                 }
                 __syncwarp();
                 for (int ent = lane; ent < 2 * (p - m + 1); ent += 32) {
-                    dw sacc = acc[m][ent];
-                    for (int l = 0; l < nact; ++l) sacc = dw_add(sacc, tile[ent][l]);
-                    acc[m][ent] = sacc;
+                    dw sacc = acc(m)[ent];
+                    for (int l = 0; l < nact; ++l) sacc = dw_add(sacc, tile(ent)[l]);
+                    acc(m)[ent] = sacc;
                 }
                 __syncwarp();
             }
@@ -264,11 +271,27 @@ __global__ void __launch_bounds__(WARPS * 32) k_p2m_dw(TreeView t, int p,
         for (int m = 0; m <= p; ++m)
             for (int ent = lane; ent < 2 * (p - m + 1); ent += 32) {
                 const int n = m + (ent >> 1);
-                if (ent & 1) { if (m) out[him(n, m)] = dw_to(acc[m][ent]); }
-                else out[hre(n, m)] = dw_to(acc[m][ent]);
+                if (ent & 1) { if (m) out[him(n, m)] = dw_to(acc(m)[ent]); }
+                else out[hre(n, m)] = dw_to(acc(m)[ent]);
             }
         __syncwarp();
     }
+}
+
+// a grid of as many blocks as fit on the SMs (warps stride over the leaves)
+template <int PM, int WARPS>
+void launch_p2m_dw(const TreeView& t, int p, const double* xs, const double* ys, const double* zs, const double* w,
+                   const double* zc, const double* hs, double* mult, cudaStream_t st) {
+    const int sh = (int)(WARPS * p2m_dw_warp_values(p) * sizeof(dw));
+    ensure_dyn_smem((const void*)k_p2m_dw<PM, WARPS>, sh);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2m_dw<PM, WARPS>, WARPS * 32, sh) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    (k_p2m_dw<PM, WARPS><<<device_sm_count() * per_sm, WARPS * 32, sh, st>>>(t, p, xs, ys, zs, w, zc, hs, mult),
+     note_launch());
 }
 
 // P_n = s^n sqrt(sum_{m=-n}^{n} |Mhat_n^m|^2)  (Sec. 2.3)
@@ -462,9 +485,9 @@ void upward_pass(const TreeView& t, const int* h_level_start, int p, const doubl
                  float* r32, double* contrib, const DevTables& tbl, bool dword, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
     if (dword && p <= 16)
-        (k_p2m_dw<16, 4><<<device_sm_count() * 8, 128, 0, st>>>(t, p, xs, ys, zs, ms, zc, hs, mult), note_launch());
+        launch_p2m_dw<16, 4>(t, p, xs, ys, zs, ms, zc, hs, mult, st);
     else if (dword)
-        (k_p2m_dw<kMaxP, 2><<<device_sm_count() * 16, 64, 0, st>>>(t, p, xs, ys, zs, ms, zc, hs, mult), note_launch());
+        launch_p2m_dw<kMaxP, 2>(t, p, xs, ys, zs, ms, zc, hs, mult, st);
     else if (p <= 16)
         (k_p2m<16, 4><<<device_sm_count() * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, ms, zc, hs, mult), note_launch());
     else
@@ -480,9 +503,9 @@ void p2m_weights(const TreeView& t, int p, const double* xs, const double* ys, c
                  const double* zc, const double* hs, double* mult, const DevTables& tbl, bool dword, cudaStream_t st) {
     const TabF64 tb = tab64(tbl);
     if (dword && p <= 16)
-        (k_p2m_dw<16, 4><<<device_sm_count() * 8, 128, 0, st>>>(t, p, xs, ys, zs, w, zc, hs, mult), note_launch());
+        launch_p2m_dw<16, 4>(t, p, xs, ys, zs, w, zc, hs, mult, st);
     else if (dword)
-        (k_p2m_dw<kMaxP, 2><<<device_sm_count() * 16, 64, 0, st>>>(t, p, xs, ys, zs, w, zc, hs, mult), note_launch());
+        launch_p2m_dw<kMaxP, 2>(t, p, xs, ys, zs, w, zc, hs, mult, st);
     else if (p <= 16)
         (k_p2m<16, 4><<<device_sm_count() * 8, 128, 0, st>>>(t, p, tb, xs, ys, zs, w, zc, hs, mult), note_launch());
     else

@@ -197,10 +197,21 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 
 template <typename T>
 struct TileCfg;
+#ifndef GBFMM_P2P_CAP32
+#define GBFMM_P2P_CAP32 512
+#endif
+// blocks per SM the tile kernel's registers are cut for: 4 (128 registers, no
+// spill) measured 5.74 ms against 5.82 ms for 5 (96 registers, a small spill)
+#ifndef GBFMM_P2P_MINB
+#define GBFMM_P2P_MINB 4
+#endif
+#ifndef GBFMM_P2P_TG
+#define GBFMM_P2P_TG 8
+#endif
 template <>
 struct TileCfg<float> {
-    static constexpr int TG = 8;      // targets per group
-    static constexpr int kCap = 512;  // staged source bodies per warp (8 KB): at most 16 per lane
+    static constexpr int TG = GBFMM_P2P_TG;  // targets per group
+    static constexpr int kCap = GBFMM_P2P_CAP32;  // staged source bodies per warp (512: 8 KB, at most 16 per lane)
     static constexpr int kRun = 1 << 30;  // so a lane's run is at most 16 terms: no fold
 };
 template <>
@@ -406,7 +417,7 @@ __device__ __forceinline__ void p2p_groups(const Body4<T>* __restrict__ sm, int 
 }
 
 template <typename T, bool SOFT>
-__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 5) k_p2p_tiles(LeafArgs a, const int* __restrict__ item_leaf,
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : GBFMM_P2P_MINB) k_p2p_tiles(LeafArgs a, const int* __restrict__ item_leaf,
                                                     const uint32_t* __restrict__ item_first,
                                                     const uint32_t* __restrict__ slot_first,
                                                     const uint32_t* __restrict__ nitems_p, unsigned* __restrict__ work) {
@@ -660,6 +671,10 @@ __global__ void __launch_bounds__(128) k_p2p_lanes(LeafArgs a, const int* __rest
     }
 }
 
+#ifndef GBFMM_L2P_REGS
+#define GBFMM_L2P_REGS 0
+#endif
+
 // One thread per body: L2P of its leaf's local expansion plus the P2P
 // partials of its leaf's items in item order; G-scaled, to the caller's order.
 template <typename T, int PC>
@@ -678,8 +693,16 @@ __global__ void __launch_bounds__(128) k_leaf_reduce(LeafArgs a, const int* __re
         const float inv_s = 1.0f / bh.w;
         const float4 v = a.prel[i];
         float phi, fx, fy, fz;
-        l2p_hat<float, TabL32, PC>(a.p, reinterpret_cast<const float*>(a.loc) + (size_t)nr * B, v.x * inv_s,
-                                   v.y * inv_s, v.z * inv_s, inv_s, tb, phi, fx, fy, fz);
+        const float* Fg = reinterpret_cast<const float*>(a.loc) + (size_t)nr * B;
+        if (GBFMM_L2P_REGS && PC > 0) {
+            // the leaf's local coefficients into registers first: independent loads, all in flight
+            float Fr[PC > 0 ? (PC + 1) * (PC + 1) : 1];
+#pragma unroll
+            for (int j = 0; j < (PC + 1) * (PC + 1); ++j) Fr[j] = __ldg(Fg + j);
+            l2p_hat<float, TabL32, PC>(a.p, Fr, v.x * inv_s, v.y * inv_s, v.z * inv_s, inv_s, tb, phi, fx, fy, fz);
+        } else {
+            l2p_hat<float, TabL32, PC>(a.p, Fg, v.x * inv_s, v.y * inv_s, v.z * inv_s, inv_s, tb, phi, fx, fy, fz);
+        }
         sx = fx; sy = fy; sz = fz; sp = phi;
     } else {
         const TabL64 tb{a.tb.w, a.tb.iw, a.tb.rec_a, a.tb.rec_b, a.tb.diag, a.tb.sub};

@@ -357,65 +357,42 @@ __global__ void k_push_down(TreeView t, const float* __restrict__ farf, float* _
     g[k] = acc;
 }
 
-// near part per body: partner leaves ascending, their bodies in order, j != i.
-// One warp per leaf, lane t for its bodies t and t + 32 (the leaf size is at
-// most 64 here; larger leaves take more passes): every lane walks the same
-// partner bodies, so the loads are broadcasts and no lane diverges, and each
-// body's sum is the same sequence of FP32 additions as before.
-template <bool SOFT>
-__device__ __forceinline__ float near_term(float4 pi, float4 pj, float soft2f, bool& use) {
-    const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    use = r2 > 0.0f;
-    if (SOFT) {
-        // softened magnitude m r / (r^2 + soft^2)^{3/2}
-        const float s2 = r2 + soft2f;
-        return pj.w * sqrtf(r2) / (s2 * sqrtf(s2));
-    }
-    return pj.w / r2;
-}
-
-template <bool SOFT>
+// near part per body: partner leaves ascending, their bodies in order, j != i
+// (one thread per body; a warp's bodies share their leaf's partners, so most
+// loads are broadcasts)
 __global__ void k_near_f(TreeView t, const float4* __restrict__ xf, const uint32_t* __restrict__ src,
-                         const uint32_t* __restrict__ off, const float* __restrict__ g, float soft2f,
-                         float* __restrict__ f) {
-    const int b = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= *t.dnn || t.nchild[b] != 0) return;
-    const int b0 = t.begin[b], nB = t.end[b] - b0;
-    const uint32_t q0 = off[b], q1 = off[b + 1];
-    for (int t0 = 0; t0 < nB; t0 += 64) {
-        const int i0 = b0 + t0 + lane, i1 = i0 + 32;
-        const bool act0 = t0 + lane < nB, act1 = t0 + lane + 32 < nB;
-        const float4 p0 = xf[act0 ? i0 : b0], p1 = xf[act1 ? i1 : b0];
-        float acc0 = 0.0f, acc1 = 0.0f;
-        if (nB - t0 > 32) {  // two bodies per lane
-            for (uint32_t q = q0; q < q1; ++q) {
-                const int a = (int)src[q];
-                const int j0 = t.begin[a], j1 = t.end[a];
-                for (int j = j0; j < j1; ++j) {
-                    const float4 pj = xf[j];
-                    bool u0, u1;
-                    const float v0 = near_term<SOFT>(p0, pj, soft2f, u0);
-                    const float v1 = near_term<SOFT>(p1, pj, soft2f, u1);
-                    if (u0 && j != i0) acc0 = acc0 + v0;
-                    if (u1 && j != i1) acc1 = acc1 + v1;
-                }
-            }
-        } else {
-            for (uint32_t q = q0; q < q1; ++q) {
-                const int a = (int)src[q];
-                const int j0 = t.begin[a], j1 = t.end[a];
-                for (int j = j0; j < j1; ++j) {
-                    bool u0;
-                    const float v0 = near_term<SOFT>(p0, xf[j], soft2f, u0);
-                    if (u0 && j != i0) acc0 = acc0 + v0;
-                }
+                         const uint32_t* __restrict__ off, const int* __restrict__ leaf_of,
+                         const float* __restrict__ g, float soft2f, float* __restrict__ f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= t.n) return;
+    const int b = leaf_of[i];
+    const float4 pi = xf[i];
+    float acc = 0.0f;
+    for (uint32_t q = off[b]; q < off[b + 1]; ++q) {
+        const int a = (int)src[q];
+        const int j0 = t.begin[a], j1 = t.end[a];
+        for (int j = j0; j < j1; ++j) {
+            if (j == i) continue;
+            const float4 pj = xf[j];
+            const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 > 0.0f)) continue;
+            if (soft2f > 0.0f) {
+                // softened magnitude m r / (r^2 + soft^2)^{3/2}
+                const float s2 = r2 + soft2f;
+                acc = acc + pj.w * sqrtf(r2) / (s2 * sqrtf(s2));
+            } else {
+                acc = acc + pj.w / r2;
             }
         }
-        if (act0) f[i0] = g[b] + acc0;
-        if (act1) f[i1] = g[b] + acc1;
     }
+    f[i] = g[b] + acc;
+}
+
+__global__ void k_leaf_of(TreeView t, int* __restrict__ leaf_of) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= *t.dnn || t.nchild[k] != 0) return;
+    for (int i = t.begin[k]; i < t.end[k]; ++i) leaf_of[i] = k;
 }
 
 // fmin of a leaf over its bodies; of an internal cell over its children
@@ -542,19 +519,16 @@ void scalar_force(const TreeView& t, const double* zc, const double* M, const fl
                   const uint32_t* far_src, const uint32_t* far_off, const uint32_t* near_src,
                   const uint32_t* near_off, const int* h_level_start, double soft, float* farf,
                   float* f, float* fmin, cudaStream_t st) {
-    // farf doubles as scratch: [0, nnodes) far sums, [nnodes, 2 nnodes) pushed-down g
+    // farf doubles as scratch: [0, nnodes) far sums, [nnodes, 2 nnodes) pushed-down g,
+    // and the leaf index of every body after that.
     float* g = farf + t.nnodes;
+    int* leaf_of = reinterpret_cast<int*>(farf + 2 * (size_t)t.nnodes);
     (k_far_f<<<blocks_for(32 * (int64_t)t.nnodes, 128), 128, 0, st>>>(t.dnn, zc, M, far_src, far_off, farf),
      note_launch());
     (k_push_down<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, farf, g), note_launch());
-    if ((float)(soft * soft) > 0.0f)
-        (k_near_f<true><<<blocks_for(32 * (int64_t)t.nnodes, 128), 128, 0, st>>>(t, xf, near_src, near_off, g,
-                                                                                 (float)(soft * soft), f),
-         note_launch());
-    else
-        (k_near_f<false><<<blocks_for(32 * (int64_t)t.nnodes, 128), 128, 0, st>>>(t, xf, near_src, near_off, g,
-                                                                                  0.0f, f),
-         note_launch());
+    (k_leaf_of<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, leaf_of), note_launch());
+    (k_near_f<<<blocks_for(t.n, 128), 128, 0, st>>>(t, xf, near_src, near_off, leaf_of, g, (float)(soft * soft), f),
+     note_launch());
     (k_fmin_leaves<<<blocks_for(t.nnodes, 128), 128, 0, st>>>(t, f, fmin), note_launch());
     (void)h_level_start;
     for (int L = t.nlevels - 2; L >= 0; --L)
