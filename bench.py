@@ -328,6 +328,8 @@ def main():
                     help="skip the config-3 orders, the ensemble and the FMA peaks (profiling runs)")
     ap.add_argument("--err-sample", type=int, default=0,
                     help="bodies in the force-error check (0: all bodies)")
+    ap.add_argument("--p2p-loads", action="store_true",
+                    help="stage the P2P sources by per-lane loads (FMM_FLAG_P2P_LOADS) instead of bulk copies")
     ap.add_argument("--cpu-table", action="store_true",
                     help="only time the oracle at configs 1-3 on this host and print one JSON line")
     args = ap.parse_args()
@@ -383,7 +385,7 @@ def main():
         barrier()
         return times, stats
 
-    mixed = gb.FMM(p=args.p, eps=args.eps, leaf_size=LEAF, precision="mixed")
+    mixed = gb.FMM(p=args.p, eps=args.eps, leaf_size=LEAF, precision="mixed", p2p_bulk=not args.p2p_loads)
     with ClockSampler(local) as clk:
         wall0 = time.perf_counter()
         times, stats = timed_solves(mixed, args.steps, args.warmup)

@@ -48,8 +48,8 @@ typedef enum {
     FMM_ERR_NONFINITE = -4,  /* a position or mass is NaN or infinite, or a mass is <= 0 */
     FMM_ERR_COINCIDENT = -5, /* two bodies share exactly the same position */
     FMM_ERR_CAPACITY = -6,   /* an internal list outgrew its capacity after one regrow */
-    FMM_ERR_TIMEOUT = -7     /* a bounded device-side wait ran out (reserved: no call of this
-                                version spins on the device, so none returns it) */
+    FMM_ERR_TIMEOUT = -7     /* a bounded device-side wait ran out (the P2P's bulk-copy
+                                staging); the context stays usable */
 } fmm_status;
 
 typedef enum {
@@ -62,7 +62,12 @@ typedef enum {
 /* fmm_config.flags bits */
 #define FMM_FLAG_FP64_LOCALS 1u /* mixed precision only: M2L, L2L and L2P run in FP64 on FP64
                                    multipole and local coefficients, P2P stays FP32 (the split
-                                   "FP64 coefficients for the high orders"); slower, see DESIGN */
+                                   "FP64 coefficients for the high orders"); slower */
+#define FMM_FLAG_P2P_LOADS 2u   /* FP32 P2P: stage the source bodies into shared memory by per-lane
+                                   loads instead of the default, one bulk copy (cp.async.bulk) per
+                                   source leaf completing on an mbarrier. Same results. The bulk
+                                   copies' waits are bounded (about one second); one that runs out
+                                   makes the call return FMM_ERR_TIMEOUT. */
 
 typedef struct {
     int p;                 /* expansion order, 1..30 (swap matrices are tabulated to 30, Sec. 2.4) */
@@ -72,7 +77,9 @@ typedef struct {
     double G;              /* gravitational constant (Henon units: 1) */
     unsigned flags;        /* FMM_FLAG_* bits (0: none); unknown bits are rejected */
     unsigned fault_inject; /* test hook, 0 in production: bit 0 forces tiny list capacities
-                              so the capacity-regrow path runs */
+                              so the capacity-regrow path runs; bit 1 makes every bulk-copy wait
+                              of the FP32 P2P expect 16 bytes that never come, so it runs out
+                              and the call returns FMM_ERR_TIMEOUT */
     double soft;           /* Plummer softening length eps_soft >= 0 (Appendix B; 0: Newtonian).
                               P2P, fmm_direct and the near part of the scalar-force estimate
                               use the softened kernel; the far field stays the expansion of

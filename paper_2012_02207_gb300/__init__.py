@@ -22,6 +22,7 @@ _lib = None
 FMM_PRECISION_FP64 = 0
 FMM_PRECISION_MIXED = 1
 FMM_FLAG_FP64_LOCALS = 1
+FMM_FLAG_P2P_LOADS = 2
 
 STATUS = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_CUDA", -3: "FMM_ERR_OOM", -4: "FMM_ERR_NONFINITE",
           -5: "FMM_ERR_COINCIDENT", -6: "FMM_ERR_CAPACITY", -7: "FMM_ERR_TIMEOUT"}
@@ -123,12 +124,14 @@ class FMM:
     """One solver context (fmm_create/fmm_destroy) on the current CUDA device."""
 
     def __init__(self, p=8, eps=1e-7, leaf_size=64, precision="mixed", G=1.0, fault_inject=0, soft=0.0,
-                 fp64_locals=False):
+                 fp64_locals=False, p2p_bulk=True):
         """fp64_locals: in mixed precision, run M2L, L2L and L2P in FP64 on FP64
-        coefficients (FMM_FLAG_FP64_LOCALS); P2P stays FP32."""
+        coefficients (FMM_FLAG_FP64_LOCALS); P2P stays FP32. p2p_bulk: stage the
+        FP32 P2P sources by bulk copies (the default; False sets
+        FMM_FLAG_P2P_LOADS, per-lane loads)."""
         if isinstance(precision, str):
             precision = {"fp64": FMM_PRECISION_FP64, "mixed": FMM_PRECISION_MIXED}[precision]
-        flags = FMM_FLAG_FP64_LOCALS if fp64_locals else 0
+        flags = (FMM_FLAG_FP64_LOCALS if fp64_locals else 0) | (0 if p2p_bulk else FMM_FLAG_P2P_LOADS)
         self.config = Config(p, eps, leaf_size, precision, G, fault_inject, soft, flags)
         cfg = _Config(p, eps, leaf_size, precision, G, flags, fault_inject, soft)
         h = ctypes.c_void_p()

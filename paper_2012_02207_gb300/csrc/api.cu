@@ -617,6 +617,9 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     la.part_hi = as<double2>(ctx->part_hi); la.part_lo = as<double2>(ctx->part_lo);
     la.tb = ctx->tb;
     la.interactions = as<unsigned long long>(ctx->dcount) + 1;
+    la.err = &ctx->ds->err;
+    la.bulk = (ctx->cfg.flags & FMM_FLAG_P2P_LOADS) == 0;
+    la.tx_extra = (ctx->cfg.fault_inject & 2u) ? 16u : 0u;
     la.slots_cap = htot[1];
     if (mixed) {
         leaf_relative_f32(t, la.xs, la.ys, la.zs, la.ms, la.zc, as<float4>(ctx->prel), st);
@@ -631,6 +634,7 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     CK(cudaStreamSynchronize(st));
     CK(cudaMemcpy(&err, &ctx->ds->err, 4, cudaMemcpyDeviceToHost));
     if (err & kErrCapacity) return fail(ctx, FMM_ERR_CAPACITY, "an internal list overflowed");
+    if (err & kErrTimeout) return fail(ctx, FMM_ERR_TIMEOUT, "a bounded wait of the P2P staging ran out");
     unsigned long long inter = 0;
     CK(cudaMemcpy(&inter, as<unsigned long long>(ctx->dcount) + 1, 8, cudaMemcpyDeviceToHost));
     ctx->stats.p2p_interactions = (int64_t)inter;
@@ -703,6 +707,7 @@ int jerk_pass(fmm_ctx* ctx, const double* vx, const double* vy, const double* vz
     if (mixed) downward_pass_f32(t, ctx->h_level_start, p, zc, hs, as<double>(ctx->geo), as<float>(ctx->jloc32), ctx->tb, st);
     else downward_pass_f64(t, ctx->h_level_start, p, zc, hs, as<double>(ctx->geo), as<double>(ctx->jloc), ctx->tb, st);
     LeafArgs la{};
+    la.err = &ctx->ds->err;
     la.t = t; la.p = p; la.G = ctx->cfg.G;
     la.soft2 = ctx->cfg.soft * ctx->cfg.soft;
     la.soft2f = (float)la.soft2;
@@ -847,7 +852,7 @@ int check_cfg(const fmm_config* c, std::string& why) {
     if (c->precision == FMM_PRECISION_MIXED && c->p > kMaxPF32) { why = "mixed precision supports p <= 16"; return FMM_ERR_ARG; }
     if (!std::isfinite(c->G)) { why = "G must be finite"; return FMM_ERR_ARG; }
     if (!(c->soft >= 0.0) || !std::isfinite(c->soft)) { why = "soft must be finite and >= 0"; return FMM_ERR_ARG; }
-    if (c->flags & ~FMM_FLAG_FP64_LOCALS) { why = "unknown flag bits"; return FMM_ERR_ARG; }
+    if (c->flags & ~(FMM_FLAG_FP64_LOCALS | FMM_FLAG_P2P_LOADS)) { why = "unknown flag bits"; return FMM_ERR_ARG; }
     if ((c->flags & FMM_FLAG_FP64_LOCALS) && c->precision != FMM_PRECISION_MIXED) {
         why = "FMM_FLAG_FP64_LOCALS applies to mixed precision only";
         return FMM_ERR_ARG;

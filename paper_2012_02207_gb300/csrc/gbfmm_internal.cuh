@@ -313,6 +313,9 @@ struct LeafArgs {
     DevTables tb;
     double soft2;  // squared Plummer softening length (0: Newtonian P2P)
     float soft2f;  // the same, rounded to FP32 (mixed P2P)
+    unsigned* err;      // kErr* bits (a bounded wait that ran out: kErrTimeout)
+    bool bulk;          // FP32 P2P: stage source leaves by bulk copies (unless FMM_FLAG_P2P_LOADS)
+    uint32_t tx_extra;  // test hook: bytes a bulk-copy wait expects beyond those copied (0)
 };
 void leaf_items_plan(const TreeView& t, const uint32_t* p2p_off, uint32_t* item_first, uint32_t* slot_first,
                      uint32_t* totals, cudaStream_t st);

@@ -222,10 +222,64 @@ struct TileCfg<double> {
 };
 constexpr int kTargetChunk = 64;  // targets whose totals a warp keeps in shared memory per pass
 
-// per warp: staged sources, the target chunk's positions, its FP64 totals
+// per warp: staged sources, the target chunk's positions, its FP64 totals, an mbarrier
 template <typename T>
 constexpr size_t p2p_tile_smem_per_warp() {
-    return sizeof(Body4<T>) * TileCfg<T>::kCap + sizeof(Body4<T>) * kTargetChunk + sizeof(double) * 4 * kTargetChunk;
+    return sizeof(Body4<T>) * TileCfg<T>::kCap + sizeof(Body4<T>) * kTargetChunk + sizeof(double) * 4 * kTargetChunk +
+           4 * sizeof(Body4<T>);
+}
+
+// Bulk-copy staging (BULK, FP32; the default, FMM_FLAG_P2P_LOADS turns it off):
+// the bodies of every staged
+// source leaf come into shared memory by one cp.async.bulk (the tensor memory
+// accelerator's 1-D copy, 16-byte aligned, a multiple of 16 bytes) that
+// completes on the warp's mbarrier; the leaf-centre offsets are then added in
+// shared memory. Waits are bounded: after kBulkWaitNs the warp raises
+// kErrTimeout and leaves the kernel (every issued copy has completed by then
+// unless the copy engine itself stalled).
+constexpr unsigned long long kBulkWaitNs = 1000000000ull;  // one second
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// generic-proxy accesses of shared memory before this are ordered before later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// wait (all lanes) for the phase of the warp's mbarrier; false: the wait ran out
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+    const unsigned long long t0 = global_ns();
+    bool done = mbar_test(bar, phase);
+    while (!done) {
+        if (global_ns() - t0 > kBulkWaitNs) break;
+        done = mbar_test(bar, phase);
+    }
+    return __all_sync(0xffffffffu, done) != 0;
 }
 
 // Stage whole source leaves src[q], src[q+1], ... (below q1) of target leaf
@@ -236,10 +290,10 @@ constexpr size_t p2p_tile_smem_per_warp() {
 // once per 32 leaves rather than once per leaf. A leaf larger than kCap (a
 // level-21 leaf can exceed the leaf size) goes in pieces of kCap bodies, soff
 // being the next body of it.
-template <typename T, int kCap>
+template <typename T, int kCap, bool BULK>
 __device__ __forceinline__ int stage_leaves(const LeafArgs& a, int B, float4 bh, float4 bl, uint32_t& q,
                                             uint32_t q1, int& soff, Body4<T>* __restrict__ sm, bool& selfin,
-                                            int lane) {
+                                            int lane, uint64_t* bar, uint32_t& phase, bool& timed_out) {
     int cnt = 0;
     selfin = false;
     {
@@ -301,6 +355,39 @@ __device__ __forceinline__ int stage_leaves(const LeafArgs& a, int B, float4 bh,
         // and this loop stops before such a leaf once anything is staged)
         const int fit = __popc(fits);  // a prefix of the leaves, since incl grows
         selfin |= __any_sync(0xffffffffu, lane < fit && A == B) != 0;
+        if (BULK && sizeof(T) == 4 && fit > 0) {
+            // one bulk copy per leaf (lane j for leaf j), then the offsets in shared memory
+            const uint32_t bytes = (uint32_t)__shfl_sync(0xffffffffu, incl, fit - 1) * (uint32_t)sizeof(Body4<T>);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_expect(bar, bytes + a.tx_extra);
+            __syncwarp();
+            if (lane < fit)
+                bulk_to_smem(sm + cnt + incl - nA, a.prel + a0, (uint32_t)nA * (uint32_t)sizeof(Body4<T>), bar);
+            const bool ok = mbar_wait_bounded(bar, phase);
+            phase ^= 1u;
+            if (!ok) {
+                timed_out = true;
+                return cnt;
+            }
+#pragma unroll 4
+            for (int j = 0; j < fit; ++j) {
+                const int nj = __shfl_sync(0xffffffffu, nA, j);
+                const int dst = cnt + __shfl_sync(0xffffffffu, incl, j) - nj;
+                const float oxj = __shfl_sync(0xffffffffu, ox, j), oyj = __shfl_sync(0xffffffffu, oy, j),
+                            ozj = __shfl_sync(0xffffffffu, oz, j);
+                for (int l = lane; l < nj; l += 32) {
+                    Body4<T>& v = sm[dst + l];
+                    v.x = (T)(v.x + oxj);
+                    v.y = (T)(v.y + oyj);
+                    v.z = (T)(v.z + ozj);
+                }
+            }
+            cnt += __shfl_sync(0xffffffffu, incl, fit - 1);
+            q += (uint32_t)fit;
+            if (fit < nl) break;
+            continue;
+        }
 #pragma unroll 4
         for (int j = 0; j < fit; ++j) {
             const int aj = __shfl_sync(0xffffffffu, a0, j), nj = __shfl_sync(0xffffffffu, nA, j);
@@ -416,7 +503,7 @@ __device__ __forceinline__ void p2p_groups(const Body4<T>* __restrict__ sm, int 
     if (t0 < nt) p2p_group<T, TG / 2, GUARD, SOFT>(sm, cnt, tg, t0, nt, s2, tot, lane);
 }
 
-template <typename T, bool SOFT>
+template <typename T, bool SOFT, bool BULK>
 __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : GBFMM_P2P_MINB) k_p2p_tiles(LeafArgs a, const int* __restrict__ item_leaf,
                                                     const uint32_t* __restrict__ item_first,
                                                     const uint32_t* __restrict__ slot_first,
@@ -428,6 +515,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : GBFMM_P2P_MINB) k_p2
     Body4<T>* sm = reinterpret_cast<Body4<T>*>(wbase);
     Body4<T>* tg = sm + kCap;
     double* tot = reinterpret_cast<double*>(tg + kTargetChunk);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tot + 4 * kTargetChunk);  // the warp's mbarrier (bulk staging)
+    uint32_t phase = 0;
+    bool timed_out = false;
+    if (BULK && sizeof(T) == 4) {
+        if (lane == 0) mbar_init(bar);
+        __syncwarp();
+    }
     const int nitems = (int)*nitems_p;
     const T s2 = SOFT ? (sizeof(T) == 4 ? (T)a.soft2f : (T)a.soft2) : T(0);
     for (;;) {
@@ -463,7 +557,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : GBFMM_P2P_MINB) k_p2
             while (q < q1) {
                 __syncwarp();
                 bool selfin = false;
-                const int cnt = stage_leaves<T, kCap>(a, B, bh, bl, q, q1, soff, sm, selfin, lane);
+                const int cnt = stage_leaves<T, kCap, BULK>(a, B, bh, bl, q, q1, soff, sm, selfin, lane, bar, phase,
+                                                            timed_out);
+                if (timed_out) {
+                    if (lane == 0) atomicOr(a.err, kErrTimeout);
+                    return;
+                }
                 __syncwarp();
                 if (tc == 0) { nsrc += (unsigned long long)cnt; self_item |= selfin; }
                 if (selfin) p2p_groups<T, true, SOFT>(sm, cnt, tg, nt, s2, tot, lane);
@@ -671,10 +770,6 @@ __global__ void __launch_bounds__(128) k_p2p_lanes(LeafArgs a, const int* __rest
     }
 }
 
-#ifndef GBFMM_L2P_REGS
-#define GBFMM_L2P_REGS 0
-#endif
-
 // One thread per body: L2P of its leaf's local expansion plus the P2P
 // partials of its leaf's items in item order; G-scaled, to the caller's order.
 template <typename T, int PC>
@@ -693,16 +788,8 @@ __global__ void __launch_bounds__(128) k_leaf_reduce(LeafArgs a, const int* __re
         const float inv_s = 1.0f / bh.w;
         const float4 v = a.prel[i];
         float phi, fx, fy, fz;
-        const float* Fg = reinterpret_cast<const float*>(a.loc) + (size_t)nr * B;
-        if (GBFMM_L2P_REGS && PC > 0) {
-            // the leaf's local coefficients into registers first: independent loads, all in flight
-            float Fr[PC > 0 ? (PC + 1) * (PC + 1) : 1];
-#pragma unroll
-            for (int j = 0; j < (PC + 1) * (PC + 1); ++j) Fr[j] = __ldg(Fg + j);
-            l2p_hat<float, TabL32, PC>(a.p, Fr, v.x * inv_s, v.y * inv_s, v.z * inv_s, inv_s, tb, phi, fx, fy, fz);
-        } else {
-            l2p_hat<float, TabL32, PC>(a.p, Fg, v.x * inv_s, v.y * inv_s, v.z * inv_s, inv_s, tb, phi, fx, fy, fz);
-        }
+        l2p_hat<float, TabL32, PC>(a.p, reinterpret_cast<const float*>(a.loc) + (size_t)nr * B, v.x * inv_s,
+                                   v.y * inv_s, v.z * inv_s, inv_s, tb, phi, fx, fy, fz);
         sx = fx; sy = fy; sz = fz; sp = phi;
     } else {
         const TabL64 tb{a.tb.w, a.tb.iw, a.tb.rec_a, a.tb.rec_b, a.tb.diag, a.tb.sub};
@@ -715,7 +802,22 @@ __global__ void __launch_bounds__(128) k_leaf_reduce(LeafArgs a, const int* __re
     }
     const uint32_t i0 = item_first[B], i1 = item_first[B + 1];
     const uint32_t s0 = slot_first[B] + (uint32_t)(i - b0);
-    for (uint32_t it = i0; it < i1; ++it) {
+    // the body's item partials in item order; four items' loads are issued
+    // before they are added, so their latencies overlap
+    uint32_t it = i0;
+    for (; it + 4 <= i1; it += 4) {
+        double2 u[4], w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t slot = s0 + (it + k - i0) * (uint32_t)nB;
+            if (slot >= a.slots_cap) slot = 0;  // only after a capacity error (the result is discarded)
+            u[k] = a.part_hi[slot];
+            w[k] = a.part_lo[slot];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { sx += u[k].x; sy += u[k].y; sz += w[k].x; sp -= w[k].y; }
+    }
+    for (; it < i1; ++it) {
         const uint32_t slot = s0 + (it - i0) * (uint32_t)nB;
         if (slot >= a.slots_cap) break;  // only after a capacity error (the result is discarded)
         const double2 u = a.part_hi[slot], w = a.part_lo[slot];
@@ -1170,6 +1272,22 @@ void leaf_items_fill(const TreeView& t, const uint32_t* item_first, int* item_le
 
 namespace {
 // persistent grid: as many blocks as fit on every SM (warps take items from a counter)
+template <typename T, bool SOFT, bool BULK>
+void launch_tiles(const LeafArgs& a, const int* item_leaf, const uint32_t* item_first, const uint32_t* slot_first,
+                  const uint32_t* nitems, unsigned* work, cudaStream_t st) {
+    const int sh = (int)(4 * p2p_tile_smem_per_warp<T>());
+    ensure_dyn_smem((const void*)k_p2p_tiles<T, SOFT, BULK>, sh);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p_tiles<T, SOFT, BULK>, 128, sh) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    (k_p2p_tiles<T, SOFT, BULK><<<device_sm_count() * per_sm, 128, sh, st>>>(a, item_leaf, item_first, slot_first,
+                                                                             nitems, work),
+     note_launch());
+}
+
 template <typename T, bool SOFT>
 void launch_p2p_tiles(const LeafArgs& a, const int* item_leaf, const uint32_t* item_first, const uint32_t* slot_first,
                       const uint32_t* nitems, unsigned* work, cudaStream_t st) {
@@ -1179,17 +1297,8 @@ void launch_p2p_tiles(const LeafArgs& a, const int* item_leaf, const uint32_t* i
          note_launch());
         return;
     }
-    const int sh = (int)(4 * p2p_tile_smem_per_warp<T>());
-    ensure_dyn_smem((const void*)k_p2p_tiles<T, SOFT>, sh);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p_tiles<T, SOFT>, 128, sh) != cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    (k_p2p_tiles<T, SOFT><<<device_sm_count() * per_sm, 128, sh, st>>>(a, item_leaf, item_first, slot_first, nitems,
-                                                                       work),
-     note_launch());
+    if (sizeof(T) == 4 && a.bulk) launch_tiles<T, SOFT, true>(a, item_leaf, item_first, slot_first, nitems, work, st);
+    else launch_tiles<T, SOFT, false>(a, item_leaf, item_first, slot_first, nitems, work, st);
 }
 }  // namespace
 

@@ -153,6 +153,32 @@ def test_deterministic_and_capacity_regrow(prec):
     assert np.array_equal(a1, a3) and np.array_equal(p1, p3)
 
 
+@pytest.mark.parametrize("soft", [0.0, 1e-3])
+def test_bulk_copy_staging_gives_the_same_forces(soft):
+    """The FP32 P2P stages its sources by cp.async.bulk and adds the leaf
+    offsets in shared memory; FMM_FLAG_P2P_LOADS stages them by per-lane loads
+    with the offsets added on the way. The same FP32 sums either way."""
+    pos, _, _ = ics.plummer(30000, 41)
+    m = ics.kroupa_masses(30000, 42)
+    _, a0, p0 = solve(pos, m, p=10, eps=1e-7, precision="mixed", soft=soft, p2p_bulk=False)
+    _, a1, p1 = solve(pos, m, p=10, eps=1e-7, precision="mixed", soft=soft, p2p_bulk=True)
+    assert np.array_equal(a0, a1) and np.array_equal(p0, p1)
+
+
+def test_bulk_copy_wait_that_runs_out_reports_a_timeout():
+    """Every bulk-copy wait is bounded. The test hook makes each wait expect
+    16 bytes that no copy delivers, so the waits run out (after about a
+    second), the call returns FMM_ERR_TIMEOUT and the device stays usable."""
+    pos, _, m = ics.plummer(5000, 43)
+    f = gb.FMM(p=8, eps=1e-7, precision="mixed", p2p_bulk=True, fault_inject=2)
+    with pytest.raises(gb.FmmError) as e:
+        f.solve(*to_dev(pos, m))
+    assert e.value.status == -7
+    _, acc, _ = solve(pos, m, p=8, eps=1e-7, precision="mixed", p2p_bulk=True)
+    _, ref, _ = solve(pos, m, p=8, eps=1e-7, precision="mixed", p2p_bulk=False)
+    assert np.array_equal(acc, ref)
+
+
 def test_host_entry_point_matches_device():
     pos, _, m = ics.plummer(5000, 17)
     f, acc, pot = solve(pos, m, p=8, eps=1e-7)

@@ -37,7 +37,7 @@ def test_create_rejects_bad_config_without_a_gpu():
     h = ctypes.c_void_p()
     for bad in (dict(p=0), dict(p=31), dict(eps=-1.0), dict(leaf_size=0), dict(precision=7),
                 dict(p=20, precision=1), dict(soft=-1e-3), dict(soft=float("inf")), dict(soft=float("nan")),
-                dict(flags=2), dict(flags=1, precision=0)):
+                dict(flags=4), dict(flags=1, precision=0)):
         cfg = dict(p=8, eps=1e-7, leaf_size=64, precision=1, G=1.0, flags=0, fault_inject=0, soft=0.0)
         cfg.update(bad)
         c = gb._Config(**cfg)
