@@ -464,17 +464,20 @@ def main():
             "phases_ms": {k: sl[-1][k] for k in ("ms_m2l", "ms_downward", "ms_leaf", "ms_total")}}
         del f64l
         # config 4: the 256-cluster ensemble as one forest at the autotuner's pick
-        from paper_2012_02207_gb300.ensemble import Ensemble  # noqa: PLC0415
+        from paper_2012_02207_gb300.ensemble import Ensemble, pick_staging  # noqa: PLC0415
         import ics  # noqa: PLC0415
         offsets, epos, emass, _, _ = ics.ensemble(256, 4)
         ens = Ensemble(offsets, epos, emass, sample=512)
-        fe = gb.FMM(p=ENSEMBLE_PICK["p"], eps=ENSEMBLE_PICK["eps"], leaf_size=ENSEMBLE_PICK["leaf"], precision="mixed")
+        pick, staging_ms = pick_staging(ens, ENSEMBLE_PICK, log=lambda s: None)
+        bulk = pick["p2p_staging"] == "bulk"
+        fe = gb.FMM(p=pick["p"], eps=pick["eps"], leaf_size=pick["leaf"], precision="mixed", p2p_bulk=bulk)
         eout, ems = ens.time_batch(fe, steps=5)
         erms = ens.errors(eout)
-        ge = gb.FMM(p=ENSEMBLE_PICK["p"], eps=ENSEMBLE_PICK["eps"], leaf_size=ENSEMBLE_PICK["leaf"], precision="mixed")
+        ge = gb.FMM(p=pick["p"], eps=pick["eps"], leaf_size=pick["leaf"], precision="mixed", p2p_bulk=bulk)
         _, ems_graph, replayed = ens.time_graph(ge)
         extras["config4_ensemble"] = {
-            "clusters": 256, "n_bodies": ens.n, **ENSEMBLE_PICK, "forest_ms": ems,
+            "clusters": 256, "n_bodies": ens.n, **ENSEMBLE_PICK, "p2p_staging": pick["p2p_staging"],
+            "staging_ms": staging_ms, "forest_ms": ems,
             "forest_particles_per_s": ens.n / (ems * 1e-3), "graph_replay_ms_host": ems_graph,
             "graph_replayed": replayed, "kernel_launches": fe.stats()["kernel_launches"],
             "worst_cluster_rms": float(erms.max()), "median_cluster_rms": float(np.median(erms)),

@@ -355,12 +355,16 @@ __global__ void k_geometry_leaves(TreeView t, const double* __restrict__ xs,
         Sz = Sz + mi * zs[i];
     }
     const double zx = Sx / Mk, zy = Sy / Mk, zz = Sz / Mk;
-    double rr = 0.0;
+    // the largest distance: a correctly rounded square root is monotonic, so
+    // the root of the largest squared distance equals the largest root (one
+    // FP64 square root per leaf instead of one per body)
+    double rr2 = 0.0;
     for (int i = b; i < e; ++i) {
         const double dx = xs[i] - zx, dy = ys[i] - zy, dz = zs[i] - zz;
-        const double d = sqrt(dx * dx + dy * dy + dz * dz);
-        if (d > rr) rr = d;
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 > rr2) rr2 = d2;
     }
+    const double rr = sqrt(rr2);
     M[k] = Mk;
     S[3 * k] = Sx; S[3 * k + 1] = Sy; S[3 * k + 2] = Sz;
     zc[3 * k] = zx; zc[3 * k + 1] = zy; zc[3 * k + 2] = zz;

@@ -8,7 +8,9 @@ The autotuner picks the leaf size, the expansion order p and the MAC
 tolerance eps that give the fastest forest solve whose RMS relative
 acceleration error (Sec. 3.1.1) is at most the target in EVERY cluster,
 measured against the FP64 direct sum over all bodies of every cluster (or
-a sample of them per cluster with --sample).
+a sample of them per cluster with --sample); then, for that pick, the
+faster way of staging the P2P source tiles (bulk copies or per-lane loads,
+which give the same forces).
 
     python -m paper_2012_02207_gb300.ensemble --out tuned_ensemble.json
 """
@@ -120,6 +122,21 @@ class Ensemble:
         return out, min(ts)
 
 
+def pick_staging(ens, best, precision="mixed", log=print):
+    """The faster P2P source staging for a picked (leaf, p, eps): bulk copies
+    or per-lane loads (the forces are the same)."""
+    from . import FMM  # noqa: PLC0415
+    times = {}
+    for name, bulk in (("bulk", True), ("loads", False)):
+        f = FMM(p=best["p"], eps=best["eps"], leaf_size=best["leaf"], precision=precision, p2p_bulk=bulk)
+        _, times[name] = ens.time_batch(f)
+        log(json.dumps({"staging": name, "ms": times[name]}))
+    best = dict(best)
+    best["p2p_staging"] = min(times, key=times.get)
+    best["ms"] = times[best["p2p_staging"]]
+    return best, times
+
+
 def autotune(ens, target=1e-6, precision="mixed", leaves=LEAVES, orders=ORDERS, log=print):
     """Fastest (leaf, p, eps) whose worst per-cluster RMS is <= target."""
     from . import FMM  # noqa: PLC0415
@@ -177,18 +194,21 @@ def main():
         tune_ens = Ensemble(offsets[:k + 1], pos[:offsets[k]], mass[:offsets[k]], sample=args.sample)
         best, trials = autotune(tune_ens, args.target, log=log)
         del tune_ens
-    f = FMM(p=best["p"], eps=best["eps"], leaf_size=best["leaf"], precision="mixed")
+    best, staging_ms = pick_staging(ens, best, log=log)
+    bulk = best["p2p_staging"] == "bulk"
+    f = FMM(p=best["p"], eps=best["eps"], leaf_size=best["leaf"], precision="mixed", p2p_bulk=bulk)
     out, ms = ens.time_batch(f, steps=5)
     rms = ens.errors(out)
     st = f.stats()
-    g = FMM(p=best["p"], eps=best["eps"], leaf_size=best["leaf"], precision="mixed")
+    g = FMM(p=best["p"], eps=best["eps"], leaf_size=best["leaf"], precision="mixed", p2p_bulk=bulk)
     gout, ms_graph, replayed = ens.time_graph(g)
     graph_equal = all(bool((a == b).all()) for a, b in zip(gout, out))
-    _, ms_loop = ens.time_loop(lambda: FMM(p=best["p"], eps=best["eps"], leaf_size=best["leaf"], precision="mixed"))
+    _, ms_loop = ens.time_loop(lambda: FMM(p=best["p"], eps=best["eps"], leaf_size=best["leaf"], precision="mixed",
+                                           p2p_bulk=bulk))
     doc = {"workload": f"ensemble of {args.clusters} Plummer clusters, N_c = floor(2^U[10,17]) (seed {args.seed}, "
                        f"cluster c drawn with seed 1000+c), virial radii U[0.5,2], equal masses 1/N_c",
            "n_bodies": ens.n, "precision": "mixed", "target_rms": args.target,
-           "tuned_on_clusters": k, "tuned": best,
+           "tuned_on_clusters": k, "tuned": best, "staging_ms": staging_ms,
            "forest_ms": ms, "forest_particles_per_s": ens.n / (ms * 1e-3),
            "graph_replay_ms_host": ms_graph, "graph_particles_per_s": ens.n / (ms_graph * 1e-3),
            "graph_replayed": replayed, "graph_equals_batch": graph_equal,
