@@ -3,22 +3,22 @@
 //
 // P2P runs over work items: a target leaf and at most kLeavesPerItem of the
 // source leaves in its (sorted) P2P list, taken by warps from a counter.
-// A warp stages the item's source bodies in shared memory and takes the
-// target bodies 32 at a time, giving each of the nt targets of a chunk
-// G = 32 / nt lanes that split the sources between them (G = 1, 2, 4 run
-// unrolled). Each item writes one partial per target body. k_leaf_reduce
-// then evaluates the leaf's local expansion at the body (L2P), adds the
-// body's partials in item order, and writes the result times G to the
-// caller's order through the sort permutation. Every sum runs in a fixed
-// order. (Balanced rounds that keep more lanes busy, e.g. 2 x 10 targets with
-// 3 lanes each for a leaf of 20, ran the leaf phase at 11.9 ms against 7.0 ms:
-// the odd lane counts take the generic loop and every round stages the
-// sources again.)
+// The default kernel (k_p2p_tiles) stages the item's source bodies in shared
+// memory, by bulk copies or plain loads, puts the sources across the lanes
+// and keeps a group of target bodies in every lane's registers, so one
+// shared-memory load serves several interactions and every lane is busy
+// whatever the leaf sizes; a fixed transpose reduction then sums the lanes.
+// The alternative kernel (k_p2p_lanes, GBFMM_P2P_TILES=0) gives each target
+// G = 32 / nt lanes that split the sources between them. Each item writes
+// one partial per target body. k_leaf_reduce then evaluates the leaf's local
+// expansion at the body (L2P), adds the body's partials in item order, and
+// writes the result to the caller's order through the sort permutation.
+// Every sum runs in a fixed order.
 //
 // Mixed precision: bodies are stored relative to their own leaf centre in
 // FP32; a source leaf A is moved into the target leaf B's frame by the
-// FP32-rounded offset z_A - z_B (computed in FP64). Terms are FP32 (rsqrtf);
-// each source leaf's partial sum is folded into an FP64 accumulator.
+// FP32-rounded offset z_A - z_B (computed from double-float centres). Terms
+// are FP32 (rsqrtf); each staged pack's sum is accumulated in FP64.
 #include "gbfmm_internal.cuh"
 
 namespace gbfmm {
@@ -212,13 +212,11 @@ template <>
 struct TileCfg<float> {
     static constexpr int TG = GBFMM_P2P_TG;  // targets per group
     static constexpr int kCap = GBFMM_P2P_CAP32;  // staged source bodies per warp (512: 8 KB, at most 16 per lane)
-    static constexpr int kRun = 1 << 30;  // so a lane's run is at most 16 terms: no fold
 };
 template <>
 struct TileCfg<double> {
     static constexpr int TG = 4;
     static constexpr int kCap = 256;          // 8 KB per warp
-    static constexpr int kRun = 1 << 30;      // FP64: no fold
 };
 constexpr int kTargetChunk = 64;  // targets whose totals a warp keeps in shared memory per pass
 
@@ -425,8 +423,21 @@ __device__ __forceinline__ void halve(T* v, int lane, int o) {
     }
 }
 
-// v[0..V-1] on every lane (V = 32, 16 or 8). On return v[0] of lane l holds
-// the sum over the 32 lanes of value l % V.
+// The same step for a lane whose halves are already swapped when bit o is
+// set (slot s of such a lane holds value s ^ (C/2)): every lane keeps the
+// lower slots and sends the upper ones, with no selects.
+template <int C, typename T>
+__device__ __forceinline__ void halve_swapped(T* v, int o) {
+#pragma unroll
+    for (int i = 0; i < C / 2; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i + C / 2], o);
+}
+
+// v[0..V-1] on every lane (V = 32, 16 or 8), value j = 4 t + c (target t,
+// component c), with lane l holding target t ^ ((l >> 2) & (V/4 - 1)) in
+// slot t (the target order p2p_group gives each lane). On return v[0] of
+// lane l holds the sum over the 32 lanes of value l % V. The steps over the
+// target bits (lane bits 4..2) need no selects; the two over the components
+// (lane bits 1, 0) do.
 template <int V, typename T>
 __device__ __forceinline__ T transpose_reduce(T* v, int lane) {
     static_assert(V == 32 || V == 16 || V == 8, "V");
@@ -438,9 +449,9 @@ __device__ __forceinline__ T transpose_reduce(T* v, int lane) {
 #pragma unroll
         for (int i = 0; i < V; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 8);
     }
-    if constexpr (V == 32) halve<32>(v, lane, 16);
-    if constexpr (V >= 16) halve<16>(v, lane, 8);
-    halve<8>(v, lane, 4);
+    if constexpr (V == 32) halve_swapped<32>(v, 16);
+    if constexpr (V >= 16) halve_swapped<16>(v, 8);
+    halve_swapped<8>(v, 4);
     halve<4>(v, lane, 2);
     halve<2>(v, lane, 1);
     return v[0];
@@ -448,26 +459,29 @@ __device__ __forceinline__ T transpose_reduce(T* v, int lane) {
 
 // One group of NT targets (b0 + t0 .. b0 + t0 + NT - 1, clamped to the last
 // target; clamped duplicates are computed and discarded) against the cnt
-// staged sources; adds the group's totals to tot[4 * (t0 + t) + c].
+// staged sources; adds the group's totals to tot[4 * (t0 + t) + c]. Lane l
+// keeps target t ^ g, g = (l >> 2) & (NT - 1), in its slot t: the order the
+// select-free steps of transpose_reduce expect. A lane's FP32 sums run over
+// at most kCap / 32 terms.
 template <typename T, int NT, bool GUARD, bool SOFT>
 __device__ __forceinline__ void p2p_group(const Body4<T>* __restrict__ sm, int cnt, const Body4<T>* __restrict__ tg,
                                           int t0, int nt, T s2, double* tot, int lane) {
-    constexpr int kRun = TileCfg<T>::kRun;
+    const int g = (lane >> 2) & (NT - 1);
     T tx[NT], ty[NT], tz[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-        const Body4<T> v = tg[t0 + t < nt ? t0 + t : nt - 1];
+        const int i = t0 + (t ^ g);
+        const Body4<T> v = tg[i < nt ? i : nt - 1];
         tx[t] = v.x; ty[t] = v.y; tz[t] = v.z;
     }
-    T run[NT * 4], acc[NT * 4];
+    T run[NT * 4];
 #pragma unroll
-    for (int e = 0; e < NT * 4; ++e) { run[e] = T(0); acc[e] = T(0); }
-    static_assert(kRun >= (1 << 30) || sizeof(T) == 4, "fold only in FP32");
+    for (int e = 0; e < NT * 4; ++e) run[e] = T(0);
+    // the stage is padded to a multiple of 32 with massless far bodies (pad_stage)
     const int per_lane = (cnt + 31) >> 5;
     for (int u = 0; u < per_lane; ++u) {
-        const int k = lane + 32 * u;
-        const Body4<T> s = sm[k < cnt ? k : cnt - 1];
-        const T mj = k < cnt ? s.w : T(0);  // padding sources carry no mass
+        const Body4<T> s = sm[lane + 32 * u];
+        const T mj = s.w;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const T dx = s.x - tx[t], dy = s.y - ty[t], dz = s.z - tz[t];
@@ -483,15 +497,19 @@ __device__ __forceinline__ void p2p_group(const Body4<T>* __restrict__ sm, int c
             run[4 * t + 2] += mr3 * dz;
             run[4 * t + 3] += mr;
         }
-        if (kRun < (1 << 30) && (u % kRun) == kRun - 1) {
-#pragma unroll
-            for (int e = 0; e < NT * 4; ++e) { acc[e] += run[e]; run[e] = T(0); }
-        }
     }
-#pragma unroll
-    for (int e = 0; e < NT * 4; ++e) acc[e] += run[e];
-    const T v = transpose_reduce<NT * 4>(acc, lane);
+    const T v = transpose_reduce<NT * 4>(run, lane);
     if (lane < NT * 4 && 4 * t0 + lane < 4 * nt) tot[4 * t0 + lane] += (double)v;
+}
+
+// Fill the stage from cnt up to the next multiple of 32 with massless bodies
+// at x = 1e18: their terms are exactly zero (r^2 ~ 1e36 stays finite in FP32,
+// 0 * r^-1 = 0), so the lanes' loops need no bounds test. kCap is a multiple
+// of 32, so the padding stays inside the stage.
+template <typename T>
+__device__ __forceinline__ void pad_stage(Body4<T>* sm, int cnt, int lane) {
+    const int k = cnt + lane;
+    if (k < ((cnt + 31) & ~31)) sm[k] = {T(1e18), T(0), T(0), T(0)};
 }
 
 template <typename T, bool GUARD, bool SOFT>
@@ -509,6 +527,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : GBFMM_P2P_MINB) k_p2
                                                     const uint32_t* __restrict__ slot_first,
                                                     const uint32_t* __restrict__ nitems_p, unsigned* __restrict__ work) {
     constexpr int kCap = TileCfg<T>::kCap;
+    static_assert(kCap % 32 == 0, "the padded stage must fit in kCap");
     extern __shared__ __align__(16) unsigned char p2p_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char* wbase = p2p_smem + (size_t)wib * p2p_tile_smem_per_warp<T>();
@@ -563,6 +582,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : GBFMM_P2P_MINB) k_p2
                     if (lane == 0) atomicOr(a.err, kErrTimeout);
                     return;
                 }
+                pad_stage<T>(sm, cnt, lane);
                 __syncwarp();
                 if (tc == 0) { nsrc += (unsigned long long)cnt; self_item |= selfin; }
                 if (selfin) p2p_groups<T, true, SOFT>(sm, cnt, tg, nt, s2, tot, lane);

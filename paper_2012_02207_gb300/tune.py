@@ -102,20 +102,36 @@ def main():
     ap.add_argument("--eps", default=None, help="comma-separated eps values to scan (default: half-decades)")
     ap.add_argument("--verify-full", action="store_true",
                     help="also measure the chosen configurations' RMS over all bodies")
+    ap.add_argument("--leaf", default="64", help="comma-separated leaf sizes to scan")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     grid = [float(x) for x in args.eps.split(",")] if args.eps else EPS_GRID
     pos, m = ics.config_inputs("kroupa1m")
-    res = tune(pos, m, [int(x) for x in args.orders.split(",")], args.target, args.precision, args.sample,
-               grid=grid)
-    if args.verify_full:
-        for p_, rec in res.items():
-            if rec:
-                rec["rms_all_bodies"] = full_rms(pos, m, p_, rec["eps"], args.precision)
-                print(f"p={p_} eps={rec['eps']:.3g} rms over all bodies {rec['rms_all_bodies']:.3e}", flush=True)
+    by_leaf = {}
+    for leaf in [int(x) for x in args.leaf.split(",")]:
+        print(f"leaf size {leaf}", flush=True)
+        res = tune(pos, m, [int(x) for x in args.orders.split(",")], args.target, args.precision, args.sample,
+                   leaf_size=leaf, grid=grid)
+        if args.verify_full:
+            for p_, rec in res.items():
+                if rec:
+                    rec["rms_all_bodies"] = full_rms(pos, m, p_, rec["eps"], args.precision, leaf_size=leaf)
+                    print(f"p={p_} leaf={leaf} eps={rec['eps']:.3g} rms over all bodies "
+                          f"{rec['rms_all_bodies']:.3e}", flush=True)
+        by_leaf[leaf] = res
+    # the fastest (leaf, p) whose sample RMS met the target
+    ok = [(rec["ms"], leaf, p_) for leaf, res in by_leaf.items() for p_, rec in res.items() if rec]
+    fastest = min(ok) if ok else None
     doc = {"workload": "plummer_kroupa_n1048576 (positions seed 2, Kroupa masses seed 3)",
            "target_rms": args.target, "precision": args.precision, "sample": args.sample,
-           "reference": "FP64 direct sum at the sampled bodies", "orders": {str(k): v for k, v in res.items()}}
+           "reference": "FP64 direct sum at the sampled bodies"}
+    if len(by_leaf) == 1:
+        doc["leaf_size"] = next(iter(by_leaf))
+        doc["orders"] = {str(k): v for k, v in next(iter(by_leaf.values())).items()}
+    else:
+        doc["by_leaf"] = {str(lf): {str(k): v for k, v in res.items()} for lf, res in by_leaf.items()}
+    if fastest:
+        doc["fastest"] = {"leaf_size": fastest[1], "p": fastest[2], "ms": fastest[0]}
     text = json.dumps(doc, indent=1)
     print(text)
     if args.out:
