@@ -214,12 +214,18 @@ int fmm_timesteps(fmm_ctx* ctx, int64_t n, const double* x, const double* y, con
  * ones); evolve the fast system for dt/2. Below dt_min (or 60 levels) a set
  * is not split further. Forces: FP64 direct sum for sets of fewer than
  * direct_below bodies, else the context's FMM solve; G and the softening
- * from the context. stats (host, may be NULL): {slow-system kicks, FMM
- * solves, direct solves, deepest level, splits}. Errors as fmm_solve, and
- * FMM_ERR_ARG for dt <= 0, eta <= 0, dt_min < 0 or nsteps < 0. */
+ * from the context. A set of at most device_below bodies (0..1024; and
+ * fewer than direct_below) evolves inside one GPU block, its whole recursion
+ * included, with no host round trip: its direct forces are the oracle's
+ * (1 / (r^2 sqrt(r^2)), no fused multiply-add, sources in set order), so
+ * such runs reproduce the oracle's trajectory bit for bit; 0 keeps every
+ * level on the host-driven path. stats (host, may be NULL): {slow-system
+ * kicks, FMM solves, direct solves, deepest level, splits}. Errors as
+ * fmm_solve, and FMM_ERR_ARG for dt <= 0, eta <= 0, dt_min < 0, nsteps < 0
+ * or device_below outside [0, 1024]. */
 int fmm_hold(fmm_ctx* ctx, int64_t n, double* x, double* y, double* z, double* vx, double* vy, double* vz,
              const double* m, double dt, int64_t nsteps, double eta, int32_t symmetrize, double dt_min,
-             int64_t direct_below, int64_t* stats, void* cuda_stream);
+             int64_t direct_below, int64_t device_below, int64_t* stats, void* cuda_stream);
 
 /* Statistics of the last solve. */
 int fmm_get_stats(const fmm_ctx* ctx, fmm_stats* out);

@@ -79,7 +79,8 @@ def lib():
             L.fmm_direct.argtypes = [vp, i64, dp, dp, dp, dp, i64, dp, dp, dp, dp, dp, vp]
             L.fmm_timesteps.argtypes = [vp, i64] + [dp] * 7 + [ctypes.c_double, ctypes.c_int32, dp, vp]
             L.fmm_hold.argtypes = [vp, i64] + [dp] * 7 + [ctypes.c_double, i64, ctypes.c_double, ctypes.c_int32,
-                                                          ctypes.c_double, i64, ctypes.POINTER(ctypes.c_int64), vp]
+                                                          ctypes.c_double, i64, i64, ctypes.POINTER(ctypes.c_int64),
+                                                          vp]
             L.fmm_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
             L.fmm_export_tree.argtypes = [vp] + [dp] * 8
             L.fmm_export_geometry.argtypes = [vp] + [dp] * 6
@@ -242,9 +243,10 @@ class FMM:
         return out
 
     def hold(self, x, y, z, vx, vy, vz, m, dt, nsteps, eta=0.025, symmetrize=True, dt_min=1e-9,
-             direct_below=4096, stream=None):
+             direct_below=4096, device_below=1024, stream=None):
         """nsteps HOLD steps (fmm_hold) on device FP64 tensors, positions and
-        velocities updated in place; returns the run's counters."""
+        velocities updated in place; returns the run's counters. Sets of at
+        most device_below bodies evolve inside one GPU block (0: none)."""
         import torch  # noqa: PLC0415
         n = x.numel()
         for t in (x, y, z, vx, vy, vz, m):
@@ -253,7 +255,8 @@ class FMM:
                                  "of equal length")
         st = (ctypes.c_int64 * 5)()
         self._check(lib().fmm_hold(self._h, n, *(_ptr(t) for t in (x, y, z, vx, vy, vz, m)), float(dt), int(nsteps),
-                                   float(eta), int(bool(symmetrize)), float(dt_min), int(direct_below), st,
+                                   float(eta), int(bool(symmetrize)), float(dt_min), int(direct_below),
+                                   int(device_below), st,
                                    _stream_handle(stream)))
         return dict(zip(("kicks", "fmm_solves", "direct_solves", "max_depth", "splits"), list(st)))
 

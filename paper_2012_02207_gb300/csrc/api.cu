@@ -744,7 +744,6 @@ int jerk_pass(fmm_ctx* ctx, const double* vx, const double* vy, const double* vz
 // the FP64 direct sum (the fast-from-slow force then with the fast masses
 // zeroed), larger ones the FMM solve (fast from slow as the difference of the
 // solves over P and over F).
-constexpr int kHoldMaxDepth = 60;
 struct HoldRun {
     fmm_ctx* ctx;
     cudaStream_t st;
@@ -753,6 +752,8 @@ struct HoldRun {
     double eta, dt_min;
     bool sym;
     int64_t direct_below;
+    int64_t device_below;                   // sets of at most this many bodies evolve in one block
+    unsigned long long* dstats = nullptr;   // the device-resident evolutions' counters (device)
     int64_t kicks = 0, fmm_solves = 0, direct_solves = 0, max_depth = 0, splits = 0;
 };
 
@@ -805,6 +806,13 @@ int hold_kick_sets(HoldRun& R, const int* S, int ns, const int* F, int nf, doubl
 int hold_evolve(HoldRun& R, const int* P, int k, double dt, int depth) {
     if (k == 0) return FMM_OK;
     fmm_ctx* ctx = R.ctx;
+    if (k <= R.device_below && k <= kHoldSmallMax && k < R.direct_below) {
+        // the whole recursion below here inside one block (direct forces, as this path would use)
+        hold_small(k, P, R.x, R.y, R.z, R.vx, R.vy, R.vz, R.m, ctx->cfg.G, ctx->cfg.soft, R.eta, R.sym, dt, R.dt_min,
+                   depth, R.dstats, R.st);
+        CK(cudaGetLastError());
+        return FMM_OK;
+    }
     if (depth > R.max_depth) R.max_depth = depth;
     const int* S = P;
     const int* F = nullptr;
@@ -1210,15 +1218,18 @@ int fmm_solve_batch(fmm_ctx* ctx, int32_t nclusters, const int64_t* offsets, con
 
 int fmm_hold(fmm_ctx* ctx, int64_t n, double* x, double* y, double* z, double* vx, double* vy, double* vz,
              const double* m, double dt, int64_t nsteps, double eta, int32_t symmetrize, double dt_min,
-             int64_t direct_below, int64_t* stats, void* cuda_stream) {
+             int64_t direct_below, int64_t device_below, int64_t* stats, void* cuda_stream) {
     if (!ctx) return FMM_ERR_ARG;
     if (n < 0 || n > (int64_t)1 << 30) return fail(ctx, FMM_ERR_ARG, "n must be in [0, 2^30]");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FMM_ERR_ARG, "dt must be finite and > 0");
     if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ctx, FMM_ERR_ARG, "eta must be finite and > 0");
     if (!(dt_min >= 0.0) || nsteps < 0) return fail(ctx, FMM_ERR_ARG, "dt_min >= 0 and nsteps >= 0 required");
+    if (device_below < 0 || device_below > kHoldSmallMax)
+        return fail(ctx, FMM_ERR_ARG, "device_below must be in [0, 1024]");
     if (n > 0 && (!x || !y || !z || !vx || !vy || !vz || !m)) return fail(ctx, FMM_ERR_ARG, "NULL pointer");
     cudaSetDevice(ctx->device);
-    HoldRun R{ctx, (cudaStream_t)cuda_stream, x, y, z, vx, vy, vz, m, eta, dt_min, symmetrize != 0, direct_below};
+    HoldRun R{ctx, (cudaStream_t)cuda_stream, x, y, z, vx, vy, vz, m, eta, dt_min, symmetrize != 0, direct_below,
+              device_below};
     const size_t N = (size_t)(n > 0 ? n : 1);
     int rc;
     if ((rc = ensure(ctx, ctx->h_all, 4 * N)) || (rc = ensure(ctx, ctx->h_gat, 56 * N)) ||
@@ -1227,10 +1238,18 @@ int fmm_hold(fmm_ctx* ctx, int64_t n, double* x, double* y, double* z, double* v
         (rc = ensure(ctx, ctx->h_scan, 4 * N)) || (rc = ensure(ctx, ctx->h_scr, 4 * scan_scratch_words((int64_t)N))) ||
         (rc = ensure(ctx, ctx->h_nf, 64)))
         return rc;
+    R.dstats = as<unsigned long long>(ctx->h_nf) + 1;  // words 1..5 (word 0 holds the split's fast count)
+    CK(cudaMemsetAsync(R.dstats, 0, 5 * sizeof(unsigned long long), R.st));
     hold_iota((int)n, as<int>(ctx->h_all), R.st);
     for (int64_t s = 0; s < nsteps && n > 0; ++s)
         if ((rc = hold_evolve(R, as<int>(ctx->h_all), (int)n, dt, 0)) != FMM_OK) return rc;
+    unsigned long long dst[5] = {0, 0, 0, 0, 0};
+    CK(cudaMemcpyAsync(dst, R.dstats, sizeof(dst), cudaMemcpyDeviceToHost, R.st));
     CK(cudaStreamSynchronize(R.st));
+    R.kicks += (int64_t)dst[0];
+    R.direct_solves += (int64_t)dst[2];
+    if ((int64_t)dst[3] > R.max_depth) R.max_depth = (int64_t)dst[3];
+    R.splits += (int64_t)dst[4];
     if (stats) {
         stats[0] = R.kicks;
         stats[1] = R.fmm_solves;

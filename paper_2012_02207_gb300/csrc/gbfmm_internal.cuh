@@ -346,6 +346,9 @@ void jerk_leaves(const LeafArgs& a, bool fp32, const void* locj, const double* v
 void timesteps_f64(int n, const double* x, const double* y, const double* z, const double* vx, const double* vy,
                    const double* vz, const double* m, double G, double eta, bool sym, double* tau, cudaStream_t st);
 // ----------------------------------------------------------------- hold.cu
+constexpr int kHoldMaxDepth = 60;                  // no set is split below this level
+constexpr int kHoldMaxLevels = kHoldMaxDepth + 1;  // frames of the device-resident recursion
+constexpr int kHoldSmallMax = 1024;                // largest set evolved inside one block
 // set operations of the HOLD integrator (index lists of bodies)
 void hold_iota(int n, int* idx, cudaStream_t st);
 // out[c * stride + a] = field c of body idx[a] (x, y, z, vx, vy, vz, m);
@@ -361,6 +364,14 @@ void hold_kick(int k, const int* idx, const double* acc, const double* sub, int 
                double* vx, double* vy, double* vz, cudaStream_t st);
 void hold_drift(int k, const int* idx, double dt, double* x, double* y, double* z, const double* vx,
                 const double* vy, const double* vz, cudaStream_t st);
+// evolve(P, dt) of the k <= kHoldSmallMax bodies idx[0..k) at recursion
+// level depth, recursion included, in one block with direct FP64 forces (the
+// oracle's operations and order); adds its counters to stats (device,
+// {kicks, -, direct solves, deepest level (max), splits})
+size_t hold_small_smem(int k);
+void hold_small(int k, const int* idx, double* x, double* y, double* z, double* vx, double* vy, double* vz,
+                const double* m, double G, double soft, double eta, bool sym, double dt, double dt_min, int depth,
+                unsigned long long* stats, cudaStream_t st);
 // soft: Plummer softening length (0: Newtonian)
 void direct_sum_f64(int64_t n, const double* x, const double* y, const double* z, const double* m,
                     double G, double soft, int64_t ntgt, const int64_t* tgt, double* ax, double* ay, double* az,

@@ -32,7 +32,7 @@ def energy(fmm, X, V, M, direct=True):
     return float(ek + 0.5 * (M * pot).sum())
 
 
-def run(pos, vel, mass, t_end, dt, eta, sym, soft, direct_below, p, eps):
+def run(pos, vel, mass, t_end, dt, eta, sym, soft, direct_below, p, eps, device_below=1024):
     import torch  # noqa: PLC0415
 
     from . import FMM  # noqa: PLC0415
@@ -47,7 +47,8 @@ def run(pos, vel, mass, t_end, dt, eta, sym, soft, direct_below, p, eps):
     errs, totals = [], {}
     t0 = time.perf_counter()
     for _ in range(int(round(t_end))):
-        st = f.hold(*X, *V, M, dt, steps_per_unit, eta=eta, symmetrize=sym, dt_min=1e-9, direct_below=direct_below)
+        st = f.hold(*X, *V, M, dt, steps_per_unit, eta=eta, symmetrize=sym, dt_min=1e-9, direct_below=direct_below,
+                    device_below=device_below)
         for k, v in st.items():
             totals[k] = max(totals.get(k, 0), v) if k == "max_depth" else totals.get(k, 0) + v
         E = energy(f, X, V, M, direct)
@@ -73,6 +74,8 @@ def main():
     ap.add_argument("--eta", type=float, default=0.025, help="step-size accuracy (Table 1: 0.025)")
     ap.add_argument("--soft", type=float, default=0.0)
     ap.add_argument("--direct-below", type=int, default=4096)
+    ap.add_argument("--device-below", type=int, default=1024,
+                    help="sets of at most this many bodies evolve inside one GPU block (0: none)")
     ap.add_argument("--p", type=int, default=12)
     ap.add_argument("--eps", type=float, default=1e-10)
     ap.add_argument("--sym", default="both", choices=["both", "on", "off"])
@@ -85,7 +88,7 @@ def main():
         for r in range(args.realizations):
             pos, vel, m = ics.plummer(args.n, args.seed + r)
             res = run(pos, vel, m, args.t_end, args.dt, args.eta, sym, args.soft, args.direct_below, args.p,
-                      args.eps)
+                      args.eps, args.device_below)
             runs.append(res)
             print(json.dumps({"rule": key, "realization": r, "max": res["max_rel_energy_error"],
                               "final": res["final_rel_energy_error"], "wall_s": res["wall_s"],

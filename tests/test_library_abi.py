@@ -110,7 +110,7 @@ def test_every_context_call_rejects_a_null_context_without_a_gpu():
         "fmm_solve_jerk": (None, 10) + (None,) * 14 + (None,),
         "fmm_direct": (None, 10, None, None, None, None, 10, None, None, None, None, None, None),
         "fmm_timesteps": (None, 10) + (None,) * 7 + (0.03, 1, None, None),
-        "fmm_hold": (None, 10) + (None,) * 7 + (0.01, 1, 0.03, 1, 1e-9, 4096, None, None),
+        "fmm_hold": (None, 10) + (None,) * 7 + (0.01, 1, 0.03, 1, 1e-9, 4096, 1024, None, None),
         "fmm_get_stats": (None, None),
         "fmm_export_tree": (None,) + (None,) * 8,
         "fmm_export_geometry": (None,) + (None,) * 6,
