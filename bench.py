@@ -80,29 +80,35 @@ def measured_fma_peaks(gb, local):
 
 
 def m2l_flops(p):
-    """Algorithmic flops of one directed rotation-accelerated M2L at order p:
-    four z-rotations (complex products on every m >= 1 coefficient), four
-    swaps (one FMA per non-zero of the cosine and sine blocks; the swap right
-    after the z-translation only over its non-zero inputs, F'_n^m with
-    m <= p - n), the z-translation (one FMA per (n, k, m) term and real/imag
-    part) and the accumulation of the (p+1)^2 result."""
+    """Algorithmic flops of one directed rotation-accelerated M2L at order p,
+    counting a linear combination of t non-zero terms as t multiplies and
+    t - 1 adds: four z-rotations (the powers of e^{i angle} and a complex
+    product on every m >= 1 coefficient), four swaps (the cosine and sine
+    blocks' non-zero entries by parity; the swap right after the
+    z-translation only over its non-zero inputs, F'_n^m with m <= p - n), the
+    z-translation (the powers of u and v, u^k times each input, one
+    combination per output and its scale) and the accumulation of the
+    (p+1)^2 result."""
+    def lin(t):
+        return 2 * t - 1 if t > 0 else 0
+
     rot = sum(6 + 6 * (p - m + 1) for m in range(1, p + 1))
 
-    def swap_terms(after_z):
-        cnt = 0
+    def swap(after_z):
+        f = 0
         for n in range(1, p + 1):
             jmax = min(n, p - n) if after_z else n
-            cnt += sum(1 for m in range(n + 1) for j in range(jmax + 1) if (j + m + n) % 2 == 0)
-            cnt += sum(1 for m in range(1, n + 1) for j in range(1, jmax + 1) if (j + m + n) % 2 == 1)
-        return cnt
-    swap4 = 3 * swap_terms(False) + swap_terms(True)
-    trans = 0
+            f += sum(lin(sum(1 for j in range(jmax + 1) if (j + m + n) % 2 == 0)) for m in range(n + 1))
+            f += sum(lin(sum(1 for j in range(1, jmax + 1) if (j + m + n) % 2 == 1)) for m in range(1, n + 1))
+        return f
+    trans = 2 * p
     for m in range(p + 1):
         parts = 2 if m else 1
-        trans += parts * (p - m + 1)                     # signs and powers of u
+        trans += parts * (p - m + 1)
         for n in range(m, p + 1):
-            trans += parts * 2 * max(0, p - n - m + 1) + parts  # FMAs + final scale
-    return 4 * rot + 2 * swap4 + 2 * trans + (p + 1) ** 2
+            t = max(0, p - n - m + 1)
+            trans += parts * (lin(t) + (1 if t else 0))
+    return 4 * rot + 3 * swap(False) + swap(True) + trans + (p + 1) ** 2
 
 
 P2P_FLOPS = 20  # per directed body-body interaction (the usual gravity-kernel count)
