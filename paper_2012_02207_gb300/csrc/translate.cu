@@ -83,8 +83,16 @@ struct WarpVec {
     T* t;    // (p+1)^2 scratch
 };
 
-// pw[2m], pw[2m+1] = (c + i s)^m for m = 0..p, lane m by binary powering
-template <typename T>
+// The G threads (a warp, or a block of 128 for the few nodes of the upper
+// levels) that evolve one node's vector synchronise with gsync<G>.
+template <int G>
+__device__ __forceinline__ void gsync() {
+    if constexpr (G == 32) __syncwarp();
+    else __syncthreads();
+}
+
+// pw[2m], pw[2m+1] = (c + i s)^m for m = 0..p, thread m by binary powering
+template <int G, typename T>
 __device__ void wpowers(T* pw, int p, T c, T s, int lane) {
     if (lane <= p) {
         T pr = ar_from<T>(1.0), pi = ar_from<T>(0.0), br = c, bi = s;
@@ -102,14 +110,14 @@ __device__ void wpowers(T* pw, int p, T c, T s, int lane) {
         pw[2 * lane] = pr;
         pw[2 * lane + 1] = pi;
     }
-    __syncwarp();
+    gsync<G>();
 }
 
 // v <- Rz: coefficient m times pw_m (or its conjugate)
-template <typename T>
+template <int G, typename T>
 __device__ void wrotz(WarpVec<T>& w, int p, const T* pw, bool conj, int lane) {
     const int ncx = p * (p + 1) / 2;  // complex coefficients with m >= 1
-    for (int q = lane; q < ncx; q += 32) {
+    for (int q = lane; q < ncx; q += G) {
         int n = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);  // q = n(n-1)/2 + (m-1), n >= 1
         while (n * (n + 1) / 2 <= q) ++n;
         while ((n - 1) * n / 2 > q) --n;
@@ -119,13 +127,13 @@ __device__ void wrotz(WarpVec<T>& w, int p, const T* pw, bool conj, int lane) {
         w.v[hre(n, mm)] = ar_sub(ar_mul(re, pr), ar_mul(im, pi));
         w.v[him(n, mm)] = ar_add(ar_mul(re, pi), ar_mul(im, pr));
     }
-    __syncwarp();
+    gsync<G>();
 }
 
-template <typename T>
+template <int G, typename T>
 __device__ void wswap(WarpVec<T>& w, int p, const RotTables<T>& tb, int lane) {
     const int nr = ncoef_real(p);
-    for (int q = lane; q < nr; q += 32) {
+    for (int q = lane; q < nr; q += G) {
         int n, mm;
         bool im;
         decode_q(q, n, mm, im);
@@ -139,8 +147,42 @@ __device__ void wswap(WarpVec<T>& w, int p, const RotTables<T>& tb, int lane) {
         }
         w.t[q] = acc;
     }
-    __syncwarp();
+    gsync<G>();
     T* tq = w.v; w.v = w.t; w.t = tq;
+}
+
+// The M2M z-shift gives output (n, m) n - m + 1 terms, from 1 to n + 1, so a
+// lane per output leaves most lanes idle while the longest finish. Outputs
+// are paired into units of n + 1 terms each: (n, 0) alone; (n, m) with
+// (n, n + 1 - m) for 1 <= m <= n/2, real parts together and imaginary parts
+// together; for odd n the real and imaginary parts of m = (n + 1)/2. Unit u
+// counts down from degree p, so the units a warp takes at once have nearly
+// equal lengths. Output A takes the first len_a terms of the unit; output B
+// (absent when len_a = n + 1) the rest.
+__device__ __forceinline__ void m2m_zshift_unit(int p, int u, int& n, int& ma, bool& ia, int& mb, bool& ib,
+                                                int& len_a) {
+    n = p;
+    while (u > n) {  // degree n owns n + 1 units
+        u -= n + 1;
+        --n;
+    }
+    if (u == 0) {
+        ma = mb = 0;
+        ia = ib = false;
+        len_a = n + 1;
+        return;
+    }
+    if ((n & 1) && u == n) {  // odd n: both parts of m = (n + 1)/2
+        ma = mb = (n + 1) >> 1;
+        ia = false;
+        ib = true;
+        len_a = n - ma + 1;
+        return;
+    }
+    ma = ((u - 1) >> 1) + 1;
+    mb = n + 1 - ma;
+    ia = ib = ((u - 1) & 1) != 0;
+    len_a = n - ma + 1;
 }
 
 // shared values per warp: vector, scratch, two power tables, u^k and (s_C/s_P)^k
@@ -172,14 +214,14 @@ __global__ void k_shift_geometry(TreeView t, const double* __restrict__ zc, cons
     g[5] = hs[C] / sP;
 }
 
-template <typename T>
+template <typename T, int G>
 __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int Lc, int p,
                                                   const double* __restrict__ geo,
                                                   const double* __restrict__ mult,
                                                   double* __restrict__ contrib, RotTables<T> tb) {
     extern __shared__ __align__(16) unsigned char sh_m2m_raw[];
     T* sh_m2m = reinterpret_cast<T*>(sh_m2m_raw);
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int lane = threadIdx.x % G, wib = threadIdx.x / G;
     const int nr = ncoef_real(p);
     T* base = sh_m2m + (size_t)wib * m2m_warp_values(p);
     WarpVec<T> wv{base, base + nr};
@@ -187,16 +229,16 @@ __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int Lc, int p,
     T* pwb = pwa + 2 * (p + 1);    // (cos theta - i sin theta)^m: Rz(-theta), conjugate for Rz(theta)
     T* upow = pwb + 2 * (p + 1);   // u^k
     T* spow = upow + (p + 1);      // (s_C/s_P)^k
-    const int C = t.dls[Lc] + blockIdx.x * (blockDim.x >> 5) + wib;
+    const int C = t.dls[Lc] + blockIdx.x * (blockDim.x / G) + wib;
     if (C >= t.dls[Lc + 1]) return;
     const int P = t.parent[C];
     const double* src = mult + (size_t)nr * C;
-    for (int q = lane; q < nr; q += 32) wv.v[q] = ar_from<T>(src[q]);
+    for (int q = lane; q < nr; q += G) wv.v[q] = ar_from<T>(src[q]);
     (void)P;
     const double* gc = geo + kShiftGeo * (size_t)C;  // the shift's geometry (k_shift_geometry)
     const double cp = gc[0], sp = gc[1], ct = gc[2], st = gc[3], u = gc[4], sg = gc[5];
-    wpowers<T>(pwa, p, ar_from<T>(sp), ar_from<T>(cp), lane);
-    wpowers<T>(pwb, p, ar_from<T>(ct), ar_from<T>(-st), lane);
+    wpowers<G, T>(pwa, p, ar_from<T>(sp), ar_from<T>(cp), lane);
+    wpowers<G, T>(pwb, p, ar_from<T>(ct), ar_from<T>(-st), lane);
     // u^k and (s_C/s_P)^k, lane k by binary powering
     if (lane <= p) {
         T a = ar_from<T>(1.0), b = ar_from<T>(1.0), ba = ar_from<T>(u), bb = ar_from<T>(sg);
@@ -208,31 +250,42 @@ __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int Lc, int p,
         upow[lane] = a;
         spow[lane] = b;
     }
-    __syncwarp();
-    wrotz(wv, p, pwa, false, lane);  // Rz(pi/2 - phi)
-    wswap(wv, p, tb, lane);
-    wrotz(wv, p, pwb, false, lane);  // Rz(-theta)
-    wswap(wv, p, tb, lane);
-    // z-shift into the scratch vector
-    for (int q = lane; q < nr; q += 32) {
-        int n, mm;
-        bool im;
-        decode_q(q, n, mm, im);
-        const int cz = zshift_offset(n, mm);
-        T acc = ar_from<T>(0.0);
-        for (int k = 0; k <= n - mm; ++k)
-            acc = ar_add(acc, ar_mul(ar_mul(tb.z(cz + k), upow[k]),
-                                     ar_mul(spow[n - k], wv.v[im ? him(n - k, mm) : hre(n - k, mm)])));
-        wv.t[q] = acc;
+    gsync<G>();
+    wrotz<G>(wv, p, pwa, false, lane);  // Rz(pi/2 - phi)
+    wswap<G>(wv, p, tb, lane);
+    wrotz<G>(wv, p, pwb, false, lane);  // Rz(-theta)
+    wswap<G>(wv, p, tb, lane);
+    // z-shift into the scratch vector, over balanced units (m2m_zshift_unit):
+    // each output's terms in the same order as a plain loop over k
+    const int nunits = (p + 1) * (p + 2) / 2;
+    for (int u = lane; u < nunits; u += G) {
+        int n, ma, mb, len_a;
+        bool ia, ib;
+        m2m_zshift_unit(p, u, n, ma, ia, mb, ib, len_a);
+        const int cza = zshift_offset(n, ma), czb = zshift_offset(n, mb);
+        T acc_a = ar_from<T>(0.0), acc_b = ar_from<T>(0.0);
+        for (int s = 0; s <= n; ++s) {
+            const bool in_a = s < len_a;
+            const int k = in_a ? s : s - len_a;
+            const int mm = in_a ? ma : mb;
+            const bool im = in_a ? ia : ib;
+            const T term = ar_mul(ar_mul(tb.z((in_a ? cza : czb) + k), upow[k]),
+                                  ar_mul(spow[n - k], wv.v[im ? him(n - k, mm) : hre(n - k, mm)]));
+            const T sum = ar_add(in_a ? acc_a : acc_b, term);  // one add on every lane, no divergence
+            acc_a = in_a ? sum : acc_a;
+            acc_b = in_a ? acc_b : sum;
+        }
+        wv.t[ia ? him(n, ma) : hre(n, ma)] = acc_a;
+        if (len_a <= n) wv.t[ib ? him(n, mb) : hre(n, mb)] = acc_b;
     }
-    __syncwarp();
+    gsync<G>();
     { T* tq = wv.v; wv.v = wv.t; wv.t = tq; }
-    wswap(wv, p, tb, lane);
-    wrotz(wv, p, pwb, true, lane);   // Rz(theta)
-    wswap(wv, p, tb, lane);
-    wrotz(wv, p, pwa, true, lane);   // Rz(phi - pi/2)
+    wswap<G>(wv, p, tb, lane);
+    wrotz<G>(wv, p, pwb, true, lane);   // Rz(theta)
+    wswap<G>(wv, p, tb, lane);
+    wrotz<G>(wv, p, pwa, true, lane);   // Rz(phi - pi/2)
     double* dst = contrib + (size_t)nr * C;
-    for (int q = lane; q < nr; q += 32) dst[q] = ar_to(wv.v[q]);
+    for (int q = lane; q < nr; q += G) dst[q] = ar_to(wv.v[q]);
 }
 
 // Rotation-accelerated L2L: with b = z_C - z_P rotated onto +z,
@@ -240,13 +293,13 @@ __global__ void __launch_bounds__(128) k_m2m_rot(TreeView t, int Lc, int p,
 // u = rho/s_P, sigma = s_C/s_P (the hat form of F_n^m(C) = sum_k rho^k/k! F_{n+k}^m(P)
 // on the axis), between the same rotations as M2M. The local coefficients
 // (T = float or double) are added to the child's, which the M2L wrote.
-template <typename T>
+template <typename T, int G>
 __global__ void __launch_bounds__(128) k_l2l_rot(TreeView t, int L, int p,
                                                   const double* __restrict__ geo,
                                                   T* __restrict__ loc, RotTables<T> tb) {
     extern __shared__ __align__(16) unsigned char sh_l2l_raw[];
     T* sh = reinterpret_cast<T*>(sh_l2l_raw);
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int lane = threadIdx.x % G, wib = threadIdx.x / G;
     const int nr = ncoef_real(p);
     T* base = sh + (size_t)wib * m2m_warp_values(p);
     WarpVec<T> wv{base, base + nr};
@@ -254,15 +307,15 @@ __global__ void __launch_bounds__(128) k_l2l_rot(TreeView t, int L, int p,
     T* pwb = pwa + 2 * (p + 1);
     T* upow = pwb + 2 * (p + 1);
     T* spow = upow + (p + 1);
-    const int C = t.dls[L] + blockIdx.x * (blockDim.x >> 5) + wib;
+    const int C = t.dls[L] + blockIdx.x * (blockDim.x / G) + wib;
     if (C >= t.dls[L + 1]) return;
     const int P = t.parent[C];
     const T* src = loc + (size_t)nr * P;
-    for (int q = lane; q < nr; q += 32) wv.v[q] = src[q];
+    for (int q = lane; q < nr; q += G) wv.v[q] = src[q];
     const double* gc = geo + kShiftGeo * (size_t)C;  // the shift's geometry (k_shift_geometry)
     const double cp = gc[0], sp = gc[1], ct = gc[2], st = gc[3], u = gc[4], sg = gc[5];
-    wpowers<T>(pwa, p, ar_from<T>(sp), ar_from<T>(cp), lane);
-    wpowers<T>(pwb, p, ar_from<T>(ct), ar_from<T>(-st), lane);
+    wpowers<G, T>(pwa, p, ar_from<T>(sp), ar_from<T>(cp), lane);
+    wpowers<G, T>(pwb, p, ar_from<T>(ct), ar_from<T>(-st), lane);
     if (lane <= p) {
         T a = ar_from<T>(1.0), b = ar_from<T>(1.0), ba = ar_from<T>(u), bb = ar_from<T>(sg);
         for (int e = lane; e > 0; e >>= 1) {
@@ -273,12 +326,12 @@ __global__ void __launch_bounds__(128) k_l2l_rot(TreeView t, int L, int p,
         upow[lane] = a;
         spow[lane] = b;
     }
-    __syncwarp();
-    wrotz(wv, p, pwa, false, lane);  // Rz(pi/2 - phi)
-    wswap(wv, p, tb, lane);
-    wrotz(wv, p, pwb, false, lane);  // Rz(-theta)
-    wswap(wv, p, tb, lane);
-    for (int q = lane; q < nr; q += 32) {
+    gsync<G>();
+    wrotz<G>(wv, p, pwa, false, lane);  // Rz(pi/2 - phi)
+    wswap<G>(wv, p, tb, lane);
+    wrotz<G>(wv, p, pwb, false, lane);  // Rz(-theta)
+    wswap<G>(wv, p, tb, lane);
+    for (int q = lane; q < nr; q += G) {
         int n, mm;
         bool im;
         decode_q(q, n, mm, im);
@@ -288,14 +341,14 @@ __global__ void __launch_bounds__(128) k_l2l_rot(TreeView t, int L, int p,
                                      wv.v[im ? him(n + k, mm) : hre(n + k, mm)]));
         wv.t[q] = ar_mul(spow[n], acc);
     }
-    __syncwarp();
+    gsync<G>();
     { T* tq = wv.v; wv.v = wv.t; wv.t = tq; }
-    wswap(wv, p, tb, lane);
-    wrotz(wv, p, pwb, true, lane);   // Rz(theta)
-    wswap(wv, p, tb, lane);
-    wrotz(wv, p, pwa, true, lane);   // Rz(phi - pi/2)
+    wswap<G>(wv, p, tb, lane);
+    wrotz<G>(wv, p, pwb, true, lane);   // Rz(theta)
+    wswap<G>(wv, p, tb, lane);
+    wrotz<G>(wv, p, pwa, true, lane);   // Rz(phi - pi/2)
     T* dst = loc + (size_t)nr * C;
-    for (int q = lane; q < nr; q += 32) dst[q] = ar_add(dst[q], wv.v[q]);
+    for (int q = lane; q < nr; q += G) dst[q] = ar_add(dst[q], wv.v[q]);
 }
 
 __global__ void k_m2m_sum(TreeView t, int L, int nr, const double* __restrict__ contrib,
@@ -309,22 +362,37 @@ __global__ void k_m2m_sum(TreeView t, int L, int nr, const double* __restrict__ 
     mult[(size_t)nr * P + j] = s;
 }
 
+// Levels with fewer nodes than kSmallLevel give each node a block of 128
+// threads: the steps of one node then take a quarter of the passes, which
+// is what bounds the time of a launch that leaves most SMs idle.
+constexpr int kSmallLevel = 2048;
+
 template <typename T>
 void launch_m2m(const TreeView& t, int Lc, int p, const double* geo,
                 const double* mult, double* contrib, const RotTables<T>& tb, cudaStream_t st) {
-    const size_t sh = (size_t)4 * m2m_warp_values(p) * sizeof(T);
-    ensure_dyn_smem((const void*)k_m2m_rot<T>, 100 * 1024);
-    const int nblk = (t.lvl_cnt[Lc] + 3) / 4;
-    (k_m2m_rot<T><<<nblk, 128, sh, st>>>(t, Lc, p, geo, mult, contrib, tb), note_launch());
+    const size_t per = (size_t)m2m_warp_values(p) * sizeof(T);
+    const int cnt = t.lvl_cnt[Lc];
+    if (cnt < kSmallLevel) {
+        ensure_dyn_smem((const void*)k_m2m_rot<T, 128>, 100 * 1024);
+        (k_m2m_rot<T, 128><<<cnt, 128, per, st>>>(t, Lc, p, geo, mult, contrib, tb), note_launch());
+        return;
+    }
+    ensure_dyn_smem((const void*)k_m2m_rot<T, 32>, 100 * 1024);
+    (k_m2m_rot<T, 32><<<(cnt + 3) / 4, 128, 4 * per, st>>>(t, Lc, p, geo, mult, contrib, tb), note_launch());
 }
 
 template <typename T>
 void launch_l2l(const TreeView& t, int L, int p, const double* geo, T* loc,
                 const RotTables<T>& tb, cudaStream_t st) {
-    const size_t sh = (size_t)4 * m2m_warp_values(p) * sizeof(T);
-    ensure_dyn_smem((const void*)k_l2l_rot<T>, 100 * 1024);
-    const int nblk = (t.lvl_cnt[L] + 3) / 4;
-    (k_l2l_rot<T><<<nblk, 128, sh, st>>>(t, L, p, geo, loc, tb), note_launch());
+    const size_t per = (size_t)m2m_warp_values(p) * sizeof(T);
+    const int cnt = t.lvl_cnt[L];
+    if (cnt < kSmallLevel) {
+        ensure_dyn_smem((const void*)k_l2l_rot<T, 128>, 100 * 1024);
+        (k_l2l_rot<T, 128><<<cnt, 128, per, st>>>(t, L, p, geo, loc, tb), note_launch());
+        return;
+    }
+    ensure_dyn_smem((const void*)k_l2l_rot<T, 32>, 100 * 1024);
+    (k_l2l_rot<T, 32><<<(cnt + 3) / 4, 128, 4 * per, st>>>(t, L, p, geo, loc, tb), note_launch());
 }
 
 }  // namespace
