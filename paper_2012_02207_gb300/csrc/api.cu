@@ -144,6 +144,7 @@ struct fmm_ctx {
     // per list: sorted directed keys, the sort's second buffer (its own, so a
     // buffer never moves to a list of another size), CSR offsets
     Buf front0, front1, lists[4], dkeys[4], dalt[4], dsrc[4], doff[4], dcount, geo;
+    Buf walk_scan;  // look-back records of the walk's ordered appends (zeroed when allocated)
     int64_t front_cap = 0, list_cap[4] = {0, 0, 0, 0};
     // host staging for fmm_solve_host
     Buf hin[4], hout[4];
@@ -197,6 +198,28 @@ int ensure(fmm_ctx* ctx, Buf& b, size_t bytes) {
         return fail(ctx, FMM_ERR_OOM, "device allocation of " + std::to_string(want) + " bytes failed");
     }
     b.bytes = want;
+    return FMM_OK;
+}
+
+// ensure, and zero the buffer whenever it is (re)allocated
+int ensure_zeroed(fmm_ctx* ctx, Buf& b, size_t bytes, cudaStream_t st) {
+    const void* old = b.ptr;
+    int rc = ensure(ctx, b, bytes);
+    if (rc != FMM_OK) return rc;
+    if (b.ptr != old && cudaMemsetAsync(b.ptr, 0, b.bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, FMM_ERR_CUDA, "clearing the walk's look-back records failed");
+    }
+    return FMM_OK;
+}
+
+int ensure_walk_scan(fmm_ctx* ctx, WalkBuffers& wb, cudaStream_t st) {
+    const int64_t tiles = walk_scan_tiles(ctx->front_cap);
+    const int rc = ensure_zeroed(ctx, ctx->walk_scan, sizeof(unsigned long long) * kWalkScanWords * (size_t)tiles, st);
+    if (rc != FMM_OK) return rc;
+    wb.scan = as<unsigned long long>(ctx->walk_scan);
+    // the records' stride is fixed by the capacity they were sized for
+    wb.scan_tiles = (int64_t)(ctx->walk_scan.bytes / (sizeof(unsigned long long) * kWalkScanWords));
     return FMM_OK;
 }
 
@@ -291,13 +314,18 @@ int build_directed(fmm_ctx* ctx, int which, cudaStream_t st) {
     if ((rc = ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(2 * np + 1))) != FMM_OK) return rc;
     ctx->ndirected[which] = 2 * np;
     unsigned long long* nkeys = as<unsigned long long>(ctx->dcount) + 8 + which;
+    // The error-controlled walk's lists (M2L, P2P) come out of the walk in a
+    // fixed order: sorting by target alone keeps that order within a target.
+    // The theta-walk's lists are sorted by (target, source), the order the
+    // scalar estimate sums in.
+    const int lo_bit = which >= 2 ? ctx->nb : 0;
     if (2 * ctx->nb <= 32) {
         // 32-bit keys: half the bytes per radix pass; both ping-pong halves fit in dalt
         uint32_t* ka = as<uint32_t>(ctx->dalt[which]);
         uint32_t* kb = ka + (2 * np + 1);
         pairs_to_directed32(as<int2>(ctx->lists[which]), ctx->ds->list_cnt + which, np, ctx->nb, ka,
                             as<unsigned long long>(ctx->dcount) + 2 + which, nkeys, st);
-        const int in1 = radix_sort32(ka, kb, 2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st, nkeys);
+        const int in1 = radix_sort32(ka, kb, 2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st, nkeys, lo_bit);
         directed_offsets_src32(in1 ? kb : ka, 2 * np, nkeys, ctx->nb, &ctx->ds->nnodes,
                                as<uint32_t>(ctx->dsrc[which]), as<uint32_t>(ctx->doff[which]), st);
         return FMM_OK;
@@ -305,7 +333,7 @@ int build_directed(fmm_ctx* ctx, int which, cudaStream_t st) {
     pairs_to_directed(as<int2>(ctx->lists[which]), ctx->ds->list_cnt + which, np, ctx->nb,
                       as<uint64_t>(ctx->dkeys[which]), as<unsigned long long>(ctx->dcount) + 2 + which, nkeys, st);
     const int in1 = radix_sort(as<uint64_t>(ctx->dkeys[which]), nullptr, as<uint64_t>(ctx->dalt[which]), nullptr,
-                               2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st, nkeys);
+                               2 * np, 2 * ctx->nb, as<uint32_t>(ctx->hist), st, nkeys, lo_bit);
     directed_offsets(as<uint64_t>(in1 ? ctx->dalt[which] : ctx->dkeys[which]), 2 * np, nkeys, ctx->nb,
                      &ctx->ds->nnodes, as<uint32_t>(ctx->dsrc[which]), as<uint32_t>(ctx->doff[which]), st);
     return FMM_OK;
@@ -329,6 +357,7 @@ int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
             wb.out[l] = as<int2>(ctx->lists[l]);
             wb.out_cap[l] = g->pair_cap[l];
         }
+        if ((rc = ensure_walk_scan(ctx, wb, st)) != FMM_OK) return rc;
         for (int l = 2 * mode; l < 2 * mode + 2; ++l) {
             if ((rc = ensure(ctx, ctx->lists[l], sizeof(int2) * (size_t)g->pair_cap[l])) != FMM_OK) return rc;
             wb.out[l] = as<int2>(ctx->lists[l]);
@@ -356,6 +385,7 @@ int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
             wb.out[l] = as<int2>(ctx->lists[l]);
             wb.out_cap[l] = ctx->list_cap[l];
         }
+        if ((rc = ensure_walk_scan(ctx, wb, st)) != FMM_OK) return rc;
         // the binomial row C(p, k) follows the sub-diagonal table (see fmm_create)
         const double* binom_row = ctx->tb.sub + (kMaxP + 1);
         CK(cudaMemsetAsync(&ctx->ds->err, 0, sizeof(unsigned), st));
@@ -376,6 +406,7 @@ int run_walk(fmm_ctx* ctx, int mode, cudaStream_t st) {
             continue;
         }
         if (it == kWalkBadIndex) return fail(ctx, FMM_ERR_CUDA, "dual-tree walk read an out-of-range cell index");
+        if (it == FMM_ERR_TIMEOUT) return fail(ctx, it, "a bounded wait of the walk's ordered appends ran out");
         if (it == FMM_ERR_CUDA)
             return fail(ctx, it, std::string("dual-tree walk failed: ") + cudaGetErrorString(cudaGetLastError()));
         if (it < 0) return fail(ctx, it, "dual-tree walk failed");
@@ -634,7 +665,8 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
     CK(cudaStreamSynchronize(st));
     CK(cudaMemcpy(&err, &ctx->ds->err, 4, cudaMemcpyDeviceToHost));
     if (err & kErrCapacity) return fail(ctx, FMM_ERR_CAPACITY, "an internal list overflowed");
-    if (err & kErrTimeout) return fail(ctx, FMM_ERR_TIMEOUT, "a bounded wait of the P2P staging ran out");
+    if (err & kErrTimeout)
+        return fail(ctx, FMM_ERR_TIMEOUT, "a bounded wait ran out (the walk's ordered appends or the P2P staging)");
     unsigned long long inter = 0;
     CK(cudaMemcpy(&inter, as<unsigned long long>(ctx->dcount) + 1, 8, cudaMemcpyDeviceToHost));
     ctx->stats.p2p_interactions = (int64_t)inter;
@@ -981,7 +1013,7 @@ void fmm_destroy(fmm_ctx* ctx) {
                   &ctx->f, &ctx->bbox, &ctx->level, &ctx->begin, &ctx->end, &ctx->parent,
                   &ctx->first_child, &ctx->nchild, &ctx->M, &ctx->S, &ctx->zc, &ctx->r, &ctx->hs, &ctx->Pk,
                   &ctx->mult, &ctx->mult32, &ctx->loc, &ctx->loc32, &ctx->fmin, &ctx->fscratch,
-                  &ctx->front0, &ctx->front1, &ctx->dcount, &ctx->zhi, &ctx->zlo, &ctx->contrib, &ctx->Phat, &ctx->r32,
+                  &ctx->front0, &ctx->front1, &ctx->walk_scan, &ctx->dcount, &ctx->zhi, &ctx->zlo, &ctx->contrib, &ctx->Phat, &ctx->r32,
                   &ctx->item_first, &ctx->slot_first, &ctx->item_leaf, &ctx->leaf_of, &ctx->part_hi,
                   &ctx->part_lo, &ctx->work, &ctx->coff, &ctx->box, &ctx->ck0, &ctx->ck1, &ctx->cv0,
                   &ctx->cv1, &ctx->cid, &ctx->jv, &ctx->jv32, &ctx->jw, &ctx->jmom, &ctx->jmult,

@@ -38,6 +38,13 @@ struct DevScalars {
     unsigned queue;                // work counter of the M2L kernels (zeroed before each launch)
     unsigned long long cnt[kMaxWalkIters + 2];  // walk frontier sizes per iteration
     unsigned long long list_cnt[4];             // far, near, m2l, p2p
+    // the walk's ordered appends: the most tiles a step of the current walk
+    // used (records to clear before the next walk), per step the tile ticket
+    // and the accepted and leaf list lengths so far
+    unsigned long long walk_tiles;
+    unsigned ticket[kMaxWalkIters + 2];
+    unsigned long long acc_hist[kMaxWalkIters + 2];
+    unsigned long long leaf_hist[kMaxWalkIters + 2];
     int nnodes;
     int level_start[kMaxLevel + 3];
 };
@@ -122,17 +129,18 @@ cudaError_t ensure_dyn_smem(const void* func, int bytes);
 void set_global_error(const char* msg);
 
 // ---------------------------------------------------------------- sort.cu
-// Stable LSD radix sort of 64-bit keys (optionally with 32-bit values) on the
-// low `bits` bits. Ping-pongs between buffers; returns 1 if the sorted data
-// ends in (k1, v1), 0 if in (k0, v0). hist needs radix_hist_words(n) words.
-// dn (device, may be NULL): the grid covers n keys but only the first
-// min(n, *dn) are sorted (a count known on the device only, in a captured solve).
+// Stable LSD radix sort of 64-bit keys (optionally with 32-bit values) on
+// bits [lo_bit, bits): keys equal there keep their input order. Ping-pongs
+// between buffers; returns 1 if the sorted data ends in (k1, v1), 0 if in
+// (k0, v0). hist needs radix_hist_words(n) words. dn (device, may be NULL):
+// the grid covers n keys but only the first min(n, *dn) are sorted (a count
+// known on the device only, in a captured solve).
 size_t radix_hist_words(int64_t n);
 int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bits,
-               uint32_t* hist, cudaStream_t st, const unsigned long long* dn = nullptr);
+               uint32_t* hist, cudaStream_t st, const unsigned long long* dn = nullptr, int lo_bit = 0);
 // The same for 32-bit keys without payload.
 int radix_sort32(uint32_t* k0, uint32_t* k1, int64_t n, int bits, uint32_t* hist, cudaStream_t st,
-                 const unsigned long long* dn = nullptr);
+                 const unsigned long long* dn = nullptr, int lo_bit = 0);
 // single-block exclusive scan of count uint32 values in place; total -> *total (device)
 void scan_exclusive_u32(uint32_t* data, int64_t count, uint32_t* total, cudaStream_t st);
 // the same for large tables (multi-block); scratch: scan_scratch_words(count) words
@@ -188,7 +196,19 @@ struct WalkBuffers {
     int64_t front_cap;
     int2* out[4];          // far, near, m2l, p2p
     int64_t out_cap[4];
+    // look-back records of the ordered appends, zeroed when allocated and
+    // after each walk: kWalkScanWords words per tile of the largest frontier
+    unsigned long long* scan;
+    int64_t scan_tiles;
 };
+constexpr int kWalkThreads = 256;    // threads of a walk block
+#ifndef GBFMM_WALK_IPT
+#define GBFMM_WALK_IPT 2
+#endif
+constexpr int kWalkIPT = GBFMM_WALK_IPT;  // frontier pairs per thread
+constexpr int kWalkTile = kWalkThreads * kWalkIPT;  // frontier pairs per tile (one block)
+constexpr int kWalkScanWords = 3;    // per tile: one record per counter (next frontier, accepted, leaf)
+inline int64_t walk_scan_tiles(int64_t front_cap) { return front_cap / kWalkTile + 2; }
 // Dual-tree walk from (root, root). mode 0: theta < 1 (lists far/near);
 // mode 1: the error-controlled MAC (lists m2l/p2p). Returns iterations or a
 // negative fmm_status. Counts land in ds->list_cnt.

@@ -274,13 +274,13 @@ void scan_exclusive_u32(uint32_t* data, int64_t count, uint32_t* total, cudaStre
 
 namespace {
 template <typename K, bool VAL>
-int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int bits, uint32_t* hist,
+int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int lo_bit, int bits, uint32_t* hist,
                     cudaStream_t st, const unsigned long long* dn) {
-    if (n <= 1 || bits <= 0) return 0;
+    if (n <= 1 || bits <= lo_bit) return 0;
     ensure_dyn_smem((const void*)k_scatter<K, VAL>, (int)scatter_smem<K, VAL>());
     const int nblocks = (int)((n + kTile - 1) / kTile);
     int cur = 0;
-    for (int shift = 0; shift < bits; shift += 8) {
+    for (int shift = lo_bit; shift < bits; shift += 8) {
         K* ki = cur ? k1 : k0;
         uint32_t* vi = cur ? v1 : v0;
         K* ko = cur ? k0 : k1;
@@ -296,14 +296,14 @@ int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int bit
 }  // namespace
 
 int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bits,
-               uint32_t* hist, cudaStream_t st, const unsigned long long* dn) {
-    return v0 ? radix_sort_impl<uint64_t, true>(k0, v0, k1, v1, n, bits, hist, st, dn)
-              : radix_sort_impl<uint64_t, false>(k0, nullptr, k1, nullptr, n, bits, hist, st, dn);
+               uint32_t* hist, cudaStream_t st, const unsigned long long* dn, int lo_bit) {
+    return v0 ? radix_sort_impl<uint64_t, true>(k0, v0, k1, v1, n, lo_bit, bits, hist, st, dn)
+              : radix_sort_impl<uint64_t, false>(k0, nullptr, k1, nullptr, n, lo_bit, bits, hist, st, dn);
 }
 
 int radix_sort32(uint32_t* k0, uint32_t* k1, int64_t n, int bits, uint32_t* hist, cudaStream_t st,
-                 const unsigned long long* dn) {
-    return radix_sort_impl<uint32_t, false>(k0, nullptr, k1, nullptr, n, bits, hist, st, dn);
+                 const unsigned long long* dn, int lo_bit) {
+    return radix_sort_impl<uint32_t, false>(k0, nullptr, k1, nullptr, n, lo_bit, bits, hist, st, dn);
 }
 
 }  // namespace gbfmm

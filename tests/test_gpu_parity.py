@@ -142,8 +142,12 @@ def test_edge_cases():
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_deterministic_and_capacity_regrow(prec):
+    """Repeated solves, and a solve whose buffers had to grow mid-walk, give
+    the same forces bit for bit and the walk's lists in the same order (the
+    walk appends in frontier order, whatever the scheduling)."""
     pos, _, m = ics.plummer(30000, 3)
     f, a1, p1 = solve(pos, m, p=8, eps=1e-7, precision=prec)
+    lists1 = [f.export_pairs(w) for w in ("far", "near", "m2l", "p2p")]
     d = to_dev(pos, m)
     ax, ay, az, pot = f.solve(*d)
     a2 = torch.stack([ax, ay, az], 1).cpu().numpy()
@@ -151,6 +155,8 @@ def test_deterministic_and_capacity_regrow(prec):
     g, a3, p3 = solve(pos, m, p=8, eps=1e-7, precision=prec, fault_inject=1)
     assert g.stats()["regrows"] > 0
     assert np.array_equal(a1, a3) and np.array_equal(p1, p3)
+    for w, l1 in zip(("far", "near", "m2l", "p2p"), lists1):
+        assert np.array_equal(l1, f.export_pairs(w)) and np.array_equal(l1, g.export_pairs(w)), w
 
 
 @pytest.mark.parametrize("soft", [0.0, 1e-3])
