@@ -79,7 +79,8 @@ typedef struct {
     unsigned fault_inject; /* test hook, 0 in production: bit 0 forces tiny list capacities
                               so the capacity-regrow path runs; bit 1 makes every bulk-copy wait
                               of the FP32 P2P expect 16 bytes that never come, so it runs out
-                              and the call returns FMM_ERR_TIMEOUT */
+                              and the call returns FMM_ERR_TIMEOUT; bit 2 makes the walk's
+                              look-back wait for records no tile writes, with the same outcome */
     double soft;           /* Plummer softening length eps_soft >= 0 (Appendix B; 0: Newtonian).
                               P2P, fmm_direct and the near part of the scalar-force estimate
                               use the softened kernel; the far field stays the expansion of

@@ -214,6 +214,7 @@ int ensure_zeroed(fmm_ctx* ctx, Buf& b, size_t bytes, cudaStream_t st) {
 }
 
 int ensure_walk_scan(fmm_ctx* ctx, WalkBuffers& wb, cudaStream_t st) {
+    wb.stall_lookback = (ctx->cfg.fault_inject & 4u) ? 1 : 0;
     const int64_t tiles = walk_scan_tiles(ctx->front_cap);
     const int rc = ensure_zeroed(ctx, ctx->walk_scan, sizeof(unsigned long long) * kWalkScanWords * (size_t)tiles, st);
     if (rc != FMM_OK) return rc;

@@ -200,6 +200,7 @@ struct WalkBuffers {
     // after each walk: kWalkScanWords words per tile of the largest frontier
     unsigned long long* scan;
     int64_t scan_tiles;
+    int stall_lookback = 0;  // test hook: the look-back waits for records no tile writes
 };
 constexpr int kWalkThreads = 256;    // threads of a walk block
 #ifndef GBFMM_WALK_IPT

@@ -6,13 +6,14 @@
 //
 // The walk (Sec. 2.1) runs level-synchronously: each launch classifies
 // every pair of the current frontier and appends the accepted pairs, the
-// leaf pairs and the child pairs of the next frontier in frontier order.
-// Blocks take tiles of 256 pairs by ticket; a tile's output offsets come
-// from a block scan and a decoupled look-back over the earlier tiles'
-// published totals, so every list comes out in one fixed order. The
-// theta-walk's lists are still sorted by (target, source) downstream (the
-// scalar estimate sums in that order); the error-controlled walk's lists
-// are sorted by target only and keep their walk order within a target.
+// leaf pairs and the child pairs of the next frontier. The error-controlled
+// walk appends in frontier order: blocks take tiles of kWalkTile pairs by
+// ticket, and a tile's output offsets come from a block scan and a
+// decoupled look-back over the earlier tiles' published totals, so its
+// lists come out in one fixed order and are then sorted by target only
+// (keeping the walk order within a target). The theta-walk appends with
+// warp-aggregated atomics; its lists are sorted by (target, source), the
+// order the scalar estimate sums in.
 #include "gbfmm_internal.cuh"
 
 namespace gbfmm {
@@ -90,6 +91,11 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ unsigned long long walk_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -114,9 +120,11 @@ __device__ __forceinline__ unsigned long long walk_record(unsigned long long kin
 // Exclusive prefix of one counter over the tiles before `tile`, by one warp:
 // lane l reads tile j - l, waiting until that tile has published for this
 // step; the nearest tile with an inclusive prefix ends the walk back.
-__device__ unsigned long long lookback(const unsigned long long* rec, int64_t tile, int it, unsigned* err) {
+__device__ unsigned long long lookback(const unsigned long long* rec, int64_t tile, int it, unsigned* err,
+                                       int stall) {
     const int lane = threadIdx.x & 31;
-    const unsigned long long step_bits = (unsigned long long)(it & 0xff);
+    // (stall: a step no record carries, so every wait runs out)
+    const unsigned long long step_bits = (unsigned long long)((stall ? it + 0x80 : it) & 0xff);
     unsigned long long excl = 0;
     const unsigned long long t0 = walk_ns();
     for (int64_t j = tile - 1;; j -= 32) {
@@ -126,7 +134,8 @@ __device__ unsigned long long lookback(const unsigned long long* rec, int64_t ti
         if (idx >= 0) {
             unsigned long long w = ld_relaxed(rec + idx);
             while ((w >> 62) == 0ull || ((w >> 54) & 0xffull) != step_bits) {
-                if (walk_ns() - t0 > kLookbackNs) {
+                // give up after kLookbackNs, or at once when some wait already ran out
+                if (walk_ns() - t0 > kLookbackNs || (ld_relaxed_u32(err) & kErrTimeout)) {
                     late = true;
                     break;
                 }
@@ -261,6 +270,84 @@ __device__ __forceinline__ void classify_pair(const WalkCells& c, const int2* __
     }
 }
 
+// the child pairs of a split pair, from fout[o] on
+__device__ __forceinline__ void emit_children(const WalkCells& c, int2* __restrict__ fout, unsigned long long o,
+                                              int split_kind, int a, int b) {
+    if (split_kind == 1) {
+        const int c0 = c.first_child[a], nc = c.nchild[a];
+        for (int i = 0; i < nc; ++i)
+            for (int j = i; j < nc; ++j) fout[o++] = make_int2(c0 + i, c0 + j);
+    } else if (split_kind == 2) {
+        const int c0 = c.first_child[a], nc = c.nchild[a];
+        for (int i = 0; i < nc; ++i) fout[o++] = make_int2(c0 + i, b);
+    } else {
+        const int c0 = c.first_child[b], nc = c.nchild[b];
+        for (int i = 0; i < nc; ++i) fout[o++] = make_int2(a, c0 + i);
+    }
+}
+
+// Append cnt items per lane to a list; returns the lane's first slot. All
+// 32 lanes of the warp must call it.
+__device__ __forceinline__ unsigned long long warp_alloc(unsigned long long* counter, unsigned cnt) {
+    const int lane = threadIdx.x & 31;
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + (incl - cnt);
+}
+
+// One step of the theta-walk (mode 0), appending with warp-aggregated
+// atomics: its lists are sorted by (target, source) afterwards, so the order
+// of the appends does not matter, and the atomics cost less than the
+// ordered appends' look-back.
+__global__ void __launch_bounds__(256) k_walk_step_any_order(WalkCells c, const int2* __restrict__ fin,
+                                                             const unsigned long long* cnt_in,
+                                                             int2* __restrict__ fout,
+                                                             unsigned long long* cnt_out, int64_t cap_out,
+                                                             int2* __restrict__ acc_list,
+                                                             unsigned long long* cnt_acc, int64_t cap_acc,
+                                                             int2* __restrict__ leaf_list,
+                                                             unsigned long long* cnt_leaf, int64_t cap_leaf,
+                                                             unsigned* err) {
+    __shared__ float binom32[kMaxP + 1];
+    if (threadIdx.x <= (unsigned)c.p) binom32[threadIdx.x] = (float)c.binom[threadIdx.x];
+    __syncthreads();
+    const float eps32 = (float)c.eps;
+    const int64_t nin = (int64_t)*cnt_in;
+    if (nin > cap_out) {  // an incomplete input frontier: the host grows the buffers
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrCapacity);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp0 * 32; base < nin; base += nwarps * 32) {
+        int a, b, split_kind;
+        unsigned n_next, n_acc, n_leaf;
+        classify_pair<0>(c, fin, nin, base + lane, binom32, eps32, err, a, b, split_kind, n_next, n_acc, n_leaf);
+        const unsigned long long so = warp_alloc(cnt_out, n_next);
+        const unsigned long long sa = warp_alloc(cnt_acc, n_acc);
+        const unsigned long long sl = warp_alloc(cnt_leaf, n_leaf);
+        if (n_acc) {
+            if ((int64_t)sa < cap_acc) acc_list[sa] = make_int2(a, b); else atomicOr(err, kErrCapacity);
+        }
+        if (n_leaf) {
+            if ((int64_t)sl < cap_leaf) leaf_list[sl] = make_int2(a, b); else atomicOr(err, kErrCapacity);
+        }
+        if (n_next) {
+            if ((int64_t)(so + n_next) > cap_out) atomicOr(err, kErrCapacity);
+            else emit_children(c, fout, so, split_kind, a, b);
+        }
+    }
+}
+
 // One step of the walk: the pairs fin[0..*cnt_in) become the next frontier
 // fout (count into *cnt_out), accepted pairs appended to acc_list from
 // position acc_hist[it] and leaf pairs to leaf_list from leaf_hist[it], in
@@ -277,7 +364,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk_step(WalkCells c, int it,
                                                          int2* __restrict__ leaf_list, int64_t cap_leaf,
                                                          DevScalars* ds, int list_acc, int list_leaf,
                                                          unsigned long long* scan, int64_t scan_tiles,
-                                                         unsigned* err) {
+                                                         int stall, unsigned* err) {
     __shared__ float binom32[kMaxP + 1];
     __shared__ unsigned s_tile;
     __shared__ unsigned s_wsum[3][kWalkThreads / 32];
@@ -352,7 +439,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk_step(WalkCells c, int it,
                 }
             } else {
                 if (lane == 0) st_relaxed(rec + tile, walk_record(kKindAgg, it, tot[warp]));
-                const unsigned long long ex = lookback(rec, tile, it, err);
+                const unsigned long long ex = lookback(rec, tile, it, err, stall);
                 if (lane == 0) {
                     st_relaxed(rec + tile, walk_record(kKindIncl, it, ex + tot[warp]));
                     s_excl[warp] = ex;
@@ -619,13 +706,13 @@ int dual_tree_walk(int mode, const TreeView& t, const double* zc, const double* 
     const int grid = device_sm_count() * 8;
     auto step = [&](int it, const int2* fi, int2* fo) {
         if (mode == 0)
-            (k_walk_step<0><<<grid, kWalkThreads, 0, st>>>(c, it, fi, ds->cnt + it, fo, ds->cnt + it + 1, wb.front_cap,
-                                                        acc_list, cap_acc, leaf_list, cap_leaf, ds, la, ll, wb.scan,
-                                                        wb.scan_tiles, &ds->err), note_launch());
+            (k_walk_step_any_order<<<grid, 256, 0, st>>>(c, fi, ds->cnt + it, fo, ds->cnt + it + 1, wb.front_cap,
+                                                          acc_list, ds->list_cnt + la, cap_acc, leaf_list,
+                                                          ds->list_cnt + ll, cap_leaf, &ds->err), note_launch());
         else
             (k_walk_step<1><<<grid, kWalkThreads, 0, st>>>(c, it, fi, ds->cnt + it, fo, ds->cnt + it + 1, wb.front_cap,
                                                         acc_list, cap_acc, leaf_list, cap_leaf, ds, la, ll, wb.scan,
-                                                        wb.scan_tiles, &ds->err), note_launch());
+                                                        wb.scan_tiles, wb.stall_lookback, &ds->err), note_launch());
     };
     if (fixed_iters > 0) {
         // a planned number of steps with no read-back (a captured solve): steps
