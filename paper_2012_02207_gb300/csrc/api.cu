@@ -510,6 +510,19 @@ int solve_device(fmm_ctx* ctx, int64_t n, int nclusters, const int64_t* offsets,
         CK(cudaStreamSynchronize(st));
         if (err & kErrNonfinite) return fail(ctx, FMM_ERR_NONFINITE, "non-finite position or mass, or a mass <= 0");
         if (err & kErrCoincident) return fail(ctx, FMM_ERR_COINCIDENT, "two bodies share the same position");
+        if (err & kErrLongRun) {
+            // a run of equal keys longer than the bounded scan: check every body exactly
+            // (the cluster pass's sort buffers are free again here)
+            if ((rc = ensure(ctx, ctx->ck0, 8 * N)) || (rc = ensure(ctx, ctx->ck1, 8 * N)) ||
+                (rc = ensure(ctx, ctx->cv0, 4 * N)) || (rc = ensure(ctx, ctx->cv1, 4 * N)))
+                return rc;
+            coincident_exact(tb, as<uint64_t>(ctx->ck0), as<uint32_t>(ctx->cv0), as<uint64_t>(ctx->ck1),
+                             as<uint32_t>(ctx->cv1), st);
+            CK(cudaMemcpyAsync(&err, &ctx->ds->err, 4, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (err & kErrCoincident) return fail(ctx, FMM_ERR_COINCIDENT, "two bodies share the same position");
+            CK(cudaMemsetAsync(&ctx->ds->err, 0, sizeof(unsigned), st));
+        }
     }
     const int nnodes = (int)total;  // the node arrays' size (the planned capacity in graph form)
     ctx->nnodes = nnodes;

@@ -23,6 +23,7 @@ enum : unsigned {
     kErrNonfinite = 4u,
     kErrTimeout = 8u,
     kErrIndex = 16u,  // a cell index out of range (an internal error)
+    kErrLongRun = 32u,  // a run of equal keys longer than the bounded coincidence scan (not an error)
 };
 
 // real layout of a hat coefficient vector: degree n starts at n*n with
@@ -178,6 +179,12 @@ struct TreeBuffers {
 // total lands at chunk_cnt[22 * nchunks]. sorted_in_1 tells where the sorted
 // keys/perm ended up.
 void tree_build_count(TreeBuffers& b, int* sorted_in_1, cudaStream_t st);
+// Exact coincidence check of all n sorted bodies (for key runs longer than
+// the bounded scan of k_lcp): sorts a 64-bit hash of (cluster, position) with
+// the body index through (hk0, hv0) / (hk1, hv1) and compares bodies with
+// equal hashes exactly; sets kErrCoincident in ds->err.
+void coincident_exact(const TreeBuffers& b, uint64_t* hk0, uint32_t* hv0, uint64_t* hk1, uint32_t* hv1,
+                      cudaStream_t st);
 // doubles (times 6) of the bounding-cube partials for nclusters clusters
 int bbox_partials(int nclusters);
 // node level/begin arrays and ds->level_start, ds->nnodes

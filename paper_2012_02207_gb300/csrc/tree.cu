@@ -184,6 +184,7 @@ __global__ void k_gather(const double* __restrict__ x, const double* __restrict_
 
 // lcp_i (levels shared by keys i-1 and i; -1 where a cluster begins) and
 // the coincident-body check (within a cluster).
+constexpr int kRunScan = 4096;
 __global__ void k_lcp(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ cid,
                       const double* __restrict__ xs, const double* __restrict__ ys,
                       const double* __restrict__ zs, int64_t n, int8_t* __restrict__ lcp, unsigned* err) {
@@ -195,11 +196,52 @@ __global__ void k_lcp(const uint64_t* __restrict__ keys, const uint32_t* __restr
     const uint64_t d = k ^ keys[i - 1];
     lcp[i] = d ? (int8_t)((__clzll((long long)d) - 1) / 3) : (int8_t)kMaxLevel;
     if (d == 0) {
-        // equal keys: compare with the earlier bodies of the run (bounded)
+        // equal keys: compare with the earlier bodies of the run, at most
+        // kRunScan back; a longer run is flagged for coincident_exact
         const double a = xs[i], b = ys[i], c = zs[i];
         int steps = 0;
-        for (int64_t j = i - 1; j >= 0 && keys[j] == k && (!cid || cid[j] == ci) && steps < 4096; --j, ++steps)
-            if (xs[j] == a && ys[j] == b && zs[j] == c) { atomicOr(err, kErrCoincident); break; }
+        int64_t j = i - 1;
+        for (; j >= 0 && keys[j] == k && (!cid || cid[j] == ci) && steps < kRunScan; --j, ++steps)
+            if (xs[j] == a && ys[j] == b && zs[j] == c) { atomicOr(err, kErrCoincident); return; }
+        if (steps == kRunScan && j >= 0 && keys[j] == k && (!cid || cid[j] == ci)) atomicOr(err, kErrLongRun);
+    }
+}
+
+// 64-bit mix of a body's cluster and position (-0.0 counted as +0.0, so
+// bodies equal under == hash alike): the finaliser of SplitMix64 over the
+// combined words
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__global__ void k_pos_hash(const double* __restrict__ xs, const double* __restrict__ ys,
+                           const double* __restrict__ zs, const uint32_t* __restrict__ cid, int64_t n,
+                           uint64_t* __restrict__ h, uint32_t* __restrict__ idx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t z = mix64((uint64_t)__double_as_longlong(xs[i] + 0.0) ^ 0x9e3779b97f4a7c15ull);
+    z = mix64(z ^ (uint64_t)__double_as_longlong(ys[i] + 0.0));
+    z = mix64(z ^ (uint64_t)__double_as_longlong(zs[i] + 0.0));
+    h[i] = mix64(z ^ (uint64_t)(cid ? cid[i] : 0u));
+    idx[i] = (uint32_t)i;
+}
+// bodies with equal hashes: compare positions and clusters exactly, each
+// with the earlier bodies of its hash run (a run of distinct positions
+// needs a 64-bit hash collision)
+__global__ void k_pos_equal(const uint64_t* __restrict__ h, const uint32_t* __restrict__ idx,
+                            const double* __restrict__ xs, const double* __restrict__ ys,
+                            const double* __restrict__ zs, const uint32_t* __restrict__ cid, int64_t n,
+                            unsigned* err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || i == 0 || h[i] != h[i - 1]) return;
+    const uint32_t bi = idx[i];
+    for (int64_t j = i - 1; j >= 0 && h[j] == h[i]; --j) {
+        const uint32_t bj = idx[j];
+        if (xs[bi] == xs[bj] && ys[bi] == ys[bj] && zs[bi] == zs[bj] && (!cid || cid[bi] == cid[bj])) {
+            atomicOr(err, kErrCoincident);
+            return;
+        }
     }
 }
 
@@ -472,6 +514,17 @@ void cell_geometry(const TreeView& t, const double* xs, const double* ys, const 
     for (int L = t.nlevels - 2; L >= 0; --L)
         if (t.lvl_cnt[L] > 0)
             (k_geometry_internal<<<blocks_for(t.lvl_cnt[L], 128), 128, 0, st>>>(t, L, M, S, zc, r), note_launch());
+}
+
+void coincident_exact(const TreeBuffers& b, uint64_t* hk0, uint32_t* hv0, uint64_t* hk1, uint32_t* hv1,
+                      cudaStream_t st) {
+    const int64_t n = b.n;
+    if (n < 2) return;
+    const uint32_t* cid = b.nclusters > 1 ? b.cid : nullptr;
+    (k_pos_hash<<<blocks_for(n, 256), 256, 0, st>>>(b.xs, b.ys, b.zs, cid, n, hk0, hv0), note_launch());
+    const int in1 = radix_sort(hk0, hv0, hk1, hv1, n, 64, b.hist, st);
+    (k_pos_equal<<<blocks_for(n, 256), 256, 0, st>>>(in1 ? hk1 : hk0, in1 ? hv1 : hv0, b.xs, b.ys, b.zs, cid, n,
+                                                     &b.ds->err), note_launch());
 }
 
 }  // namespace gbfmm

@@ -205,6 +205,44 @@ def test_walk_lookback_wait_that_runs_out_reports_a_timeout():
     assert np.array_equal(acc, acc2) and np.array_equal(pot, pot2)
 
 
+def _long_key_run(coincident):
+    """Two bodies at opposite corners of the cube [-1, 1]^3 and 5000 more inside
+    one level-21 cell near (0.3, 0.3, 0.3), so their Morton keys are all equal;
+    with `coincident`, the last of them sits on the first, 4999 places apart in
+    the key run, beyond the bounded scan of equal keys."""
+    rng = np.random.default_rng(11)
+    core = 0.3 + rng.random((5000, 3)) * 1e-7
+    if coincident:
+        core[-1] = core[0]
+    pos = np.vstack([[[-1.0, -1.0, -1.0], [1.0, 1.0, 1.0]], core])
+    return pos, np.full(len(pos), 1.0 / len(pos))
+
+
+@pytest.mark.parametrize("coincident", [True, False])
+def test_coincident_bodies_beyond_the_bounded_key_scan(coincident):
+    """A run of more than 4096 equal keys sends the solve to the exact check
+    (a hash sort of all positions): the GPU reports coincident bodies exactly
+    when the oracle does, and otherwise solves the degenerate leaf (5000 bodies
+    that level 21 cannot split) to the oracle's forces."""
+    pos, m = _long_key_run(coincident)
+    run = oracle.OracleRun(pos, m, p=8, eps=1e-7, stage=oracle.STAGE_TREE)
+    if coincident:
+        assert run.status == -5
+    else:
+        keys = run.tree()["keys"]
+        longest = np.max(np.diff(np.flatnonzero(np.r_[True, keys[1:] != keys[:-1], True])))
+        assert run.status == 0 and longest > 4096
+    for precision in ("fp64", "mixed"):
+        if coincident:
+            with pytest.raises(gb.FmmError) as e:
+                solve(pos, m, p=8, eps=1e-7, precision=precision)
+            assert e.value.status == -5
+        elif precision == "fp64":
+            _, acc, _ = solve(pos, m, p=8, eps=1e-7, precision=precision)
+            oacc, _ = oracle.fmm(pos, m, p=8, eps=1e-7)
+            assert np.max(np.linalg.norm(acc - oacc, axis=1) / np.linalg.norm(oacc, axis=1)) <= 1e-10
+
+
 def test_host_entry_point_matches_device():
     pos, _, m = ics.plummer(5000, 17)
     f, acc, pot = solve(pos, m, p=8, eps=1e-7)
