@@ -252,7 +252,9 @@ size_t scan_scratch_words(int64_t count) { return (size_t)((count + kSegment - 1
 
 void scan_exclusive_u32_large(uint32_t* data, int64_t count, uint32_t* total, uint32_t* scratch,
                               cudaStream_t st) {
-    if (count <= 65536) {
+    // one block scans 4096 values at a time, one tile after another: beyond a
+    // few tiles the three parallel passes finish sooner
+    if (count <= 4 * 4096) {
         (k_scan<<<1, 1024, 0, st>>>(data, count, total), note_launch());
         return;
     }
