@@ -316,7 +316,10 @@ void m2l_f32(const int* dnn, int p, const uint32_t* src, const uint32_t* off,
 bool m2l32_supported(int p);
 
 // ----------------------------------------------------------------- p2p.cu
-constexpr int kLeavesPerItem = 64;  // source leaves per P2P work item
+#ifndef GBFMM_LEAVES_PER_ITEM
+#define GBFMM_LEAVES_PER_ITEM 128
+#endif
+constexpr int kLeavesPerItem = GBFMM_LEAVES_PER_ITEM;  // source leaves per P2P work item
 void upload_leaf_tables(const HostTables& h);
 // Leaf evaluation: P2P over bounded work items (target leaf, up to
 // kLeavesPerItem source leaves) written as per-body partials, then per body
