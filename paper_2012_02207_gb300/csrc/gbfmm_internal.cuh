@@ -211,7 +211,7 @@ struct WalkBuffers {
 };
 constexpr int kWalkThreads = 256;    // threads of a walk block
 #ifndef GBFMM_WALK_IPT
-#define GBFMM_WALK_IPT 2
+#define GBFMM_WALK_IPT 4
 #endif
 constexpr int kWalkIPT = GBFMM_WALK_IPT;  // frontier pairs per thread
 constexpr int kWalkTile = kWalkThreads * kWalkIPT;  // frontier pairs per tile (one block)
