@@ -203,8 +203,9 @@ struct WalkBuffers {
     int64_t front_cap;
     int2* out[4];          // far, near, m2l, p2p
     int64_t out_cap[4];
-    // look-back records of the ordered appends, zeroed when allocated and
-    // after each walk: kWalkScanWords words per tile of the largest frontier
+    // look-back records of the ordered appends, zeroed when allocated; each
+    // walk first clears those the previous walk used. kWalkScanWords words
+    // per tile of the largest frontier
     unsigned long long* scan;
     int64_t scan_tiles;
     int stall_lookback = 0;  // test hook: the look-back waits for records no tile writes
